@@ -1,0 +1,92 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws random numbers; it holds none of the alias-table
+arithmetic.  The same arrays feed the CUDA library and the CPU oracle.
+
+The paper evaluates on uniform random weights and on shuffled power-law
+weights w_i = i^-alpha in random order (Sec. 6).  The generators below cover
+those and the other shapes the workloads use:
+
+* ``uniform``           U[0,1) drawn in FP64, rounded to FP32.
+* ``zipf_permuted``     w = 1/rank^s with the ranks 1..N randomly permuted.
+* ``exponential``       Exp(1) drawn in FP64, rounded to FP32.
+* ``gamma``             Gamma(shape, 1) in FP64, rounded to FP32 (shape 0.1
+                        gives exact zeros and FP32 subnormals).
+* ``log_uniform_sizes`` segment sizes floor(exp(U[ln lo, ln hi])).
+* ``batched``           many segments of the above, concatenated, with
+                        64-bit offsets.
+
+All use ``numpy.random.default_rng(seed)`` and draw in chunks of 2^24 so the
+host never holds more than one FP64 chunk at a time.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_CHUNK = 1 << 24
+
+
+def _chunked(n: int, draw) -> np.ndarray:
+    out = np.empty(n, np.float32)
+    for a in range(0, n, _CHUNK):
+        b = min(n, a + _CHUNK)
+        out[a:b] = draw(b - a).astype(np.float32)
+    return out
+
+
+def uniform(n: int, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return _chunked(n, lambda m: rng.random(m))
+
+
+def zipf_permuted(n: int, seed: int, s: float = 1.0) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    rank = rng.permutation(n).astype(np.float64) + 1.0
+    out = np.empty(n, np.float32)
+    for a in range(0, n, _CHUNK):
+        b = min(n, a + _CHUNK)
+        out[a:b] = (1.0 / np.power(rank[a:b], s)).astype(np.float32)
+    return out
+
+
+def exponential(n: int, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return _chunked(n, lambda m: rng.exponential(1.0, m))
+
+
+def gamma(n: int, seed: int, shape: float = 0.1) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return _chunked(n, lambda m: rng.gamma(shape, 1.0, m))
+
+
+def log_uniform_sizes(count: int, seed: int, lo: int, hi: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    x = np.floor(np.exp(rng.uniform(math.log(lo), math.log(hi), count)))
+    return np.clip(x, lo, hi).astype(np.int64)
+
+
+def batched(sizes, seed: int, kind: str = "gamma", **kw):
+    """Concatenate one segment per size; returns (weights f32, offsets u64)."""
+    sizes = np.asarray(sizes, np.int64)
+    off = np.zeros(sizes.size + 1, np.uint64)
+    off[1:] = np.cumsum(sizes).astype(np.uint64)
+    total = int(off[-1])
+    gen = {"gamma": gamma, "uniform": uniform, "exponential": exponential}[kind]
+    return gen(total, seed, **kw), off
+
+
+def by_name(kind: str, n: int, seed: int) -> np.ndarray:
+    """Named weight distributions used by tests and the benchmark."""
+    if kind == "uniform":
+        return uniform(n, seed)
+    if kind == "zipf":
+        return zipf_permuted(n, seed, 1.0)
+    if kind == "zipf0.5":
+        return zipf_permuted(n, seed, 0.5)
+    if kind == "exponential":
+        return exponential(n, seed)
+    if kind == "gamma":
+        return gamma(n, seed, 0.1)
+    raise ValueError(kind)
