@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark: alias-table build + sampling on GB300, one JSON line on rank 0.
+
+Workload (default): one table of N = 1e8 FP32 weights w_i = 1/rank^1.0 with
+the ranks randomly permuted (seed 3) -- the paper's shuffled power law --
+built with PSA, then 1e9 samples drawn by Walker's rule (Philox seed 2).
+A step is one build plus the samples.  Inputs (400 MB weights, 800 MB table,
+4 GB samples) are larger than L2, so no L2 flush is needed between steps.
+
+`value` is build throughput (items/s) from CUDA events around the build
+kernels of every timed step; `samples_per_s` comes from the events around
+the sampler.  Under torchrun every rank builds and samples its own table (an
+independent problem, no data-path collective): scaling is weak and `value`
+sums all ranks' items over the slowest rank's time.
+
+`--impl reference` times the CPU oracle (Vose's FP64 construction) on the
+host cores for the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "alias build items/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+BUILD_BYTES_PER_ITEM = 32      # read w twice, write + read lh, write rows
+SAMPLE_BYTES_PER_DRAW = 36     # one 32-byte row sector + a 4-byte output
+KERNELS_PER_BUILD = 7          # sum, total, partition, split ends, split, pack, info
+KERNELS_PER_SAMPLE = 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["wrs", "reference"], default="wrs")
+    ap.add_argument("--n", type=int, default=100_000_000)
+    ap.add_argument("--samples", type=int, default=1_000_000_000)
+    ap.add_argument("--section", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+
+def oracle_build_items_per_s(w, reps_budget_s: float = 20.0):
+    """Time the FP64 Vose oracle (single thread) on `w`; returns (items/s, runs)."""
+    import oracle
+    oracle.build()
+    times = []
+    t_all = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        oracle.vose(w)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all > reps_budget_s or len(times) >= 3:
+            break
+    return w.size / statistics.median(times), len(times)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2106_12270_gb300 import inputs
+    import oracle
+    oracle.build()
+    # bounded sample of the workload: the first 1e7 items of the same array
+    # recipe keep each step near one second of single-core work
+    n = min(args.n, 10_000_000)
+    w = inputs.zipf_permuted(n, 3)
+    for _ in range(args.warmup):
+        oracle.vose(w)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.vose(w)
+        ts.append(time.perf_counter() - t0)
+    sec = sum(ts) / len(ts)
+    value = n / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "items/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"single table, shuffled power law s=1.0 (seed 3), "
+                               f"oracle sample N={n} of N={args.n}", "n": n},
+        "cpu_baseline": {"value": value, "unit": "items/s", "cores": 1, "kind": "oracle",
+                         "sample": f"Vose FP64 build of N={n} shuffled-power-law weights"},
+        "e2e": {"value": value, "unit": "items/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_2106_12270_gb300 as wrs
+    from paper_2106_12270_gb300 import _build, inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    _build.build()
+    wrs.lib()
+
+    n, count = args.n, args.samples
+    cfg = wrs.config(args.section)
+    w_host = inputs.zipf_permuted(n, 3 + rank)
+    w = torch.from_numpy(w_host).cuda()
+    builder = wrs.Builder(n, cfg)
+    rows = torch.empty(n, dtype=torch.int64, device="cuda")
+    out = torch.empty(count, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        wrs.build_rows(w, rows, builder.ws, builder.info, cfg)
+        if evs:
+            evs[1].record(stream)
+        wrs.sample_rows(rows, n, 0, count, 2, out)
+        if evs:
+            evs[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    info = wrs.parse_info(builder.info)
+    if info["status"] != wrs.OK:
+        raise RuntimeError(f"build failed: {info}")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)  # let the sampler see the region
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    build_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    sample_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    if dist:
+        t = torch.tensor([total_ms, build_ms, sample_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, build_ms, sample_ms = t.tolist()
+    ms_per_step = total_ms / args.steps
+
+    # end to end through the C ABI with host buffers: pinned weights in,
+    # table rows out, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        w_pin = torch.from_numpy(w_host).pin_memory()
+        rows_pin = torch.empty(n, dtype=torch.int64).pin_memory()
+        w_dev = torch.empty_like(w)
+
+        def e2e_step():
+            w_dev.copy_(w_pin, non_blocking=True)
+            wrs.build_rows(w_dev, rows, builder.ws, builder.info, cfg)
+            rows_pin.copy_(rows, non_blocking=True)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = a.elapsed_time(b) / args.steps
+        if dist:
+            t = torch.tensor([e2e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = t.item()
+        e2e = {"value": world * n / (e2e_ms / 1e3), "unit": "items/s",
+               "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n,
+               "ms_per_step": e2e_ms}
+
+    hbm, peak_kind = peaks()
+    build_gbs = BUILD_BYTES_PER_ITEM * n / (build_ms / 1e3) / 1e9
+    sample_gbs = SAMPLE_BYTES_PER_DRAW * count / (sample_ms / 1e3) / 1e9
+    build_roof = {"bound": "hbm", "achieved": build_gbs, "peak": hbm, "unit": "GB/s",
+                  "frac": build_gbs / hbm, "traffic": None, "kernel": "build (7 kernels)",
+                  "peak_kind": peak_kind}
+    sample_roof = {"bound": "hbm", "achieved": sample_gbs, "peak": hbm, "unit": "GB/s",
+                   "frac": sample_gbs / hbm, "traffic": None, "kernel": "k_sample_naive",
+                   "peak_kind": peak_kind}
+    dominant = sample_roof if sample_ms >= build_ms else build_roof
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nb = min(n, 10_000_000)
+        ips, runs = oracle_build_items_per_s(w_host[:nb].copy())
+        cpu = {"value": ips, "unit": "items/s", "cores": 1, "kind": "oracle",
+               "sample": f"Vose FP64 build of the first {nb} weights, median of {runs} runs"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": world * n / (build_ms / 1e3), "unit": "items/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u128 fixed point (build), u32 (sampling)",
+            "data": "synthetic",
+            "config": {"workload": "single table N=1e8, shuffled power law w=1/rank (seed 3); "
+                                   "build + 1e9 naive Walker samples (Philox seed 2)",
+                       "n": n, "samples": count, "section_size": args.section,
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
+            "build_ms": build_ms, "sample_ms": sample_ms,
+            "samples_per_s": world * count / (sample_ms / 1e3),
+            "roofline": dominant, "build_roofline": build_roof, "sample_roofline": sample_roof,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": args.steps * (KERNELS_PER_BUILD + KERNELS_PER_SAMPLE),
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,190 @@
+/*
+ * wrs.h - C ABI of the GB300 alias-table library (weighted random sampling,
+ * "Weighted Random Sampling on GPUs", Lehmann, Huebschle-Schneider, Sanders,
+ * arXiv 2106.12270).
+ *
+ * Problem (Sec. 1): items 0..N-1 with weights w_i >= 0 and total W; draw
+ * item i with probability w_i / W, with replacement.
+ *
+ * Alias table (Sec. 2.2): N rows, each one bucket of W/N.  Row b keeps the
+ * share prob_b (in [0,1], in units of one bucket) for item b and gives the
+ * rest to item alias_b.  A row is 8 bytes: {float prob; uint32 alias}.
+ *
+ * Conventions for every call:
+ *  - Pointers named d_* are device pointers (GPU global memory), h_* are
+ *    host pointers.  The caller owns every buffer it passes; the library
+ *    never frees, resizes or keeps a caller buffer beyond the call (except
+ *    where a table object is documented to own memory).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls named *_rows / wrs_step_* / wrs_sample* only enqueue
+ *    work on that stream and return without synchronising; their device
+ *    results are valid once the stream reaches that point.
+ *  - Every call returns an int status (enum wrs_status).  Argument errors
+ *    are detected on the host before anything is enqueued, and output
+ *    buffers are then left untouched.  Errors that depend on the data (a
+ *    negative or non-finite weight, a zero total) are found on the device
+ *    and reported through wrs_build_info.status.
+ *  - N is limited to [1, 2^31 - 1] (indices are 32-bit).
+ *  - No call here uses more than one GPU; every call runs on the current
+ *    CUDA device of the calling thread.
+ */
+#ifndef WRS_H
+#define WRS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------------- */
+/* Status codes                                                            */
+/* ---------------------------------------------------------------------- */
+enum wrs_status {
+    WRS_OK = 0,
+    WRS_EINVAL = 1,      /* bad argument or negative weight */
+    WRS_EZEROSUM = 2,    /* all weights are zero: no distribution (Sec. 1) */
+    WRS_ENONFINITE = 3,  /* a weight is NaN or infinite */
+    WRS_ENOMEM = 4,      /* device allocation failed or budget exceeded */
+    WRS_ETIMEOUT = 5,    /* a bounded device wait gave up */
+    WRS_ECUDA = 6,       /* a CUDA runtime call failed */
+    WRS_EBUSY = 7,       /* request loop: no room right now */
+    WRS_ENOTFOUND = 8    /* request loop: unknown ticket */
+};
+
+/* Text for a status code (static storage, never NULL). */
+const char *wrs_strerror(int status);
+/* CUDA error of the last call that returned WRS_ECUDA on this thread. */
+int wrs_last_cuda_error(void);
+/* ABI version: increases when a signature or struct layout changes. */
+int wrs_abi_version(void);
+
+/* ---------------------------------------------------------------------- */
+/* Data layout                                                             */
+/* ---------------------------------------------------------------------- */
+
+/* One alias-table row (Sec. 2.2): row b keeps `prob` of its bucket for item
+ * b and gives 1 - prob to item `alias`.  prob is the paper's T^w_b / (W/N). */
+typedef struct wrs_row {
+    float prob;
+    uint32_t alias;
+} wrs_row;
+
+/* Tuning knobs of the build. */
+typedef struct wrs_config {
+    /* Buckets per pack section ("N/s items per section", Sec. 2.2); one CTA
+     * packs one section.  Multiple of 256 in [256, 8192]; default 4096. */
+    uint32_t section_size;
+    /* Split search (Sec. 4.1): WRS_SPLIT_PARY (partial p-ary search,
+     * Algorithm 1; default) or WRS_SPLIT_BINARY (one binary search per
+     * split, the PSA baseline). */
+    uint32_t split_method;
+    uint32_t reserved[6];
+} wrs_config;
+
+enum wrs_split_method { WRS_SPLIT_PARY = 0, WRS_SPLIT_BINARY = 1 };
+
+/* Fill *cfg with the defaults. */
+void wrs_config_default(wrs_config *cfg);
+
+/* Summary of one build, written by the device at the end of the build.
+ * Layout is fixed (ABI); all fields little-endian. */
+typedef struct wrs_build_info {
+    int32_t status;   /* WRS_OK or a data error (EINVAL/ENONFINITE/EZEROSUM/ETIMEOUT) */
+    int32_t scale;    /* fixed-point scale S: q_i = round(w_i * 2^S) */
+    double W;         /* sum of the weights, exact, rounded once to FP64 */
+    double avg;       /* W / N in FP64: the bucket size (Sec. 2.2) */
+    uint64_t nl;      /* number of light items, w_i <= avg */
+    uint64_t nh;      /* number of heavy items, w_i > avg */
+    uint32_t Q[4];    /* bucket size in fixed point (128-bit, low limb first) */
+    float light_max;  /* largest FP32 value <= avg: light iff w_i <= light_max */
+    uint32_t sections;/* number of pack sections s */
+    uint64_t reserved[4];
+} wrs_build_info;
+
+/* ---------------------------------------------------------------------- */
+/* Construction (PSA on the GPU, Sec. 2.2 and Sec. 4)                      */
+/* ---------------------------------------------------------------------- */
+
+/* Bytes of device workspace a build of n items needs. */
+int wrs_build_workspace_bytes(uint64_t n, const wrs_config *cfg,
+                              uint64_t *bytes);
+
+/* Offsets (bytes from the workspace start) of the build's intermediate
+ * arrays, for inspection after a build:
+ *   lh:    n entries {uint32 item, float weight}; light items in index order
+ *          from the front (entry a = l[a]), heavy items in index order from
+ *          the back (entry n-1-b = h[b])  (Sec. 4.2 "weight in l and h").
+ *   ckl:   128-bit D'(32c) for c = 0..floor(nl/32): N*(light deficit prefix)
+ *          in fixed point, one value per 32 light items.
+ *   ckh:   128-bit E'(32c) for c = 0..floor(nh/32): N*(heavy excess prefix).
+ *   splits: s+1 records {uint32 i, uint32 j, uint32 pad[2], uint32 D[4],
+ *          uint32 E[4]} = the Vose state after t*section_size buckets
+ *          (Sec. 2.2 split) with D = D'(i), E = E'(j). */
+typedef struct wrs_layout {
+    uint64_t lh, ckl, ckh, splits;
+    uint64_t sections;       /* s */
+    uint64_t total_bytes;
+} wrs_layout;
+int wrs_build_layout(uint64_t n, const wrs_config *cfg, wrs_layout *out);
+
+/* Full build: d_w (n FP32 weights, device) -> d_rows (n rows, device).
+ * Steps: total weight, classify + stable partition + prefix sums, split
+ * search, sweep-pack (Sec. 2.2, Sec. 4).  No allocation, no host sync.
+ * d_ws: >= wrs_build_workspace_bytes(n) bytes, 256-byte aligned, device.
+ * d_info: device wrs_build_info, written at the end of the build.
+ * cfg may be NULL (defaults).  The weights are not modified. */
+int wrs_build_rows(const float *d_w, uint64_t n, wrs_row *d_rows,
+                   void *d_ws, uint64_t ws_bytes, const wrs_config *cfg,
+                   wrs_build_info *d_info, void *stream);
+
+/* The same build, one step per call (each enqueues its kernels; run them in
+ * this order on one stream with the same workspace).  They exist so each
+ * step can be checked on its own. */
+/* a1: W = sum w_i exactly, avg = W/N, fixed-point scale (Sec. 1, Sec. 2.2). */
+int wrs_step_total(const float *d_w, uint64_t n, void *d_ws, uint64_t ws_bytes,
+                   const wrs_config *cfg, void *stream);
+/* a2+a3: classify light/heavy, stable partition into lh, prefix sums of the
+ * light deficits and heavy excesses (Sec. 2.2, Sec. 4.2). */
+int wrs_step_partition(const float *d_w, uint64_t n, void *d_ws,
+                       uint64_t ws_bytes, const wrs_config *cfg, void *stream);
+/* a4: split search for every section boundary (Sec. 2.2, Sec. 4.1). */
+int wrs_step_split(uint64_t n, void *d_ws, uint64_t ws_bytes,
+                   const wrs_config *cfg, void *stream);
+/* a5: sweep-pack every section into rows (Sec. 2.2, Sec. 4.2). */
+int wrs_step_pack(uint64_t n, wrs_row *d_rows, void *d_ws, uint64_t ws_bytes,
+                  const wrs_config *cfg, void *stream);
+/* Copy the build summary out of the workspace into d_info (device). */
+int wrs_step_info(uint64_t n, void *d_ws, uint64_t ws_bytes,
+                  const wrs_config *cfg, wrs_build_info *d_info, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Sampling (Sec. 2.2 Walker's rule, Sec. 5)                               */
+/* ---------------------------------------------------------------------- */
+
+/* Philox-4x32-10 counter layout (Salmon et al., SC'11): key = (seed_lo,
+ * seed_hi); counter = (c_lo, c_hi, stream_lo, stream_hi).  Call c yields two
+ * samples: 2c uses output words (x0,x1), 2c+1 uses (x2,x3) as u = x_hi<<32 |
+ * x_lo.  With P = u * rows (128-bit): row = P >> 64 (integer part of U*N),
+ * coin = bits 32..63 of P (fraction of U*N); the sample is the row if
+ * coin < ceil(prob_row * 2^32), else alias_row. */
+enum wrs_stream_tag {
+    WRS_TAG_NAIVE = 0,     /* plain sampling: stream_hi of wrs_sample_rows */
+    WRS_TAG_SECTION = 1,   /* sectioned sampling: (section, WRS_TAG_SECTION) */
+    WRS_TAG_COUNTS = 2,    /* sectioned counts tree nodes */
+    WRS_TAG_BATCH = 3      /* batched sampling: (table, WRS_TAG_BATCH) */
+};
+
+/* a6: naive sampling (Sec. 5 "baseline"): samples first .. first+count-1 of
+ * the stream (seed, stream_lo, stream_hi) from n rows; d_out[t] receives
+ * sample first+t as an item index in [0, n).  Deterministic: the same
+ * arguments give the same samples on any launch configuration. */
+int wrs_sample_rows(const wrs_row *d_rows, uint64_t n, uint64_t first,
+                    uint64_t count, uint64_t seed, uint32_t stream_lo,
+                    uint32_t stream_hi, uint32_t *d_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WRS_H */

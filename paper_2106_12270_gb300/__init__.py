@@ -1,1 +1,215 @@
-"""Alias-table construction and sampling on GB300 (placeholder; binding added with the CUDA library)."""
+"""Alias-table construction and sampling on GB300 (sm_103a).
+
+Thin Python binding of the C ABI declared in ``include/wrs.h``: every
+function here only marshals arguments (torch tensors for device memory,
+torch streams) and calls ``libwrs.so``; every step of the computation runs
+in the library's CUDA kernels.  There is no CPU fallback: if the library is
+missing or no GPU is present, calls raise.
+
+Method: "Weighted Random Sampling on GPUs" (Lehmann, Huebschle-Schneider,
+Sanders, arXiv 2106.12270) -- PSA construction (Sec. 2.2, Sec. 4) and
+Walker / sectioned sampling (Sec. 2.2, Sec. 5).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "WrsError", "lib", "config", "build_workspace_bytes", "build_layout", "build_rows",
+    "step_total", "step_partition", "step_split", "step_pack", "step_info", "sample_rows",
+    "parse_info", "INFO_BYTES", "ROW_BYTES", "Builder", "rows_to_numpy",
+]
+
+OK, EINVAL, EZEROSUM, ENONFINITE, ENOMEM, ETIMEOUT, ECUDA, EBUSY, ENOTFOUND = range(9)
+SPLIT_PARY, SPLIT_BINARY = 0, 1
+TAG_NAIVE, TAG_SECTION, TAG_COUNTS, TAG_BATCH = 0, 1, 2, 3
+ROW_BYTES = 8
+
+_lock = threading.Lock()
+_lib = None
+
+
+class WrsError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        msg = lib().wrs_strerror(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{what}: wrs status {status} ({msg})")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("section_size", ctypes.c_uint32), ("split_method", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32 * 6)]
+
+
+class Layout(ctypes.Structure):
+    _fields_ = [("lh", ctypes.c_uint64), ("ckl", ctypes.c_uint64), ("ckh", ctypes.c_uint64),
+                ("splits", ctypes.c_uint64), ("sections", ctypes.c_uint64),
+                ("total_bytes", ctypes.c_uint64)]
+
+
+INFO_DTYPE = np.dtype([("status", "<i4"), ("scale", "<i4"), ("W", "<f8"), ("avg", "<f8"),
+                       ("nl", "<u8"), ("nh", "<u8"), ("Q", "<u4", (4,)),
+                       ("light_max", "<f4"), ("sections", "<u4"), ("reserved", "<u8", (4,))])
+INFO_BYTES = INFO_DTYPE.itemsize
+
+
+def lib():
+    """Load libwrs.so (built by __graft_entry__.build()); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"{_build.LIB} is missing: build the CUDA library first "
+                                   "(python -c 'import __graft_entry__ as g; g.build()')")
+            L = ctypes.CDLL(_build.LIB)
+            P, U64, U32, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+            CP = ctypes.POINTER(Config)
+            sigs = {
+                "wrs_build_workspace_bytes": (I, [U64, CP, ctypes.POINTER(U64)]),
+                "wrs_build_layout": (I, [U64, CP, ctypes.POINTER(Layout)]),
+                "wrs_build_rows": (I, [P, U64, P, P, U64, CP, P, P]),
+                "wrs_step_total": (I, [P, U64, P, U64, CP, P]),
+                "wrs_step_partition": (I, [P, U64, P, U64, CP, P]),
+                "wrs_step_split": (I, [U64, P, U64, CP, P]),
+                "wrs_step_pack": (I, [U64, P, P, U64, CP, P]),
+                "wrs_step_info": (I, [U64, P, U64, CP, P, P]),
+                "wrs_sample_rows": (I, [P, U64, U64, U64, U64, U32, U32, P, P]),
+                "wrs_strerror": (ctypes.c_char_p, [I]),
+                "wrs_last_cuda_error": (I, []),
+                "wrs_abi_version": (I, []),
+                "wrs_config_default": (None, [CP]),
+            }
+            for name, (res, args) in sigs.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def config(section_size: int = 4096, split_method: int = SPLIT_PARY) -> Config:
+    c = Config()
+    lib().wrs_config_default(ctypes.byref(c))
+    c.section_size = section_size
+    c.split_method = split_method
+    return c
+
+
+def _cfg(cfg):
+    return ctypes.byref(cfg) if cfg is not None else None
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise WrsError(rc, what)
+
+
+def build_workspace_bytes(n: int, cfg: Config | None = None) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().wrs_build_workspace_bytes(n, _cfg(cfg), ctypes.byref(out)),
+           "wrs_build_workspace_bytes")
+    return out.value
+
+
+def build_layout(n: int, cfg: Config | None = None) -> dict:
+    out = Layout()
+    _check(lib().wrs_build_layout(n, _cfg(cfg), ctypes.byref(out)), "wrs_build_layout")
+    return {f: getattr(out, f) for f, _ in Layout._fields_}
+
+
+def build_rows(w, rows, ws, info, cfg: Config | None = None, stream=None):
+    """Enqueue a full build (Sec. 2.2, Sec. 4): w (float32 [n], device) ->
+    rows (int64 [n], device, {prob, alias} per row)."""
+    n = w.numel()
+    _check(lib().wrs_build_rows(_ptr(w), n, _ptr(rows), _ptr(ws), ws.numel() * ws.element_size(),
+                                _cfg(cfg), _ptr(info), _stream(stream)), "wrs_build_rows")
+
+
+def step_total(w, ws, cfg=None, stream=None):
+    _check(lib().wrs_step_total(_ptr(w), w.numel(), _ptr(ws), ws.numel() * ws.element_size(),
+                                _cfg(cfg), _stream(stream)), "wrs_step_total")
+
+
+def step_partition(w, ws, cfg=None, stream=None):
+    _check(lib().wrs_step_partition(_ptr(w), w.numel(), _ptr(ws), ws.numel() * ws.element_size(),
+                                    _cfg(cfg), _stream(stream)), "wrs_step_partition")
+
+
+def step_split(n, ws, cfg=None, stream=None):
+    _check(lib().wrs_step_split(n, _ptr(ws), ws.numel() * ws.element_size(), _cfg(cfg),
+                                _stream(stream)), "wrs_step_split")
+
+
+def step_pack(n, rows, ws, cfg=None, stream=None):
+    _check(lib().wrs_step_pack(n, _ptr(rows), _ptr(ws), ws.numel() * ws.element_size(),
+                               _cfg(cfg), _stream(stream)), "wrs_step_pack")
+
+
+def step_info(n, ws, info, cfg=None, stream=None):
+    _check(lib().wrs_step_info(n, _ptr(ws), ws.numel() * ws.element_size(), _cfg(cfg),
+                               _ptr(info), _stream(stream)), "wrs_step_info")
+
+
+def sample_rows(rows, n: int, first: int, count: int, seed: int, out,
+                stream_lo: int = 0, stream_hi: int = TAG_NAIVE, stream=None):
+    """Enqueue naive Walker sampling (Sec. 2.2, Sec. 5): samples
+    first..first+count-1 of stream (seed, stream_lo, stream_hi) into out
+    (int32/uint32 [count], device)."""
+    _check(lib().wrs_sample_rows(_ptr(rows), n, first, count, seed & (2**64 - 1), stream_lo,
+                                 stream_hi, _ptr(out), _stream(stream)), "wrs_sample_rows")
+
+
+def parse_info(info_tensor) -> dict:
+    """Decode a device wrs_build_info (uint8 [INFO_BYTES]) after the stream synced."""
+    raw = info_tensor.detach().cpu().numpy().tobytes()
+    rec = np.frombuffer(raw, INFO_DTYPE, count=1)[0]
+    q = [int(x) for x in rec["Q"]]
+    return dict(status=int(rec["status"]), scale=int(rec["scale"]), W=float(rec["W"]),
+                avg=float(rec["avg"]), nl=int(rec["nl"]), nh=int(rec["nh"]),
+                Q=q[0] | q[1] << 32 | q[2] << 64 | q[3] << 96,
+                light_max=float(rec["light_max"]), sections=int(rec["sections"]))
+
+
+def rows_to_numpy(rows):
+    """Split an int64 row tensor into (prob float32, alias uint32) numpy arrays."""
+    a = rows.detach().cpu().numpy().view(np.uint32).reshape(-1, 2)
+    return a[:, 0].copy().view(np.float32), a[:, 1].copy()
+
+
+class Builder:
+    """Owns a build workspace sized for up to `capacity` items and builds
+    tables into caller-provided row tensors."""
+
+    def __init__(self, capacity: int, cfg: Config | None = None, device="cuda"):
+        import torch
+        self.cfg = cfg if cfg is not None else config()
+        self.capacity = capacity
+        nbytes = build_workspace_bytes(capacity, self.cfg)
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.info = torch.zeros(INFO_BYTES, dtype=torch.uint8, device=device)
+
+    def build(self, w, rows=None, stream=None):
+        import torch
+        n = w.numel()
+        if n > self.capacity:
+            raise ValueError("table larger than the workspace capacity")
+        if rows is None:
+            rows = torch.empty(n, dtype=torch.int64, device=w.device)
+        build_rows(w, rows, self.ws, self.info, self.cfg, stream)
+        return rows

@@ -1,0 +1,185 @@
+// wrs_api.cu - the C ABI (include/wrs.h): argument checks on the host, then
+// kernel launches on the caller's stream.  No torch types, no exceptions.
+#include <string.h>
+
+#include "wrs_internal.cuh"
+
+namespace wrs {
+cudaError_t launch_total(const float *, uint64_t, unsigned char *, const Layout &, cudaStream_t);
+cudaError_t launch_partition(const float *, uint64_t, unsigned char *, const Layout &,
+                             cudaStream_t);
+cudaError_t launch_split(uint64_t, unsigned char *, const Layout &, uint32_t, uint32_t,
+                         cudaStream_t);
+cudaError_t launch_pack(uint64_t, wrs_row *, unsigned char *, const Layout &, uint32_t,
+                        cudaStream_t);
+cudaError_t launch_info(unsigned char *, const Layout &, wrs_build_info *, cudaStream_t);
+cudaError_t launch_sample_naive(const wrs_row *, uint64_t, uint64_t, uint64_t, uint64_t,
+                                uint32_t, uint32_t, uint32_t *, cudaStream_t);
+
+thread_local int g_last_cuda = 0;
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return WRS_OK;
+    g_last_cuda = (int)e;
+    return e == cudaErrorMemoryAllocation ? WRS_ENOMEM : WRS_ECUDA;
+}
+
+constexpr uint64_t kMaxN = 0x7fffffffull;
+
+int resolve_cfg(const wrs_config *in, wrs_config *out) {
+    wrs_config_default(out);
+    if (in) *out = *in;
+    if (out->section_size < 256 || out->section_size > 8192 || out->section_size % 256)
+        return WRS_EINVAL;
+    if (out->split_method != WRS_SPLIT_PARY && out->split_method != WRS_SPLIT_BINARY)
+        return WRS_EINVAL;
+    return WRS_OK;
+}
+
+// Common checks of the step calls; fills the layout.
+static int prep(uint64_t n, const void *ws, uint64_t ws_bytes, const wrs_config *cfg,
+                wrs_config *c, Layout *L) {
+    if (n == 0 || n > kMaxN) return WRS_EINVAL;
+    int rc = resolve_cfg(cfg, c);
+    if (rc) return rc;
+    *L = make_layout(n, c->section_size);
+    if (!ws || ((uintptr_t)ws & 255u) || ws_bytes < L->total) return WRS_EINVAL;
+    return WRS_OK;
+}
+
+}  // namespace wrs
+
+using namespace wrs;
+
+extern "C" {
+
+const char *wrs_strerror(int s) {
+    switch (s) {
+        case WRS_OK: return "ok";
+        case WRS_EINVAL: return "invalid argument or negative weight";
+        case WRS_EZEROSUM: return "all weights are zero";
+        case WRS_ENONFINITE: return "a weight is NaN or infinite";
+        case WRS_ENOMEM: return "out of device memory or over budget";
+        case WRS_ETIMEOUT: return "a bounded device wait gave up";
+        case WRS_ECUDA: return "CUDA runtime error";
+        case WRS_EBUSY: return "busy: no room right now";
+        case WRS_ENOTFOUND: return "unknown ticket";
+        default: return "unknown status";
+    }
+}
+
+int wrs_last_cuda_error(void) { return g_last_cuda; }
+
+int wrs_abi_version(void) { return 1; }
+
+void wrs_config_default(wrs_config *cfg) {
+    if (!cfg) return;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->section_size = 4096;
+    cfg->split_method = WRS_SPLIT_PARY;
+}
+
+int wrs_build_workspace_bytes(uint64_t n, const wrs_config *cfg, uint64_t *bytes) {
+    wrs_config c;
+    if (!bytes || n == 0 || n > kMaxN) return WRS_EINVAL;
+    int rc = resolve_cfg(cfg, &c);
+    if (rc) return rc;
+    *bytes = make_layout(n, c.section_size).total;
+    return WRS_OK;
+}
+
+int wrs_build_layout(uint64_t n, const wrs_config *cfg, wrs_layout *out) {
+    wrs_config c;
+    if (!out || n == 0 || n > kMaxN) return WRS_EINVAL;
+    int rc = resolve_cfg(cfg, &c);
+    if (rc) return rc;
+    Layout L = make_layout(n, c.section_size);
+    out->lh = L.lh;
+    out->ckl = L.ckl;
+    out->ckh = L.ckh;
+    out->splits = L.splits;
+    out->sections = L.sections;
+    out->total_bytes = L.total;
+    return WRS_OK;
+}
+
+int wrs_step_total(const float *d_w, uint64_t n, void *d_ws, uint64_t ws_bytes,
+                   const wrs_config *cfg, void *stream) {
+    wrs_config c;
+    Layout L;
+    int rc = prep(n, d_ws, ws_bytes, cfg, &c, &L);
+    if (rc) return rc;
+    if (!d_w || ((uintptr_t)d_w & 3u)) return WRS_EINVAL;
+    return cuda_status(launch_total(d_w, n, (unsigned char *)d_ws, L, (cudaStream_t)stream));
+}
+
+int wrs_step_partition(const float *d_w, uint64_t n, void *d_ws, uint64_t ws_bytes,
+                       const wrs_config *cfg, void *stream) {
+    wrs_config c;
+    Layout L;
+    int rc = prep(n, d_ws, ws_bytes, cfg, &c, &L);
+    if (rc) return rc;
+    if (!d_w || ((uintptr_t)d_w & 3u)) return WRS_EINVAL;
+    return cuda_status(launch_partition(d_w, n, (unsigned char *)d_ws, L, (cudaStream_t)stream));
+}
+
+int wrs_step_split(uint64_t n, void *d_ws, uint64_t ws_bytes, const wrs_config *cfg,
+                   void *stream) {
+    wrs_config c;
+    Layout L;
+    int rc = prep(n, d_ws, ws_bytes, cfg, &c, &L);
+    if (rc) return rc;
+    return cuda_status(launch_split(n, (unsigned char *)d_ws, L, c.section_size,
+                                    c.split_method, (cudaStream_t)stream));
+}
+
+int wrs_step_pack(uint64_t n, wrs_row *d_rows, void *d_ws, uint64_t ws_bytes,
+                  const wrs_config *cfg, void *stream) {
+    wrs_config c;
+    Layout L;
+    int rc = prep(n, d_ws, ws_bytes, cfg, &c, &L);
+    if (rc) return rc;
+    if (!d_rows || ((uintptr_t)d_rows & 7u)) return WRS_EINVAL;
+    return cuda_status(
+        launch_pack(n, d_rows, (unsigned char *)d_ws, L, c.section_size, (cudaStream_t)stream));
+}
+
+int wrs_step_info(uint64_t n, void *d_ws, uint64_t ws_bytes, const wrs_config *cfg,
+                  wrs_build_info *d_info, void *stream) {
+    wrs_config c;
+    Layout L;
+    int rc = prep(n, d_ws, ws_bytes, cfg, &c, &L);
+    if (rc) return rc;
+    if (!d_info) return WRS_EINVAL;
+    return cuda_status(launch_info((unsigned char *)d_ws, L, d_info, (cudaStream_t)stream));
+}
+
+int wrs_build_rows(const float *d_w, uint64_t n, wrs_row *d_rows, void *d_ws, uint64_t ws_bytes,
+                   const wrs_config *cfg, wrs_build_info *d_info, void *stream) {
+    wrs_config c;
+    Layout L;
+    int rc = prep(n, d_ws, ws_bytes, cfg, &c, &L);
+    if (rc) return rc;
+    if (!d_w || ((uintptr_t)d_w & 3u) || !d_rows || ((uintptr_t)d_rows & 7u) || !d_info)
+        return WRS_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *ws = (unsigned char *)d_ws;
+    cudaError_t e = launch_total(d_w, n, ws, L, st);
+    if (!e) e = launch_partition(d_w, n, ws, L, st);
+    if (!e) e = launch_split(n, ws, L, c.section_size, c.split_method, st);
+    if (!e) e = launch_pack(n, d_rows, ws, L, c.section_size, st);
+    if (!e) e = launch_info(ws, L, d_info, st);
+    return cuda_status(e);
+}
+
+int wrs_sample_rows(const wrs_row *d_rows, uint64_t n, uint64_t first, uint64_t count,
+                    uint64_t seed, uint32_t stream_lo, uint32_t stream_hi, uint32_t *d_out,
+                    void *stream) {
+    if (n == 0 || n > kMaxN || !d_rows || ((uintptr_t)d_rows & 7u)) return WRS_EINVAL;
+    if (count && (!d_out || ((uintptr_t)d_out & 3u))) return WRS_EINVAL;
+    if (first + count < first) return WRS_EINVAL;
+    return cuda_status(launch_sample_naive(d_rows, n, first, count, seed, stream_lo, stream_hi,
+                                           d_out, (cudaStream_t)stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,867 @@
+// wrs_build.cu - alias-table construction on GB300 (sm_103a).
+//
+// The PSA method (Sec. 2.2, Sec. 4 of "Weighted Random Sampling on GPUs")
+// in four kernels, with integer fixed-point prefix sums:
+//
+//   k_sum / k_total      a1: W = sum w_i, exact (per-exponent-band integer
+//                        sums), rounded once to FP64; avg = W/N; the scale S
+//                        of the fixed point q_i = round(w_i 2^S).
+//   k_partition          a2+a3: light iff w_i <= W/N; stable partition into
+//                        one array (lights from the front, heavies from the
+//                        back, Sec. 4.2 "weight in l and h"); single-pass
+//                        decoupled look-back over tiles for the global
+//                        ranks and the q prefix sums; one checkpoint of the
+//                        scaled deficit/excess prefix every 32 items.
+//   k_split              a4: for every section boundary k the Vose state
+//                        (i lights, k-i heavies closed) by a monotone search
+//                        over the checkpoints -- partial p-ary search
+//                        (Algorithm 1) or plain binary search -- followed by
+//                        a warp-cooperative search inside one checkpoint.
+//   k_pack               a5: one CTA per section sweeps the section as a
+//                        merge of the light deficit prefix D' and the heavy
+//                        excess prefix E' (Sec. 2.2 "pack"), staged in shared
+//                        memory (Sec. 4.2), writing rows by item index.
+//
+// Fixed point.  With Q = round(W 2^S) in [2^93, 2^94] a bucket is Q units.
+// For light items d'_a = Q - N q_a >= 0 (its deficit times N) and for heavy
+// items e'_b = N q_b - Q > 0.  D'(i) = sum of the first i light d', E'(j) =
+// sum of the first j heavy e' (both < 2^126).  The sweep closes heavy h[j]
+// (its remaining weight fits in one bucket) iff E'(j+1) <= D'(i), else light
+// l[i]; a heavy row keeps 1 - (D'(i) - E'(j+1)) / Q of its bucket.  All of it
+// is exact integer arithmetic: the splits and every section end agree
+// exactly, and no FP64 unit is used per item.
+#include <stdio.h>
+
+#include "wrs_internal.cuh"
+
+namespace wrs {
+
+Layout make_layout(uint64_t n, uint32_t S) {
+    Layout L;
+    uint64_t off = 0;
+    auto take = [&](uint64_t bytes) {
+        uint64_t o = off;
+        off = align_up(off + (bytes ? bytes : 1), 256);
+        return o;
+    };
+    L.ntiles = (n + kTile - 1) / kTile;
+    L.sections = (n + S - 1) / S;
+    L.params = take(sizeof(BuildParams));
+    L.sum_bins = take((uint64_t)kSumMaxBlocks * kBands * sizeof(u128));
+    L.counter = take(16);
+    L.tflag = take(L.ntiles * 4);
+    L.tagg = take(L.ntiles * sizeof(TileVal));
+    L.tincl = take(L.ntiles * sizeof(TileVal));
+    L.lh = take(n * sizeof(Entry));
+    L.ckl = take((n / 32 + 2) * sizeof(u128));
+    L.ckh = take((n / 32 + 2) * sizeof(u128));
+    L.splits = take((L.sections + 1) * sizeof(SplitRec));
+    L.total = off;
+    return L;
+}
+
+// ===========================================================================
+// a1: exact total weight
+// ===========================================================================
+
+// Each FP32 weight m * 2^(e'-150) (e' = max(biased exponent, 1)) goes into
+// band e'/24 as m << (e' mod 24) < 2^47.  A thread sees at most 2^15 items,
+// so its per-band sum stays below 2^62; blocks reduce to 128-bit sums.
+__global__ void __launch_bounds__(kSumThreads)
+k_sum(const float *__restrict__ w, uint64_t n, u128 *__restrict__ bins_out,
+      BuildParams *__restrict__ P, int aligned) {
+    __shared__ uint64_t bins[kBands][kSumThreads];
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int b = 0; b < kBands; ++b) bins[b][tid] = 0;
+    uint32_t bad = 0;
+    auto add = [&](float x) {
+        uint32_t u = __float_as_uint(x);
+        uint32_t e = (u >> 23) & 0xffu;
+        bad |= (e == 0xffu) ? ERR_NONFINITE : 0u;
+        bad |= ((u >> 31) && (u & 0x7fffffffu)) ? ERR_NEGATIVE : 0u;
+        uint32_t ee = e ? e : 1u;
+        uint32_t m = (e == 0xffu) ? 0u : ((u & 0x7fffffu) | (e ? 0x800000u : 0u));
+        uint32_t band = (ee * 2731u) >> 16;  // ee / 24 for ee < 256
+        uint32_t sh = ee - 24u * band;
+        bins[band][tid] += (uint64_t)m << sh;
+    };
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + tid;
+    uint64_t tail = 0;
+    if (aligned) {
+        const uint64_t n4 = n / 4;
+        const float4 *w4 = reinterpret_cast<const float4 *>(w);
+        for (uint64_t i = g; i < n4; i += T) {
+            float4 v = __ldg(w4 + i);
+            add(v.x); add(v.y); add(v.z); add(v.w);
+        }
+        tail = n4 * 4;
+    }
+    for (uint64_t i = tail + g; i < n; i += T) add(__ldg(w + i));
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int b = warp; b < kBands; b += kSumThreads / 32) {
+        u128 s = 0;
+#pragma unroll
+        for (int k = 0; k < kSumThreads / 32; ++k) s += bins[b][lane + 32 * k];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            uint64_t lo = __shfl_down_sync(0xffffffffu, (uint64_t)s, d);
+            uint64_t hi = __shfl_down_sync(0xffffffffu, (uint64_t)(s >> 64), d);
+            s += ((u128)hi << 64) | lo;
+        }
+        if (lane == 0) bins_out[(uint64_t)blockIdx.x * kBands + b] = s;
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (lane == 0 && bad) atomicOr(&P->status, bad);
+}
+
+// Bits [pos, pos+cnt) of a 384-bit integer (cnt <= 128; bits outside are 0).
+__device__ static u128 big_bits(const uint32_t *big, int pos, int cnt) {
+    u128 r = 0;
+    for (int k = cnt - 1; k >= 0; --k) {
+        int p = pos + k;
+        uint32_t bit = (p >= 0 && p < 384) ? ((big[p >> 5] >> (p & 31)) & 1u) : 0u;
+        r = (r << 1) | bit;
+    }
+    return r;
+}
+
+__device__ static int big_any_below(const uint32_t *big, int pos) {
+    for (int p = 0; p < pos && p < 384; ++p)
+        if ((big[p >> 5] >> (p & 31)) & 1u) return 1;
+    return 0;
+}
+
+// One warp: reduce the block band sums, assemble W exactly (units of
+// 2^-150), round to FP64 (ties to even), derive avg, the light threshold and
+// the fixed-point scale.
+__global__ void k_total(const u128 *__restrict__ bins_in, int nblocks, uint64_t n,
+                        uint32_t sections, BuildParams *__restrict__ P) {
+    __shared__ u128 band[kBands];
+    const int lane = threadIdx.x;
+    if (lane < kBands) {
+        u128 s = 0;
+        for (int b = 0; b < nblocks; ++b) s += bins_in[(uint64_t)b * kBands + lane];
+        band[lane] = s;
+    }
+    __syncwarp();
+    if (lane != 0) return;
+    uint32_t big[12];
+    for (int k = 0; k < 12; ++k) big[k] = 0;
+    for (int b = 0; b < kBands; ++b) {
+        // big += band[b] << 24b
+        u128 v = band[b];
+        int shift = 24 * b;
+        uint64_t carry = 0;
+        for (int k = 0; k < 12; ++k) {
+            int o = 32 * k - shift;  // bit of v that lands at bit 0 of limb k
+            uint32_t part = 0;
+            if (o >= 0 && o < 128) part = (uint32_t)(v >> o);
+            else if (o < 0 && o > -32) part = (uint32_t)(v << (-o));
+            uint64_t s = (uint64_t)big[k] + part + carry;
+            big[k] = (uint32_t)s;
+            carry = s >> 32;
+        }
+    }
+    int top = -1;
+    for (int k = 11; k >= 0 && top < 0; --k)
+        if (big[k]) top = 32 * k + 31 - __clz(big[k]);
+    P->n = n;
+    P->sections = sections;
+    if (top < 0) {
+        P->W = 0.0;
+        P->avg = 0.0;
+        atomicOr(&P->status, ERR_ZEROSUM);
+        return;
+    }
+    // W: 53 bits from the top, round to nearest even.
+    uint64_t mant = (uint64_t)big_bits(big, top - 52, 53);
+    int t = top;
+    if (top >= 53) {
+        int half = (int)big_bits(big, top - 53, 1);
+        int sticky = big_any_below(big, top - 53);
+        if (half && (sticky || (mant & 1u))) {
+            ++mant;
+            if (mant >> 53) { mant >>= 1; ++t; }
+        }
+    }
+    uint64_t bits = ((uint64_t)(t + 873) << 52) | (mant & ((1ull << 52) - 1));
+    double W = __longlong_as_double((long long)bits);
+    double avg = W / (double)n;
+    // Q = round(W_exact * 2^(243 - top)) in [2^93, 2^94]
+    u128 Q = big_bits(big, top - 93, 94);
+    if (top >= 94) Q += big_bits(big, top - 94, 1);
+    P->Q = Q;
+    P->Qn = Q / (u128)n;
+    P->W = W;
+    P->avg = avg;
+    P->scale = 243 - top;
+    P->qshift = 93 - top;
+    P->light_max = __double2float_rd(avg);
+    P->inv_avg = __double2float_rn(1.0 / avg);
+    P->Qf = __ull2float_rn((unsigned long long)(Q >> 62));
+}
+
+// ===========================================================================
+// a2 + a3: classify, stable partition, prefix sums (decoupled look-back)
+// ===========================================================================
+
+__device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
+
+__device__ __forceinline__ TileVal load_tileval(const TileVal *p) {
+    TileVal v;
+    const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(p);
+    ulonglong2 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
+    v.sl = ((u128)a.y << 64) | a.x;
+    v.sh = ((u128)b.y << 64) | b.x;
+    v.nl = (uint32_t)c.x;
+    v.pad[0] = v.pad[1] = v.pad[2] = 0;
+    return v;
+}
+
+__device__ __forceinline__ void store_tileval(TileVal *p, const TileVal &v) {
+    ulonglong2 *q = reinterpret_cast<ulonglong2 *>(p);
+    __stcg(q, make_ulonglong2((uint64_t)v.sl, (uint64_t)(v.sl >> 64)));
+    __stcg(q + 1, make_ulonglong2((uint64_t)v.sh, (uint64_t)(v.sh >> 64)));
+    __stcg(q + 2, make_ulonglong2((uint64_t)v.nl, 0ull));
+}
+
+struct PartShared {
+    union {
+        float wv[kTile + kTile / 32];   // staged weights (padded, conflict-free)
+        Entry e[kTile];                 // staged output entries
+    } buf;
+    TileVal warp_tot[kPartThreads / 32];
+    TileVal prefix;                     // exclusive prefix of this tile
+    uint32_t tile;
+    uint32_t tile_nl;
+    uint32_t bad;                       // the look-back gave up: write nothing
+};
+
+template <bool kAligned>
+__global__ void __launch_bounds__(kPartThreads)
+k_partition(const float *__restrict__ w, uint64_t n, BuildParams *__restrict__ P,
+            uint32_t *__restrict__ counter, uint32_t *__restrict__ tflag,
+            TileVal *__restrict__ tagg, TileVal *__restrict__ tincl,
+            Entry *__restrict__ lh, u128 *__restrict__ ckl, u128 *__restrict__ ckh,
+            uint32_t ntiles) {
+    __shared__ PartShared sm;
+    if (P->status) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) sm.tile = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t tile = sm.tile;
+    const uint64_t base = (uint64_t)tile * kTile;
+    const int qshift = P->qshift;
+    const u128 Q = P->Q, Qn = P->Qn;
+    const float lmax = P->light_max;
+    const u128 N = (u128)n;
+
+    // ---- load: coalesced 16-byte loads per warp, then a padded smem
+    // transpose so each lane owns 16 consecutive items.
+    const int wbase = warp * 512;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        int e = wbase + r * 128 + lane * 4;
+        uint64_t g = base + e;
+        float4 v;
+        if (kAligned && g + 3 < n) {
+            v = __ldcs(reinterpret_cast<const float4 *>(w + g));
+        } else {
+            v.x = g + 0 < n ? w[g + 0] : 0.f;
+            v.y = g + 1 < n ? w[g + 1] : 0.f;
+            v.z = g + 2 < n ? w[g + 2] : 0.f;
+            v.w = g + 3 < n ? w[g + 3] : 0.f;
+        }
+        sm.buf.wv[pad32(e + 0)] = v.x;
+        sm.buf.wv[pad32(e + 1)] = v.y;
+        sm.buf.wv[pad32(e + 2)] = v.z;
+        sm.buf.wv[pad32(e + 3)] = v.w;
+    }
+    __syncwarp();
+    float x[kPartItems];
+    const int e0 = wbase + lane * kPartItems;
+#pragma unroll
+    for (int k = 0; k < kPartItems; ++k) x[k] = sm.buf.wv[pad32(e0 + k)];
+
+    // ---- classify; per-lane light count and q sums
+    uint32_t lmask = 0, vmask = 0;
+    uint32_t cnt = 0;
+    u128 sl = 0, sh = 0;
+#pragma unroll
+    for (int k = 0; k < kPartItems; ++k) {
+        bool valid = base + e0 + k < n;
+        bool light = valid && x[k] <= lmax;
+        vmask |= (uint32_t)valid << k;
+        lmask |= (uint32_t)light << k;
+        if (light) { sl += light_q(x[k], qshift, Qn); ++cnt; }
+        else if (valid) sh += heavy_q(x[k], qshift, Qn);
+    }
+    // warp inclusive scan of (cnt, sl, sh)
+    uint32_t icnt = cnt;
+    u128 isl = sl, ish = sh;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t c2 = __shfl_up_sync(0xffffffffu, icnt, d);
+        u128 a2 = shfl_up_u128(isl, d), b2 = shfl_up_u128(ish, d);
+        if (lane >= d) { icnt += c2; isl += a2; ish += b2; }
+    }
+    if (lane == 31) {
+        sm.warp_tot[warp].nl = icnt;
+        sm.warp_tot[warp].sl = isl;
+        sm.warp_tot[warp].sh = ish;
+    }
+    __syncthreads();
+
+    // ---- tile aggregate and look-back (thread 0)
+    if (tid == 0) {
+        TileVal agg;
+        agg.nl = 0; agg.sl = 0; agg.sh = 0;
+        for (int k = 0; k < kPartThreads / 32; ++k) {
+            agg.nl += sm.warp_tot[k].nl;
+            agg.sl += sm.warp_tot[k].sl;
+            agg.sh += sm.warp_tot[k].sh;
+        }
+        TileVal pre;
+        pre.nl = 0; pre.sl = 0; pre.sh = 0;
+        sm.bad = 0;
+        if (tile == 0) {
+            store_tileval(&tincl[0], agg);
+            __threadfence();
+            st_release(&tflag[0], 2u);
+        } else {
+            store_tileval(&tagg[tile], agg);
+            __threadfence();
+            st_release(&tflag[tile], 1u);
+            int64_t p = (int64_t)tile - 1;
+            uint32_t polls = 0;
+            bool timed_out = false;
+            while (p >= 0) {
+                uint32_t f = ld_acquire(&tflag[p]);
+                if (f == 0u) {
+                    // give up after kSpinLimit polls, or at once when another
+                    // tile already failed (it will never publish)
+                    if (++polls > kSpinLimit || ld_acquire(&P->status) != 0u) {
+                        timed_out = true;
+                        break;
+                    }
+                    __nanosleep(polls < 64 ? 32 : 256);
+                    continue;
+                }
+                TileVal v = load_tileval(f == 2u ? &tincl[p] : &tagg[p]);
+                pre.nl += v.nl; pre.sl += v.sl; pre.sh += v.sh;
+                if (f == 2u) break;
+                --p;
+            }
+            if (timed_out) {
+                atomicOr(&P->status, ERR_TIMEOUT);
+                sm.bad = 1;
+            }
+            TileVal inc;
+            inc.nl = pre.nl + agg.nl; inc.sl = pre.sl + agg.sl; inc.sh = pre.sh + agg.sh;
+            store_tileval(&tincl[tile], inc);
+            __threadfence();
+            st_release(&tflag[tile], 2u);
+        }
+        sm.prefix = pre;
+        sm.tile_nl = agg.nl;
+        if (tile == ntiles - 1 && !sm.bad) {
+            uint64_t nl = (uint64_t)pre.nl + agg.nl, nh = n - nl;
+            u128 Dtot = (u128)nl * Q - N * (pre.sl + agg.sl);
+            u128 Etot = N * (pre.sh + agg.sh) - (u128)nh * Q;
+            P->nl = nl;
+            P->nh = nh;
+            P->Dtot = Dtot;
+            P->Etot = Etot;
+            if ((nl & 31u) == 0) ckl[nl >> 5] = Dtot;
+            if ((nh & 31u) == 0) ckh[nh >> 5] = Etot;
+        }
+    }
+    __syncthreads();   // also: every warp is done reading buf.wv
+    if (sm.bad) return;
+
+    // ---- ranks, staging of entries, checkpoints
+    uint32_t wpre_nl = 0;
+    u128 wpre_sl = 0, wpre_sh = 0;
+    for (int k = 0; k < warp; ++k) {
+        wpre_nl += sm.warp_tot[k].nl;
+        wpre_sl += sm.warp_tot[k].sl;
+        wpre_sh += sm.warp_tot[k].sh;
+    }
+    const TileVal pre = sm.prefix;
+    const uint64_t pre_nh = base - pre.nl;
+    uint32_t lrank = wpre_nl + icnt - cnt;                   // tile-local light rank
+    uint32_t hrank = (uint32_t)(wbase + lane * kPartItems) - lrank;  // tile-local heavy rank
+    u128 rsl = pre.sl + wpre_sl + isl - sl;                  // light q before this item
+    u128 rsh = pre.sh + wpre_sh + ish - sh;                  // heavy q before this item
+#pragma unroll
+    for (int k = 0; k < kPartItems; ++k) {
+        if (!((vmask >> k) & 1u)) continue;
+        uint32_t item = (uint32_t)(base + e0 + k);
+        if ((lmask >> k) & 1u) {
+            uint64_t gr = (uint64_t)pre.nl + lrank;
+            if ((gr & 31u) == 0) ckl[gr >> 5] = (u128)gr * Q - N * rsl;
+            sm.buf.e[lrank] = Entry{item, x[k]};
+            rsl += light_q(x[k], qshift, Qn);
+            ++lrank;
+        } else {
+            uint64_t gr = pre_nh + hrank;
+            if ((gr & 31u) == 0) ckh[gr >> 5] = N * rsh - (u128)gr * Q;
+            sm.buf.e[kTile - 1 - hrank] = Entry{item, x[k]};
+            rsh += heavy_q(x[k], qshift, Qn);
+            ++hrank;
+        }
+    }
+    __syncthreads();
+
+    // ---- coalesced copy-out: lights ascending from pre.nl, heavies
+    // descending from n-1-pre_nh
+    const uint32_t tnl = sm.tile_nl;
+    const uint64_t tvalid = (n - base < (uint64_t)kTile) ? n - base : (uint64_t)kTile;
+    const uint32_t tnh = (uint32_t)tvalid - tnl;
+    uint2 *lh2 = reinterpret_cast<uint2 *>(lh);
+    const uint2 *e2 = reinterpret_cast<const uint2 *>(sm.buf.e);
+    for (uint32_t a = tid; a < tnl; a += kPartThreads) lh2[pre.nl + a] = e2[a];
+    for (uint32_t b = tid; b < tnh; b += kPartThreads)
+        lh2[n - 1 - (pre_nh + b)] = e2[kTile - 1 - b];
+}
+
+// ===========================================================================
+// a4: splits
+// ===========================================================================
+
+struct SplitCtx {
+    const u128 *ckl, *ckh;
+    const Entry *lh;
+    uint64_t n, nl, nh;
+    uint64_t S;
+};
+
+__device__ __forceinline__ u128 ld128(const u128 *p) {
+    ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p));
+    return ((u128)v.y << 64) | v.x;
+}
+
+// P(32c) for bucket count k: monotone in c; false below the valid range of
+// i, true from its upper end on, E'(k-32c) <= D'(32c) inside.
+__device__ __forceinline__ bool pred_c(const SplitCtx &C, uint64_t k, uint64_t c) {
+    uint64_t lo = k > C.nh ? k - C.nh : 0;
+    uint64_t hi = k < C.nl ? k : C.nl;
+    uint64_t i = 32 * c;
+    if (i < lo) return false;
+    if (i >= hi) return true;
+    return ld128(C.ckh + ((k - i) >> 5)) <= ld128(C.ckl + c);
+}
+
+__device__ __forceinline__ void crange(const SplitCtx &C, uint64_t k, uint64_t &clo,
+                                       uint64_t &chi) {
+    uint64_t lo = k > C.nh ? k - C.nh : 0;
+    uint64_t hi = k < C.nl ? k : C.nl;
+    clo = lo / 32;
+    chi = (hi + 31) / 32;
+}
+
+// Given the smallest c with P(32c), finish the split for bucket count k with
+// one warp: the answer is in (32(c-1), 32c]; lane x tests i = 32(c-1)+1+x.
+__device__ void split_fine(const SplitCtx &C, const BuildParams &Pm, uint64_t k, uint64_t c,
+                           SplitRec *out, int lane) {
+    uint64_t lo = k > C.nh ? k - C.nh : 0;
+    uint64_t hi = k < C.nl ? k : C.nl;
+    const u128 N = (u128)C.n;
+    uint64_t ans;
+    u128 Dv, Ev;
+    if (c == 0) {
+        ans = 0;
+        Dv = 0;
+        Ev = ld128(C.ckh + (k >> 5));
+    } else {
+        uint64_t lb = 32 * (c - 1);  // light base
+        uint64_t hb = k - 32 * c;    // heavy base, multiple of 32
+        u128 d = 0, e = 0;
+        if (lb + lane < C.nl) {
+            Entry en = C.lh[lb + lane];
+            d = Pm.Q - N * light_q(en.w, Pm.qshift, Pm.Qn);
+        }
+        if (hb + lane < C.nh) {
+            Entry en = C.lh[C.n - 1 - (hb + lane)];
+            e = N * heavy_q(en.w, Pm.qshift, Pm.Qn) - Pm.Q;
+        }
+        u128 dinc = d, einc = e;
+#pragma unroll
+        for (int s = 1; s < 32; s <<= 1) {
+            u128 a = shfl_up_u128(dinc, s), b = shfl_up_u128(einc, s);
+            if (lane >= s) { dinc += a; einc += b; }
+        }
+        u128 eexc = einc - e;
+        u128 Dbase = ld128(C.ckl + (c - 1));
+        u128 Ebase = ld128(C.ckh + (hb >> 5));
+        u128 Dl = Dbase + dinc;                                   // D'(lb + 1 + lane)
+        u128 Eh = Ebase + shfl_u128(eexc, 31 - lane);             // E'(k - (lb + 1 + lane))
+        uint64_t i = lb + 1 + lane;
+        bool ok = i >= lo && i <= hi && (i == hi || Eh <= Dl);
+        uint32_t bal = __ballot_sync(0xffffffffu, ok);
+        int first = bal ? __ffs(bal) - 1 : 31;
+        ans = lb + 1 + first;
+        Dv = shfl_u128(Dl, first);
+        Ev = shfl_u128(Eh, first);
+    }
+    if (lane == 0) {
+        SplitRec r;
+        r.i = (uint32_t)ans;
+        r.j = (uint32_t)(k - ans);
+        r.pad[0] = r.pad[1] = 0;
+        r.D = Dv;
+        r.E = Ev;
+        *out = r;
+    }
+}
+
+// Interior splits t = 1..s-1, one thread each (k = t*S is a multiple of 32).
+// kPary: Algorithm 1 first narrows the block's shared range of c with
+// kSplitThreads pivots, judging "below every answer" with the block's first
+// split and "at or above every answer" with its last; it repeats while the
+// range shrinks to at most half.  Then each thread binary-searches its own c
+// inside the shared range.  Without kPary each thread searches alone.
+template <bool kPary>
+__global__ void __launch_bounds__(kSplitThreads)
+k_split(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
+        const u128 *__restrict__ ckl, const u128 *__restrict__ ckh,
+        SplitRec *__restrict__ splits, uint64_t n, uint64_t S, uint32_t sections) {
+    __shared__ uint64_t s_c[kSplitThreads];
+    __shared__ unsigned long long s_a, s_b;
+    __shared__ int s_go;
+    if (P->status) return;
+    const BuildParams Pm = *P;
+    SplitCtx C;
+    C.ckl = ckl; C.ckh = ckh; C.lh = lh; C.n = n; C.nl = Pm.nl; C.nh = Pm.nh; C.S = S;
+    const int tid = threadIdx.x;
+    const uint64_t t0 = 1 + (uint64_t)blockIdx.x * kSplitThreads;   // first split of block
+    const uint64_t t = t0 + tid;
+    const uint64_t tlast_blk = min((uint64_t)sections - 1, t0 + kSplitThreads - 1);
+    const bool active = t < sections;
+    const uint64_t k = t * S;
+    uint64_t clo = 0, chi = 0;
+    if (active) crange(C, k, clo, chi);
+
+    uint64_t a = clo, b = chi;   // the answer c* of this split lies in [a, b]
+    if (kPary) {
+        uint64_t kf = t0 * S, kl = tlast_blk * S, dummy;
+        uint64_t A, B;
+        crange(C, kf, A, dummy);
+        crange(C, kl, dummy, B);
+        if (A > B) A = B;
+        for (;;) {
+            uint64_t width = B - A;
+            if (width < kSplitThreads) break;
+            if (tid == 0) { s_a = A; s_b = B; }
+            __syncthreads();
+            uint64_t s = A + (width * (uint64_t)tid) / (kSplitThreads - 1);
+            if (!pred_c(C, kf, s)) atomicMax(&s_a, (unsigned long long)(s + 1));
+            else if (pred_c(C, kl, s)) atomicMin(&s_b, (unsigned long long)s);
+            __syncthreads();
+            uint64_t nA = s_a, nB = s_b;
+            __syncthreads();
+            if (nB < nA) nB = nA;
+            bool shrink = 2 * (nB - nA) <= width;
+            A = nA;
+            B = nB;
+            if (!shrink) break;
+        }
+        if (A > a) a = A;
+        if (B < b) b = B;
+        if (a > b) a = b;
+    }
+    if (active) {
+        while (a < b) {
+            uint64_t m = a + (b - a) / 2;
+            if (pred_c(C, k, m)) b = m;
+            else a = m + 1;
+        }
+    }
+    s_c[tid] = a;
+    __syncthreads();
+    // fine phase: each warp handles its 32 splits one after another
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int q = 0; q < 32; ++q) {
+        int st = warp * 32 + q;
+        uint64_t tt = t0 + st;
+        if (tt >= sections) break;
+        split_fine(C, Pm, tt * S, s_c[st], splits + tt, lane);
+    }
+    (void)s_go;
+}
+
+// Splits 0 and s (the whole table's ends).
+__global__ void k_split_ends(const BuildParams *__restrict__ P, SplitRec *__restrict__ splits,
+                             uint32_t sections) {
+    if (P->status) return;
+    SplitRec r0, rs;
+    r0.i = r0.j = 0; r0.pad[0] = r0.pad[1] = 0; r0.D = 0; r0.E = 0;
+    rs.i = (uint32_t)P->nl; rs.j = (uint32_t)P->nh; rs.pad[0] = rs.pad[1] = 0;
+    rs.D = P->Dtot; rs.E = P->Etot;
+    splits[0] = r0;
+    splits[sections] = rs;
+}
+
+// ===========================================================================
+// a5: pack
+// ===========================================================================
+
+// Shared memory of one pack CTA for a section of up to S buckets:
+//   item[K+1] (uint32), w[K+1 padded] (float), P[K+1] (u128 prefix of the
+// section's d' (lights first) then e' (heavies)).
+__host__ __device__ inline uint32_t pack_smem_bytes(uint32_t S) {
+    uint32_t K1 = S + 1;
+    uint32_t b = 16 * K1;                       // P
+    b += 4 * K1;                                // item
+    b += 4 * (K1 + K1 / 32 + 1);                // w (padded)
+    return (b + 15) & ~15u;
+}
+
+__global__ void __launch_bounds__(kPackThreads)
+k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
+       const SplitRec *__restrict__ splits, uint2 *__restrict__ rows, uint64_t n,
+       uint32_t S) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if (P->status) return;
+    const uint32_t K1 = S + 1;
+    u128 *sP = reinterpret_cast<u128 *>(smem);
+    uint32_t *sItem = reinterpret_cast<uint32_t *>(smem + 16 * K1);
+    float *sW = reinterpret_cast<float *>(smem + 16 * K1 + 4 * K1);
+
+    const int tid = threadIdx.x;
+    const uint32_t t = blockIdx.x;
+    const uint64_t nh = P->nh;
+    const u128 Q = P->Q, Qn = P->Qn, N = (u128)n;
+    const int qshift = P->qshift;
+    const float inv_avg = P->inv_avg, Qf = P->Qf;
+    const SplitRec R0 = splits[t], R1 = splits[t + 1];
+    const uint32_t i0 = R0.i, j0 = R0.j;
+    const uint32_t L = R1.i - R0.i, H = R1.j - R0.j, K = L + H;
+    const uint32_t extra = (R1.j < nh) ? 1u : 0u;
+    const u128 D0 = R0.D, E0 = R0.E;
+    if (R1.i < R0.i || R1.j < R0.j || K > S || R1.i > P->nl || R1.j > nh) {
+        if (tid == 0) atomicOr(const_cast<uint32_t *>(&P->status), ERR_INTERNAL);
+        return;   // inconsistent splits: write nothing
+    }
+
+    // phase 1: coalesced load of the section's lights, heavies and the next
+    // heavy item (the alias of the last rows)
+    for (uint32_t e = tid; e < K + extra; e += kPackThreads) {
+        Entry en = (e < L) ? lh[(uint64_t)i0 + e] : lh[n - 1 - ((uint64_t)j0 + (e - L))];
+        sItem[e] = en.item;
+        sW[pad32(e)] = en.w;
+    }
+    __syncthreads();
+
+    // phase 2: blocked values (d' for lights, e' for heavies) and a block
+    // exclusive scan into sP[0..K]
+    constexpr int kPer = 16;
+    const uint32_t b0 = tid * kPer;
+    u128 v[kPer];
+    u128 run = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        uint32_t e = b0 + k;
+        u128 val = 0;
+        if (e < K) {
+            float wv = sW[pad32(e)];
+            val = (e < L) ? Q - N * light_q(wv, qshift, Qn) : N * heavy_q(wv, qshift, Qn) - Q;
+        }
+        v[k] = val;
+        run += val;
+    }
+    __shared__ u128 s_wsum[kPackThreads / 32];
+    const int warp = tid >> 5, lane = tid & 31;
+    u128 inc = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        u128 o = shfl_up_u128(inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) s_wsum[warp] = inc;
+    __syncthreads();
+    u128 pre = inc - run;
+    for (int k = 0; k < warp; ++k) pre += s_wsum[k];
+    if (tid == 0) sP[0] = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        uint32_t e = b0 + k;
+        pre += v[k];
+        if (e < K) sP[e + 1] = pre;
+    }
+    __syncthreads();
+
+    // phase 3: merge path.  A(x) = D'(i0+x) = D0 + sP[x] (x <= L);
+    // B(y) = E'(j0+y+1) = E0 + sP[L+y+1] - sP[L] (y < H).
+    const u128 PL = sP[L];
+    auto Av = [&](uint32_t x) { return D0 + sP[x]; };
+    auto Bv = [&](uint32_t y) { return E0 + (sP[L + y + 1] - PL); };
+    uint32_t d0 = b0;
+    if (d0 >= K) return;
+    uint32_t lo = d0 > H ? d0 - H : 0, hi = d0 < L ? d0 : L;
+    while (lo < hi) {   // smallest x with (d0-x == 0) || x == L || B(d0-x-1) <= A(x)
+        uint32_t m = (lo + hi) >> 1;
+        bool p = (d0 - m == 0) || (m == L) || (Bv(d0 - m - 1) <= Av(m));
+        if (p) hi = m;
+        else lo = m + 1;
+    }
+    uint32_t x = lo, y = d0 - lo;
+    const uint32_t dend = min(d0 + kPer, K);
+    for (uint32_t d = d0; d < dend; ++d) {
+        bool heavy = (y < H) && (x == L || Bv(y) <= Av(x));
+        uint32_t item;
+        float prob;
+        uint32_t alias;
+        if (heavy) {
+            item = sItem[L + y];
+            if ((uint64_t)j0 + y + 1 < nh) {
+                u128 a = Av(x), bb = Bv(y);
+                if (bb > a) {
+                    prob = 1.0f;      // rounding left more excess than deficit
+                } else {
+                    u128 delta = a - bb;   // < Q
+                    float df = __ull2float_rn((unsigned long long)(delta >> 62));
+                    prob = fminf(fmaxf(1.0f - __fdiv_rn(df, Qf), 0.0f), 1.0f);
+                }
+                alias = sItem[L + y + 1];
+            } else {
+                prob = 1.0f;          // last heavy item keeps its whole bucket
+                alias = item;
+            }
+            ++y;
+        } else {
+            item = sItem[x];
+            if ((uint64_t)j0 + y < nh) {
+                prob = fminf(sW[pad32(x)] * inv_avg, 1.0f);
+                alias = sItem[L + y];
+            } else {
+                prob = 1.0f;          // no heavy item left to fill the bucket
+                alias = item;
+            }
+            ++x;
+        }
+        rows[item] = make_uint2(__float_as_uint(prob), alias);
+    }
+}
+
+// ===========================================================================
+// build summary
+// ===========================================================================
+__global__ void k_info(const BuildParams *__restrict__ P, wrs_build_info *__restrict__ out) {
+    uint32_t st = P->status;
+    wrs_build_info r;
+    r.status = (st & ERR_NONFINITE) ? WRS_ENONFINITE
+             : (st & (ERR_NEGATIVE | ERR_INTERNAL)) ? WRS_EINVAL
+             : (st & ERR_ZEROSUM) ? WRS_EZEROSUM
+             : (st & ERR_TIMEOUT) ? WRS_ETIMEOUT : WRS_OK;
+    r.scale = P->scale;
+    r.W = P->W;
+    r.avg = P->avg;
+    r.nl = P->nl;
+    r.nh = P->nh;
+    for (int k = 0; k < 4; ++k) r.Q[k] = (uint32_t)(P->Q >> (32 * k));
+    r.light_max = P->light_max;
+    r.sections = P->sections;
+    for (int k = 0; k < 4; ++k) r.reserved[k] = 0;
+    *out = r;
+}
+
+// ===========================================================================
+// host launchers
+// ===========================================================================
+
+static int g_num_sms = 0;
+int num_sms() {
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 152;
+    }
+    return g_num_sms;
+}
+
+cudaError_t launch_total(const float *d_w, uint64_t n, unsigned char *ws, const Layout &L,
+                         cudaStream_t st) {
+    BuildParams *P = reinterpret_cast<BuildParams *>(ws + L.params);
+    cudaError_t err = cudaMemsetAsync(P, 0, sizeof(BuildParams), st);
+    if (err) return err;
+    uint64_t want = (n + 4095) / 4096;
+    int blocks = (int)(want < (uint64_t)kSumMaxBlocks ? (want ? want : 1) : kSumMaxBlocks);
+    int aligned = ((uintptr_t)d_w % 16) == 0;
+    k_sum<<<blocks, kSumThreads, 0, st>>>(d_w, n, reinterpret_cast<u128 *>(ws + L.sum_bins), P,
+                                           aligned);
+    k_total<<<1, 32, 0, st>>>(reinterpret_cast<const u128 *>(ws + L.sum_bins), blocks, n,
+                              (uint32_t)L.sections, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_partition(const float *d_w, uint64_t n, unsigned char *ws, const Layout &L,
+                             cudaStream_t st) {
+    BuildParams *P = reinterpret_cast<BuildParams *>(ws + L.params);
+    cudaError_t err = cudaMemsetAsync(ws + L.counter, 0, 16, st);
+    if (!err) err = cudaMemsetAsync(ws + L.tflag, 0, L.ntiles * 4, st);
+    if (err) return err;
+    auto *cnt = reinterpret_cast<uint32_t *>(ws + L.counter);
+    auto *flag = reinterpret_cast<uint32_t *>(ws + L.tflag);
+    auto *agg = reinterpret_cast<TileVal *>(ws + L.tagg);
+    auto *inc = reinterpret_cast<TileVal *>(ws + L.tincl);
+    auto *lh = reinterpret_cast<Entry *>(ws + L.lh);
+    auto *ckl = reinterpret_cast<u128 *>(ws + L.ckl);
+    auto *ckh = reinterpret_cast<u128 *>(ws + L.ckh);
+    if (((uintptr_t)d_w % 16) == 0)
+        k_partition<true><<<(unsigned)L.ntiles, kPartThreads, 0, st>>>(
+            d_w, n, P, cnt, flag, agg, inc, lh, ckl, ckh, (uint32_t)L.ntiles);
+    else
+        k_partition<false><<<(unsigned)L.ntiles, kPartThreads, 0, st>>>(
+            d_w, n, P, cnt, flag, agg, inc, lh, ckl, ckh, (uint32_t)L.ntiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split(uint64_t n, unsigned char *ws, const Layout &L, uint32_t S,
+                         uint32_t method, cudaStream_t st) {
+    const BuildParams *P = reinterpret_cast<const BuildParams *>(ws + L.params);
+    auto *lh = reinterpret_cast<const Entry *>(ws + L.lh);
+    auto *ckl = reinterpret_cast<const u128 *>(ws + L.ckl);
+    auto *ckh = reinterpret_cast<const u128 *>(ws + L.ckh);
+    auto *sp = reinterpret_cast<SplitRec *>(ws + L.splits);
+    uint32_t s = (uint32_t)L.sections;
+    k_split_ends<<<1, 1, 0, st>>>(P, sp, s);
+    if (s > 1) {
+        unsigned blocks = (unsigned)((s - 1 + kSplitThreads - 1) / kSplitThreads);
+        if (method == WRS_SPLIT_BINARY)
+            k_split<false><<<blocks, kSplitThreads, 0, st>>>(P, lh, ckl, ckh, sp, n, S, s);
+        else
+            k_split<true><<<blocks, kSplitThreads, 0, st>>>(P, lh, ckl, ckh, sp, n, S, s);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(uint64_t n, wrs_row *d_rows, unsigned char *ws, const Layout &L,
+                        uint32_t S, cudaStream_t st) {
+    const BuildParams *P = reinterpret_cast<const BuildParams *>(ws + L.params);
+    uint32_t smem = pack_smem_bytes(S);
+    static uint32_t configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e) return e;
+        configured = smem;
+    }
+    k_pack<<<(unsigned)L.sections, kPackThreads, smem, st>>>(
+        P, reinterpret_cast<const Entry *>(ws + L.lh),
+        reinterpret_cast<const SplitRec *>(ws + L.splits), reinterpret_cast<uint2 *>(d_rows), n,
+        S);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_info(unsigned char *ws, const Layout &L, wrs_build_info *d_info,
+                        cudaStream_t st) {
+    k_info<<<1, 1, 0, st>>>(reinterpret_cast<const BuildParams *>(ws + L.params), d_info);
+    return cudaGetLastError();
+}
+
+}  // namespace wrs

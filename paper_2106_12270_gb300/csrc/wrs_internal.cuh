@@ -1,0 +1,196 @@
+// wrs_internal.cuh - device helpers and internal layouts of the GB300
+// alias-table library.  Not part of the public ABI (include/wrs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/wrs.h"
+
+namespace wrs {
+
+typedef unsigned __int128 u128;
+
+// ---------------------------------------------------------------------------
+// Status bits raised by kernels (combined with atomicOr, turned into one
+// wrs_status by the info step; the worst error wins).
+// ---------------------------------------------------------------------------
+enum : uint32_t {
+    ERR_NEGATIVE = 1u,   // a weight with the sign bit set (other than -0)
+    ERR_NONFINITE = 2u,  // NaN or Inf
+    ERR_ZEROSUM = 4u,    // W == 0
+    ERR_TIMEOUT = 8u,    // a bounded wait gave up
+    ERR_INTERNAL = 16u   // an invariant failed (reported as EINVAL)
+};
+
+// Upper bound on polls of one bounded wait (each poll sleeps up to ~256 ns,
+// so a wait gives up after roughly a quarter of a second).
+constexpr uint32_t kSpinLimit = 1u << 20;
+
+// ---------------------------------------------------------------------------
+// Build parameters, computed on the device by the total-weight step and read
+// by every later step.  Lives at the start of the build workspace.
+// ---------------------------------------------------------------------------
+struct __align__(16) BuildParams {
+    u128 Q;            // bucket size W*2^S in fixed point, in [2^93, 2^94]
+    u128 Qn;           // floor(Q / N)
+    u128 Dtot;         // D'(nl): total scaled light deficit
+    u128 Etot;         // E'(nh): total scaled heavy excess
+    double W;          // exact total weight rounded to FP64
+    double avg;        // W / N
+    uint64_t n;
+    uint64_t nl, nh;   // written by the last partition tile
+    uint32_t status;   // ERR_* bits
+    int32_t scale;     // S
+    int32_t qshift;    // q_i = m_i * 2^(e'_i + qshift) (e' = max(biased exp, 1))
+    float light_max;   // largest FP32 <= avg
+    float inv_avg;     // (float)(1 / avg)
+    float Qf;          // (float)(Q >> 62)
+    uint32_t sections; // s
+    uint32_t pad;
+};
+
+// Workspace layout (all offsets 256-byte aligned).
+struct Layout {
+    uint64_t params;     // BuildParams
+    uint64_t sum_bins;   // kSumMaxBlocks * kBands u128
+    uint64_t counter;    // uint32 tile counter (+ pad)
+    uint64_t tflag;      // ntiles uint32 flags
+    uint64_t tagg;       // ntiles TileVal (aggregate)
+    uint64_t tincl;      // ntiles TileVal (inclusive prefix)
+    uint64_t lh;         // n Entry
+    uint64_t ckl;        // (n/32 + 2) u128
+    uint64_t ckh;        // (n/32 + 2) u128
+    uint64_t splits;     // (s+1) SplitRec
+    uint64_t total;
+    uint64_t ntiles;
+    uint64_t sections;
+};
+
+struct __align__(8) Entry {   // one slot of the l/h array
+    uint32_t item;
+    float w;
+};
+
+struct __align__(16) TileVal {  // per-tile partition aggregate / prefix
+    u128 sl;      // sum of light q (adjusted)
+    u128 sh;      // sum of heavy q (adjusted)
+    uint32_t nl;  // light count
+    uint32_t pad[3];
+};
+
+struct __align__(16) SplitRec {  // Vose state after k_t buckets
+    uint32_t i, j;
+    uint32_t pad[2];
+    u128 D;       // D'(i)
+    u128 E;       // E'(j)
+};
+
+// Sizes shared by host and device code.
+constexpr int kBands = 11;            // exponent bands of width 24
+constexpr int kSumThreads = 256;
+constexpr int kSumMaxBlocks = 1216;   // 8 x 152 SMs
+constexpr int kPartThreads = 256;
+constexpr int kPartItems = 16;
+constexpr int kTile = kPartThreads * kPartItems;   // 4096 items per tile
+constexpr int kPackThreads = 256;
+constexpr int kSplitThreads = 256;    // also p of the partial p-ary search
+
+static inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+Layout make_layout(uint64_t n, uint32_t section_size);
+
+// ---------------------------------------------------------------------------
+// Small device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ u128 shfl_up_u128(u128 v, int d) {
+    uint64_t lo = (uint64_t)v, hi = (uint64_t)(v >> 64);
+    lo = __shfl_up_sync(0xffffffffu, lo, d);
+    hi = __shfl_up_sync(0xffffffffu, hi, d);
+    return ((u128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ u128 shfl_u128(u128 v, int src) {
+    uint64_t lo = (uint64_t)v, hi = (uint64_t)(v >> 64);
+    lo = __shfl_sync(0xffffffffu, lo, src);
+    hi = __shfl_sync(0xffffffffu, hi, src);
+    return ((u128)hi << 64) | lo;
+}
+
+// Fixed-point value of an FP32 weight: round(w * 2^S) = m * 2^(e' + qshift),
+// rounded half up when the shift is negative.  The weight must be finite and
+// non-negative (checked by the total-weight step before any caller runs).
+__device__ __forceinline__ u128 fixed_of(float w, int qshift) {
+    uint32_t u = __float_as_uint(w) & 0x7fffffffu;
+    uint32_t e = u >> 23;
+    uint32_t m = (u & 0x7fffffu) | (e ? 0x800000u : 0u);
+    int sh = (int)(e ? e : 1u) + qshift;
+    if (sh >= 0)
+        return (u128)m << sh;           // sh <= 70: m * 2^sh < 2^94
+    int r = -sh;
+    if (r > 24)
+        return 0;
+    return (u128)((m + (1u << (r - 1))) >> r);
+}
+
+// Light weights give d' = Q - N*q >= 0 and heavy weights e' = N*q - Q > 0,
+// after clamping q into the side of Q/N its class requires.
+__device__ __forceinline__ u128 light_q(float w, int qshift, u128 Qn) {
+    u128 q = fixed_of(w, qshift);
+    return q > Qn ? Qn : q;
+}
+__device__ __forceinline__ u128 heavy_q(float w, int qshift, u128 Qn) {
+    u128 q = fixed_of(w, qshift);
+    return q <= Qn ? Qn + 1 : q;
+}
+
+// ---------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplies with fixed odd constants, mixing the high halves with
+// the other two words and the round key; the key advances by fixed Weyl
+// increments after every round.
+// ---------------------------------------------------------------------------
+struct Philox {
+    static constexpr uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
+    static constexpr uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
+};
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(Philox::kMul0, c.x), lo0 = Philox::kMul0 * c.x;
+        uint32_t hi1 = __umulhi(Philox::kMul1, c.z), lo1 = Philox::kMul1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += Philox::kWeyl0;
+        k1 += Philox::kWeyl1;
+    }
+    return c;
+}
+
+// Walker's rule on one 64-bit uniform u for `rows` rows starting at `base`:
+// P = u * rows; row = P >> 64; coin = bits 32..63 of P.
+__device__ __forceinline__ void walker_split(uint64_t u, uint64_t rows,
+                                             uint64_t &row, uint32_t &coin) {
+    row = __umul64hi(u, rows);
+    coin = (uint32_t)((u * rows) >> 32);
+}
+
+// Keep the row iff coin < ceil(prob * 2^32).  prob * 2^32 is exact in FP32
+// (power-of-two scaling) and the conversion rounds up, so this is the ceiling.
+__device__ __forceinline__ uint32_t walker_pick(uint32_t row, uint32_t coin,
+                                                uint2 r) {
+    uint64_t tau = __float2ull_ru(__uint_as_float(r.x) * 4294967296.0f);
+    return (uint64_t)coin < tau ? row : r.y;
+}
+
+// Bounded-spin helpers for device-scope flags.
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+}  // namespace wrs
