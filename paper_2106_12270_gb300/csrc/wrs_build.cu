@@ -656,21 +656,17 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
     }
     __syncthreads();
 
-    // phase 2: blocked values (d' for lights, e' for heavies) and a block
-    // exclusive scan into sP[0..K]
-    constexpr int kPer = 16;
-    const uint32_t b0 = tid * kPer;
-    u128 v[kPer];
+    // phase 2: blocked values (d' for lights, e' for heavies) written to
+    // sP[e+1], then a block exclusive scan in place: sP[e] = sum of values < e
+    const uint32_t per = (S + kPackThreads - 1) / kPackThreads;
+    const uint32_t b0 = tid * per;
     u128 run = 0;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
+    for (uint32_t k = 0; k < per; ++k) {
         uint32_t e = b0 + k;
-        u128 val = 0;
-        if (e < K) {
-            float wv = sW[pad32(e)];
-            val = (e < L) ? Q - N * light_q(wv, qshift, Qn) : N * heavy_q(wv, qshift, Qn) - Q;
-        }
-        v[k] = val;
+        if (e >= K) break;
+        float wv = sW[pad32(e)];
+        u128 val = (e < L) ? Q - N * light_q(wv, qshift, Qn) : N * heavy_q(wv, qshift, Qn) - Q;
+        sP[e + 1] = val;
         run += val;
     }
     __shared__ u128 s_wsum[kPackThreads / 32];
@@ -686,11 +682,11 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
     u128 pre = inc - run;
     for (int k = 0; k < warp; ++k) pre += s_wsum[k];
     if (tid == 0) sP[0] = 0;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
+    for (uint32_t k = 0; k < per; ++k) {
         uint32_t e = b0 + k;
-        pre += v[k];
-        if (e < K) sP[e + 1] = pre;
+        if (e >= K) break;
+        pre += sP[e + 1];
+        sP[e + 1] = pre;
     }
     __syncthreads();
 
@@ -709,7 +705,7 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
         else lo = m + 1;
     }
     uint32_t x = lo, y = d0 - lo;
-    const uint32_t dend = min(d0 + kPer, K);
+    const uint32_t dend = min(d0 + per, K);
     for (uint32_t d = d0; d < dend; ++d) {
         bool heavy = (y < H) && (x == L || Bv(y) <= Av(x));
         uint32_t item;
