@@ -117,37 +117,56 @@ k_sum(const float *__restrict__ w, uint64_t n, u128 *__restrict__ bins_out,
     if (lane == 0 && bad) atomicOr(&P->status, bad);
 }
 
-// Bits [pos, pos+cnt) of a 384-bit integer (cnt <= 128; bits outside are 0).
+// Bits [pos, pos+cnt) of a 384-bit integer held in 12 32-bit limbs, low
+// limb first (cnt <= 128; bits outside the integer read as 0).
 __device__ static u128 big_bits(const uint32_t *big, int pos, int cnt) {
-    u128 r = 0;
-    for (int k = cnt - 1; k >= 0; --k) {
-        int p = pos + k;
-        uint32_t bit = (p >= 0 && p < 384) ? ((big[p >> 5] >> (p & 31)) & 1u) : 0u;
-        r = (r << 1) | bit;
+    int li = pos >= 0 ? pos / 32 : -((31 - pos) / 32);   // floor(pos / 32)
+    int s = pos - 32 * li;                                // 0..31
+    u128 lo = 0;
+    for (int k = 0; k < 4; ++k) {
+        int idx = li + k;
+        uint32_t v = (idx >= 0 && idx < 12) ? big[idx] : 0u;
+        lo |= (u128)v << (32 * k);
     }
+    int idx5 = li + 4;
+    uint32_t v5 = (idx5 >= 0 && idx5 < 12) ? big[idx5] : 0u;
+    u128 r = lo >> s;
+    if (s) r |= (u128)v5 << (128 - s);
+    if (cnt < 128) r &= (((u128)1) << cnt) - 1;
     return r;
 }
 
+// Any set bit strictly below position pos?
 __device__ static int big_any_below(const uint32_t *big, int pos) {
-    for (int p = 0; p < pos && p < 384; ++p)
-        if ((big[p >> 5] >> (p & 31)) & 1u) return 1;
+    for (int k = 0; k < 12 && 32 * k < pos; ++k) {
+        int nb = pos - 32 * k;   // bits of limb k that lie below pos
+        uint32_t m = nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u);
+        if (big[k] & m) return 1;
+    }
     return 0;
 }
 
-// One warp: reduce the block band sums, assemble W exactly (units of
-// 2^-150), round to FP64 (ties to even), derive avg, the light threshold and
-// the fixed-point scale.
-__global__ void k_total(const u128 *__restrict__ bins_in, int nblocks, uint64_t n,
-                        uint32_t sections, BuildParams *__restrict__ P) {
+// kBands warps: warp b reduces band b over the blocks; thread 0 then
+// assembles W exactly (units of 2^-150), rounds it to FP64 (ties to even)
+// and derives avg, the light threshold and the fixed-point scale.
+__global__ void __launch_bounds__(32 * kBands)
+k_total(const u128 *__restrict__ bins_in, int nblocks, uint64_t n, uint32_t sections,
+        BuildParams *__restrict__ P) {
     __shared__ u128 band[kBands];
-    const int lane = threadIdx.x;
-    if (lane < kBands) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    {
         u128 s = 0;
-        for (int b = 0; b < nblocks; ++b) s += bins_in[(uint64_t)b * kBands + lane];
-        band[lane] = s;
+        for (int b = lane; b < nblocks; b += 32) s += bins_in[(uint64_t)b * kBands + warp];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            uint64_t lo = __shfl_down_sync(0xffffffffu, (uint64_t)s, d);
+            uint64_t hi = __shfl_down_sync(0xffffffffu, (uint64_t)(s >> 64), d);
+            s += ((u128)hi << 64) | lo;
+        }
+        if (lane == 0) band[warp] = s;
     }
-    __syncwarp();
-    if (lane != 0) return;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     uint32_t big[12];
     for (int k = 0; k < 12; ++k) big[k] = 0;
     for (int b = 0; b < kBands; ++b) {
@@ -160,9 +179,9 @@ __global__ void k_total(const u128 *__restrict__ bins_in, int nblocks, uint64_t 
             uint32_t part = 0;
             if (o >= 0 && o < 128) part = (uint32_t)(v >> o);
             else if (o < 0 && o > -32) part = (uint32_t)(v << (-o));
-            uint64_t s = (uint64_t)big[k] + part + carry;
-            big[k] = (uint32_t)s;
-            carry = s >> 32;
+            uint64_t sum = (uint64_t)big[k] + part + carry;
+            big[k] = (uint32_t)sum;
+            carry = sum >> 32;
         }
     }
     int top = -1;
@@ -229,19 +248,107 @@ __device__ __forceinline__ void store_tileval(TileVal *p, const TileVal &v) {
 }
 
 struct PartShared {
-    union {
-        float wv[kTile + kTile / 32];   // staged weights (padded, conflict-free)
-        Entry e[kTile];                 // staged output entries
-    } buf;
+    float wv[kTile + kTile / 32];   // staged weights (padded, conflict-free)
+    Entry e[kTile];                 // staged output entries
     TileVal warp_tot[kPartThreads / 32];
-    TileVal prefix;                     // exclusive prefix of this tile
+    TileVal prefix;                 // exclusive prefix of this tile
     uint32_t tile;
     uint32_t tile_nl;
-    uint32_t bad;                       // the look-back gave up: write nothing
+    uint32_t bad;                   // the look-back gave up: write nothing
 };
 
+__device__ __forceinline__ TileVal tv_zero() {
+    TileVal v;
+    v.sl = 0; v.sh = 0; v.nl = 0;
+    v.pad[0] = v.pad[1] = v.pad[2] = 0;
+    return v;
+}
+
+__device__ __forceinline__ void tv_add(TileVal &a, const TileVal &b) {
+    a.sl += b.sl; a.sh += b.sh; a.nl += b.nl;
+}
+
+__device__ __forceinline__ TileVal tv_warp_sum(TileVal v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        TileVal o;
+        uint64_t a0 = __shfl_xor_sync(0xffffffffu, (uint64_t)v.sl, d);
+        uint64_t a1 = __shfl_xor_sync(0xffffffffu, (uint64_t)(v.sl >> 64), d);
+        uint64_t b0 = __shfl_xor_sync(0xffffffffu, (uint64_t)v.sh, d);
+        uint64_t b1 = __shfl_xor_sync(0xffffffffu, (uint64_t)(v.sh >> 64), d);
+        o.nl = __shfl_xor_sync(0xffffffffu, v.nl, d);
+        o.sl = ((u128)a1 << 64) | a0;
+        o.sh = ((u128)b1 << 64) | b0;
+        tv_add(v, o);
+    }
+    return v;
+}
+
+// Decoupled look-back (single-pass prefix over tiles), run by one full warp:
+// publish this tile's aggregate, then examine 32 predecessors at a time
+// (lane k looks at tile-1-k); stop at the nearest one that already published
+// its inclusive prefix and add the aggregates in between.  Every poll is
+// bounded; when a wait gives up (or another tile already failed) the warp
+// reports failure and publishes nothing more.
+__device__ TileVal lookback(uint32_t tile, const TileVal &agg, uint32_t *tflag, TileVal *tagg,
+                            TileVal *tincl, BuildParams *P, bool &failed) {
+    const int lane = threadIdx.x & 31;
+    failed = false;
+    TileVal pre = tv_zero();
+    if (tile == 0) {
+        if (lane == 0) {
+            store_tileval(&tincl[0], agg);
+            __threadfence();
+            st_release(&tflag[0], 2u);
+        }
+        return pre;
+    }
+    if (lane == 0) {
+        store_tileval(&tagg[tile], agg);
+        __threadfence();
+        st_release(&tflag[tile], 1u);
+    }
+    int64_t top = (int64_t)tile - 1;   // predecessor examined by lane 0
+    for (;;) {
+        const int64_t p = top - lane;
+        uint32_t f = 0;
+        bool gave_up = false;
+        if (p >= 0) {
+            uint32_t polls = 0;
+            for (;;) {
+                f = ld_acquire(&tflag[p]);
+                if (f != 0u) break;
+                if (++polls > kSpinLimit || ld_acquire(&P->status) != 0u) {
+                    gave_up = true;
+                    break;
+                }
+                __nanosleep(polls < 64 ? 32 : 256);
+            }
+        }
+        if (__any_sync(0xffffffffu, gave_up)) {
+            failed = true;
+            return pre;
+        }
+        const uint32_t incl = __ballot_sync(0xffffffffu, p >= 0 && f == 2u);
+        const int stop = incl ? __ffs(incl) - 1 : 32;   // nearest inclusive prefix
+        TileVal v = tv_zero();
+        if (p >= 0 && lane <= stop) v = load_tileval(f == 2u ? &tincl[p] : &tagg[p]);
+        tv_add(pre, tv_warp_sum(v));
+        if (incl) break;
+        top -= 32;
+    }
+    if (lane == 0) {
+        TileVal inc = pre;
+        tv_add(inc, agg);
+        store_tileval(&tincl[tile], inc);
+        __threadfence();
+        st_release(&tflag[tile], 2u);
+    }
+    return pre;
+}
+
 template <bool kAligned>
-__global__ void __launch_bounds__(kPartThreads)
+__global__ void __launch_bounds__(kPartThreads, 3)
 k_partition(const float *__restrict__ w, uint64_t n, BuildParams *__restrict__ P,
             uint32_t *__restrict__ counter, uint32_t *__restrict__ tflag,
             TileVal *__restrict__ tagg, TileVal *__restrict__ tincl,
@@ -255,9 +362,8 @@ k_partition(const float *__restrict__ w, uint64_t n, BuildParams *__restrict__ P
     const uint32_t tile = sm.tile;
     const uint64_t base = (uint64_t)tile * kTile;
     const int qshift = P->qshift;
-    const u128 Q = P->Q, Qn = P->Qn;
+    const u128 Qn = P->Qn;
     const float lmax = P->light_max;
-    const u128 N = (u128)n;
 
     // ---- load: coalesced 16-byte loads per warp, then a padded smem
     // transpose so each lane owns 16 consecutive items.
@@ -275,29 +381,27 @@ k_partition(const float *__restrict__ w, uint64_t n, BuildParams *__restrict__ P
             v.z = g + 2 < n ? w[g + 2] : 0.f;
             v.w = g + 3 < n ? w[g + 3] : 0.f;
         }
-        sm.buf.wv[pad32(e + 0)] = v.x;
-        sm.buf.wv[pad32(e + 1)] = v.y;
-        sm.buf.wv[pad32(e + 2)] = v.z;
-        sm.buf.wv[pad32(e + 3)] = v.w;
+        sm.wv[pad32(e + 0)] = v.x;
+        sm.wv[pad32(e + 1)] = v.y;
+        sm.wv[pad32(e + 2)] = v.z;
+        sm.wv[pad32(e + 3)] = v.w;
     }
     __syncwarp();
-    float x[kPartItems];
     const int e0 = wbase + lane * kPartItems;
-#pragma unroll
-    for (int k = 0; k < kPartItems; ++k) x[k] = sm.buf.wv[pad32(e0 + k)];
+    const uint64_t lim = n - base;   // valid items of this tile start below lim
 
     // ---- classify; per-lane light count and q sums
-    uint32_t lmask = 0, vmask = 0;
+    uint32_t lmask = 0;
     uint32_t cnt = 0;
     u128 sl = 0, sh = 0;
 #pragma unroll
     for (int k = 0; k < kPartItems; ++k) {
-        bool valid = base + e0 + k < n;
-        bool light = valid && x[k] <= lmax;
-        vmask |= (uint32_t)valid << k;
+        float x = sm.wv[pad32(e0 + k)];
+        bool valid = (uint64_t)(e0 + k) < lim;
+        bool light = valid && x <= lmax;
         lmask |= (uint32_t)light << k;
-        if (light) { sl += light_q(x[k], qshift, Qn); ++cnt; }
-        else if (valid) sh += heavy_q(x[k], qshift, Qn);
+        if (light) { sl += light_q(x, qshift, Qn); ++cnt; }
+        else if (valid) sh += heavy_q(x, qshift, Qn);
     }
     // warp inclusive scan of (cnt, sl, sh)
     uint32_t icnt = cnt;
@@ -313,117 +417,78 @@ k_partition(const float *__restrict__ w, uint64_t n, BuildParams *__restrict__ P
         sm.warp_tot[warp].sl = isl;
         sm.warp_tot[warp].sh = ish;
     }
+    // lane-exclusive prefixes within the warp
+    const uint32_t xcnt = icnt - cnt;
+    const u128 xsl = isl - sl, xsh = ish - sh;
     __syncthreads();
 
-    // ---- tile aggregate and look-back (thread 0)
-    if (tid == 0) {
-        TileVal agg;
-        agg.nl = 0; agg.sl = 0; agg.sh = 0;
-        for (int k = 0; k < kPartThreads / 32; ++k) {
-            agg.nl += sm.warp_tot[k].nl;
-            agg.sl += sm.warp_tot[k].sl;
-            agg.sh += sm.warp_tot[k].sh;
-        }
-        TileVal pre;
-        pre.nl = 0; pre.sl = 0; pre.sh = 0;
-        sm.bad = 0;
-        if (tile == 0) {
-            store_tileval(&tincl[0], agg);
-            __threadfence();
-            st_release(&tflag[0], 2u);
-        } else {
-            store_tileval(&tagg[tile], agg);
-            __threadfence();
-            st_release(&tflag[tile], 1u);
-            int64_t p = (int64_t)tile - 1;
-            uint32_t polls = 0;
-            bool timed_out = false;
-            while (p >= 0) {
-                uint32_t f = ld_acquire(&tflag[p]);
-                if (f == 0u) {
-                    // give up after kSpinLimit polls, or at once when another
-                    // tile already failed (it will never publish)
-                    if (++polls > kSpinLimit || ld_acquire(&P->status) != 0u) {
-                        timed_out = true;
-                        break;
-                    }
-                    __nanosleep(polls < 64 ? 32 : 256);
-                    continue;
-                }
-                TileVal v = load_tileval(f == 2u ? &tincl[p] : &tagg[p]);
-                pre.nl += v.nl; pre.sl += v.sl; pre.sh += v.sh;
-                if (f == 2u) break;
-                --p;
+    // ---- tile aggregate and look-back (warp 0)
+    if (warp == 0) {
+        TileVal agg = tv_zero();
+        for (int k = 0; k < kPartThreads / 32; ++k) tv_add(agg, sm.warp_tot[k]);
+        bool failed;
+        TileVal pre = lookback(tile, agg, tflag, tagg, tincl, P, failed);
+        if (lane == 0) {
+            sm.bad = failed;
+            sm.prefix = pre;
+            sm.tile_nl = agg.nl;
+            if (failed) atomicOr(&P->status, ERR_TIMEOUT);
+            if (!failed && tile == ntiles - 1) {
+                const u128 Q = P->Q, N = (u128)n;
+                uint64_t nl = (uint64_t)pre.nl + agg.nl, nh = n - nl;
+                u128 Dtot = (u128)nl * Q - N * (pre.sl + agg.sl);
+                u128 Etot = N * (pre.sh + agg.sh) - (u128)nh * Q;
+                P->nl = nl;
+                P->nh = nh;
+                P->Dtot = Dtot;
+                P->Etot = Etot;
+                if ((nl & 31u) == 0) ckl[nl >> 5] = Dtot;
+                if ((nh & 31u) == 0) ckh[nh >> 5] = Etot;
             }
-            if (timed_out) {
-                atomicOr(&P->status, ERR_TIMEOUT);
-                sm.bad = 1;
-            }
-            TileVal inc;
-            inc.nl = pre.nl + agg.nl; inc.sl = pre.sl + agg.sl; inc.sh = pre.sh + agg.sh;
-            store_tileval(&tincl[tile], inc);
-            __threadfence();
-            st_release(&tflag[tile], 2u);
-        }
-        sm.prefix = pre;
-        sm.tile_nl = agg.nl;
-        if (tile == ntiles - 1 && !sm.bad) {
-            uint64_t nl = (uint64_t)pre.nl + agg.nl, nh = n - nl;
-            u128 Dtot = (u128)nl * Q - N * (pre.sl + agg.sl);
-            u128 Etot = N * (pre.sh + agg.sh) - (u128)nh * Q;
-            P->nl = nl;
-            P->nh = nh;
-            P->Dtot = Dtot;
-            P->Etot = Etot;
-            if ((nl & 31u) == 0) ckl[nl >> 5] = Dtot;
-            if ((nh & 31u) == 0) ckh[nh >> 5] = Etot;
         }
     }
-    __syncthreads();   // also: every warp is done reading buf.wv
+    __syncthreads();
     if (sm.bad) return;
 
     // ---- ranks, staging of entries, checkpoints
-    uint32_t wpre_nl = 0;
-    u128 wpre_sl = 0, wpre_sh = 0;
-    for (int k = 0; k < warp; ++k) {
-        wpre_nl += sm.warp_tot[k].nl;
-        wpre_sl += sm.warp_tot[k].sl;
-        wpre_sh += sm.warp_tot[k].sh;
-    }
-    const TileVal pre = sm.prefix;
-    const uint64_t pre_nh = base - pre.nl;
-    uint32_t lrank = wpre_nl + icnt - cnt;                   // tile-local light rank
-    uint32_t hrank = (uint32_t)(wbase + lane * kPartItems) - lrank;  // tile-local heavy rank
-    u128 rsl = pre.sl + wpre_sl + isl - sl;                  // light q before this item
-    u128 rsh = pre.sh + wpre_sh + ish - sh;                  // heavy q before this item
+    TileVal wpre = sm.prefix;
+    for (int k = 0; k < warp; ++k) tv_add(wpre, sm.warp_tot[k]);
+    const uint32_t tpre_nl = sm.prefix.nl;
+    const uint64_t pre_nh = base - tpre_nl;
+    uint32_t lrank = wpre.nl - tpre_nl + xcnt;                      // tile-local light rank
+    uint32_t hrank = (uint32_t)e0 - lrank;                          // tile-local heavy rank
+    u128 rsl = wpre.sl + xsl;                                       // light q before this item
+    u128 rsh = wpre.sh + xsh;                                       // heavy q before this item
+    const u128 Q = P->Q, N = (u128)n;
 #pragma unroll
     for (int k = 0; k < kPartItems; ++k) {
-        if (!((vmask >> k) & 1u)) continue;
+        if ((uint64_t)(e0 + k) >= lim) break;
+        float x = sm.wv[pad32(e0 + k)];
         uint32_t item = (uint32_t)(base + e0 + k);
         if ((lmask >> k) & 1u) {
-            uint64_t gr = (uint64_t)pre.nl + lrank;
+            uint64_t gr = (uint64_t)tpre_nl + lrank;
             if ((gr & 31u) == 0) ckl[gr >> 5] = (u128)gr * Q - N * rsl;
-            sm.buf.e[lrank] = Entry{item, x[k]};
-            rsl += light_q(x[k], qshift, Qn);
+            sm.e[lrank] = Entry{item, x};
+            rsl += light_q(x, qshift, Qn);
             ++lrank;
         } else {
             uint64_t gr = pre_nh + hrank;
             if ((gr & 31u) == 0) ckh[gr >> 5] = N * rsh - (u128)gr * Q;
-            sm.buf.e[kTile - 1 - hrank] = Entry{item, x[k]};
-            rsh += heavy_q(x[k], qshift, Qn);
+            sm.e[kTile - 1 - hrank] = Entry{item, x};
+            rsh += heavy_q(x, qshift, Qn);
             ++hrank;
         }
     }
     __syncthreads();
 
-    // ---- coalesced copy-out: lights ascending from pre.nl, heavies
-    // descending from n-1-pre_nh
+    // ---- coalesced copy-out: lights ascending from the tile's light offset,
+    // heavies descending from n-1-(heavies before the tile)
     const uint32_t tnl = sm.tile_nl;
-    const uint64_t tvalid = (n - base < (uint64_t)kTile) ? n - base : (uint64_t)kTile;
+    const uint64_t tvalid = lim < (uint64_t)kTile ? lim : (uint64_t)kTile;
     const uint32_t tnh = (uint32_t)tvalid - tnl;
     uint2 *lh2 = reinterpret_cast<uint2 *>(lh);
-    const uint2 *e2 = reinterpret_cast<const uint2 *>(sm.buf.e);
-    for (uint32_t a = tid; a < tnl; a += kPartThreads) lh2[pre.nl + a] = e2[a];
+    const uint2 *e2 = reinterpret_cast<const uint2 *>(sm.e);
+    for (uint32_t a = tid; a < tnl; a += kPartThreads) lh2[tpre_nl + a] = e2[a];
     for (uint32_t b = tid; b < tnh; b += kPartThreads)
         lh2[n - 1 - (pre_nh + b)] = e2[kTile - 1 - b];
 }
@@ -610,15 +675,19 @@ __global__ void k_split_ends(const BuildParams *__restrict__ P, SplitRec *__rest
 // ===========================================================================
 
 // Shared memory of one pack CTA for a section of up to S buckets:
-//   item[K+1] (uint32), w[K+1 padded] (float), P[K+1] (u128 prefix of the
-// section's d' (lights first) then e' (heavies)).
+//   P[K+1] (u128 prefix of the section's d' (lights first) then e'
+//   (heavies), one pad slot every 8 entries against bank conflicts),
+//   item[K+1] (uint32), w[K+1 padded] (float).
+__host__ __device__ inline uint32_t pack_p_slots(uint32_t S) { return S + 1 + (S + 1) / 8 + 1; }
 __host__ __device__ inline uint32_t pack_smem_bytes(uint32_t S) {
     uint32_t K1 = S + 1;
-    uint32_t b = 16 * K1;                       // P
+    uint32_t b = 16 * pack_p_slots(S);          // P
     b += 4 * K1;                                // item
     b += 4 * (K1 + K1 / 32 + 1);                // w (padded)
     return (b + 15) & ~15u;
 }
+
+__device__ __forceinline__ uint32_t pp8(uint32_t e) { return e + (e >> 3); }
 
 __global__ void __launch_bounds__(kPackThreads)
 k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
@@ -628,8 +697,8 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
     if (P->status) return;
     const uint32_t K1 = S + 1;
     u128 *sP = reinterpret_cast<u128 *>(smem);
-    uint32_t *sItem = reinterpret_cast<uint32_t *>(smem + 16 * K1);
-    float *sW = reinterpret_cast<float *>(smem + 16 * K1 + 4 * K1);
+    uint32_t *sItem = reinterpret_cast<uint32_t *>(smem + 16 * pack_p_slots(S));
+    float *sW = reinterpret_cast<float *>(smem + 16 * pack_p_slots(S) + 4 * K1);
 
     const int tid = threadIdx.x;
     const uint32_t t = blockIdx.x;
@@ -657,7 +726,7 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
     __syncthreads();
 
     // phase 2: blocked values (d' for lights, e' for heavies) written to
-    // sP[e+1], then a block exclusive scan in place: sP[e] = sum of values < e
+    // P[e+1], then a block exclusive scan in place: P[e] = sum of values < e
     const uint32_t per = (S + kPackThreads - 1) / kPackThreads;
     const uint32_t b0 = tid * per;
     u128 run = 0;
@@ -666,7 +735,7 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
         if (e >= K) break;
         float wv = sW[pad32(e)];
         u128 val = (e < L) ? Q - N * light_q(wv, qshift, Qn) : N * heavy_q(wv, qshift, Qn) - Q;
-        sP[e + 1] = val;
+        sP[pp8(e + 1)] = val;
         run += val;
     }
     __shared__ u128 s_wsum[kPackThreads / 32];
@@ -685,17 +754,17 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
     for (uint32_t k = 0; k < per; ++k) {
         uint32_t e = b0 + k;
         if (e >= K) break;
-        pre += sP[e + 1];
-        sP[e + 1] = pre;
+        pre += sP[pp8(e + 1)];
+        sP[pp8(e + 1)] = pre;
     }
     __syncthreads();
 
-    // phase 3: merge path.  A(x) = D'(i0+x) = D0 + sP[x] (x <= L);
-    // B(y) = E'(j0+y+1) = E0 + sP[L+y+1] - sP[L] (y < H).
-    const u128 PL = sP[L];
-    auto Av = [&](uint32_t x) { return D0 + sP[x]; };
-    auto Bv = [&](uint32_t y) { return E0 + (sP[L + y + 1] - PL); };
-    uint32_t d0 = b0;
+    // phase 3: merge path.  A(x) = D'(i0+x) = D0 + P[x] (x <= L);
+    // B(y) = E'(j0+y+1) = E0 + P[L+y+1] - P[L] (y < H).
+    const u128 PL = sP[pp8(L)];
+    auto Av = [&](uint32_t x) { return D0 + sP[pp8(x)]; };
+    auto Bv = [&](uint32_t y) { return E0 + (sP[pp8(L + y + 1)] - PL); };
+    const uint32_t d0 = b0;
     if (d0 >= K) return;
     uint32_t lo = d0 > H ? d0 - H : 0, hi = d0 < L ? d0 : L;
     while (lo < hi) {   // smallest x with (d0-x == 0) || x == L || B(d0-x-1) <= A(x)
@@ -705,20 +774,20 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
         else lo = m + 1;
     }
     uint32_t x = lo, y = d0 - lo;
+    u128 a = Av(x);                 // D'(i0 + x)
+    u128 b = y < H ? Bv(y) : 0;     // E'(j0 + y + 1)
     const uint32_t dend = min(d0 + per, K);
     for (uint32_t d = d0; d < dend; ++d) {
-        bool heavy = (y < H) && (x == L || Bv(y) <= Av(x));
-        uint32_t item;
+        bool heavy = (y < H) && (x == L || b <= a);
+        uint32_t item, alias;
         float prob;
-        uint32_t alias;
         if (heavy) {
             item = sItem[L + y];
             if ((uint64_t)j0 + y + 1 < nh) {
-                u128 a = Av(x), bb = Bv(y);
-                if (bb > a) {
+                if (b > a) {
                     prob = 1.0f;      // rounding left more excess than deficit
                 } else {
-                    u128 delta = a - bb;   // < Q
+                    u128 delta = a - b;   // < Q
                     float df = __ull2float_rn((unsigned long long)(delta >> 62));
                     prob = fminf(fmaxf(1.0f - __fdiv_rn(df, Qf), 0.0f), 1.0f);
                 }
@@ -728,6 +797,7 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
                 alias = item;
             }
             ++y;
+            if (y < H) b = Bv(y);
         } else {
             item = sItem[x];
             if ((uint64_t)j0 + y < nh) {
@@ -738,6 +808,7 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
                 alias = item;
             }
             ++x;
+            a = Av(x);
         }
         rows[item] = make_uint2(__float_as_uint(prob), alias);
     }
@@ -790,7 +861,7 @@ cudaError_t launch_total(const float *d_w, uint64_t n, unsigned char *ws, const 
     int aligned = ((uintptr_t)d_w % 16) == 0;
     k_sum<<<blocks, kSumThreads, 0, st>>>(d_w, n, reinterpret_cast<u128 *>(ws + L.sum_bins), P,
                                            aligned);
-    k_total<<<1, 32, 0, st>>>(reinterpret_cast<const u128 *>(ws + L.sum_bins), blocks, n,
+    k_total<<<1, 32 * kBands, 0, st>>>(reinterpret_cast<const u128 *>(ws + L.sum_bins), blocks, n,
                               (uint32_t)L.sections, P);
     return cudaGetLastError();
 }

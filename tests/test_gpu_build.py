@@ -220,3 +220,33 @@ def test_invalid_arguments_rejected_on_host():
     assert e.value.status == wrs.EINVAL
     with pytest.raises(wrs.WrsError):
         wrs.build_workspace_bytes(10, wrs.config(300))  # not a multiple of 256
+
+
+def test_total_weight_rounding_golden():
+    """The device's exact sum rounds like IEEE binary64 ties-to-even: the
+    hand-worked cases of tests/golden/exact_sum_rounding.txt."""
+    import struct
+    from golden_io import read
+    for key, spec in read("exact_sum_rounding.txt").items():
+        lhs, rhs = spec.split("->")
+        w = np.array([struct.unpack("<f", struct.pack("<I", int(h, 16)))[0]
+                      for h in lhs.split()], np.float32)
+        want = struct.unpack("<d", struct.pack("<Q", int(rhs.strip(), 16)))[0]
+        b = Built(w)
+        if want == 0.0:
+            assert b.info["status"] == wrs.EZEROSUM, key
+        else:
+            assert struct.pack("<d", b.info["W"]) == struct.pack("<d", want), key
+
+
+def test_total_weight_wide_range_random():
+    rng = np.random.default_rng(21)
+    for trial in range(20):
+        n = int(rng.integers(1, 5000))
+        e = rng.integers(-149, 127, n)
+        w = np.ldexp(rng.random(n) + 0.5, e).astype(np.float32)
+        w[~np.isfinite(w)] = 3.0e38
+        b = Built(w)
+        assert b.info["W"] == oracle.exact_sum(w), trial
+        l, h = oracle.classify(w, b.info["W"] / n)
+        assert (b.info["nl"], b.info["nh"]) == (len(l), len(h))
