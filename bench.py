@@ -36,7 +36,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 BUILD_BYTES_PER_ITEM = 32      # read w twice, write + read lh, write rows
 SAMPLE_BYTES_PER_DRAW = 36     # one 32-byte row sector + a 4-byte output
-KERNELS_PER_BUILD = 7          # sum, total, partition, split ends, split, pack, info
+KERNELS_PER_BUILD = 9          # sum, total, count, scatter, segscan, split ends, split, pack, info
 KERNELS_PER_SAMPLE = 1
 
 
@@ -286,15 +286,34 @@ def run_gpu(args):
                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n,
                "ms_per_step": e2e_ms}
 
+    # random-gather probe: the naive sampler's access pattern alone (same
+    # table size, same number of draws), best of the three load paths
+    probe = {}
+    for flavor in (0, 1, 2):
+        wrs.diag_random_gather(rows, n, count, 7, flavor, out)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        wrs.diag_random_gather(rows, n, count, 7, flavor, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        probe[flavor] = a.elapsed_time(b)
+    probe_ms = min(probe.values())
+
     hbm, peak_kind = peaks()
     build_gbs = BUILD_BYTES_PER_ITEM * n / (build_ms / 1e3) / 1e9
     sample_gbs = SAMPLE_BYTES_PER_DRAW * count / (sample_ms / 1e3) / 1e9
     build_roof = {"bound": "hbm", "achieved": build_gbs, "peak": hbm, "unit": "GB/s",
-                  "frac": build_gbs / hbm, "traffic": None, "kernel": "build (7 kernels)",
+                  "frac": build_gbs / hbm, "traffic": None, "kernel": "build (9 kernels)",
                   "peak_kind": peak_kind}
+    probe_gbs = SAMPLE_BYTES_PER_DRAW * count / (probe_ms / 1e3) / 1e9
     sample_roof = {"bound": "hbm", "achieved": sample_gbs, "peak": hbm, "unit": "GB/s",
                    "frac": sample_gbs / hbm, "traffic": None, "kernel": "k_sample_naive",
-                   "peak_kind": peak_kind}
+                   "peak_kind": peak_kind,
+                   "random_gather_probe": {"achieved": probe_gbs, "unit": "GB/s",
+                                           "frac_of_probe": sample_gbs / probe_gbs,
+                                           "ms": {str(k): v for k, v in probe.items()}}}
     dominant = sample_roof if sample_ms >= build_ms else build_roof
 
     cpu = None

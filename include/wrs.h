@@ -113,17 +113,26 @@ int wrs_build_workspace_bytes(uint64_t n, const wrs_config *cfg,
 
 /* Offsets (bytes from the workspace start) of the build's intermediate
  * arrays, for inspection after a build:
- *   lh:    n entries {uint32 item, float weight}; light items in index order
- *          from the front (entry a = l[a]), heavy items in index order from
- *          the back (entry n-1-b = h[b])  (Sec. 4.2 "weight in l and h").
- *   ckl:   128-bit D'(32c) for c = 0..floor(nl/32): N*(light deficit prefix)
- *          in fixed point, one value per 32 light items.
- *   ckh:   128-bit E'(32c) for c = 0..floor(nh/32): N*(heavy excess prefix).
+ *   lh:     n entries {uint32 item, float weight}; light items in index order
+ *           from the front (entry a = l[a]), heavy items in index order from
+ *           the back (entry n-1-b = h[b])  (Sec. 4.2 "weight in l and h").
+ *   ckl:    checkpoints of the light prefix sums, one per 32 entries: record c
+ *           (16 bytes) = {uint32 seg, uint32 s[3]} where s is the 96-bit sum of
+ *           the fixed-point weights q of l[0..32c) that lie in partition
+ *           segment `seg`; the sum over the earlier segments is seg_pre[seg].
+ *   ckh:    the same for the heavy list h.
+ *   seg_pre: segment prefixes, 48 bytes each: {uint32 sl[4], uint32 sh[4],
+ *           uint64 nl, uint64 pad}: 128-bit q sums of the light and heavy
+ *           items before the segment and its number of light items before it.
  *   splits: s+1 records {uint32 i, uint32 j, uint32 pad[2], uint32 D[4],
- *          uint32 E[4]} = the Vose state after t*section_size buckets
- *          (Sec. 2.2 split) with D = D'(i), E = E'(j). */
+ *           uint32 E[4]}: the Vose state after t*section_size buckets
+ *           (Sec. 2.2 split).
+ * With Q (wrs_build_info.Q) the bucket in fixed point and sigma the q sums:
+ *   D'(i) = i*Q - N*sigma_l(i)  (N times the light deficit before l[i]) and
+ *   E'(j) = N*sigma_h(j) - j*Q  (N times the heavy excess before h[j]);
+ *   split record t holds D = D'(i_t), E = E'(j_t). */
 typedef struct wrs_layout {
-    uint64_t lh, ckl, ckh, splits;
+    uint64_t lh, ckl, ckh, seg_pre, splits;
     uint64_t sections;       /* s */
     uint64_t total_bytes;
 } wrs_layout;
@@ -183,6 +192,19 @@ enum wrs_stream_tag {
 int wrs_sample_rows(const wrs_row *d_rows, uint64_t n, uint64_t first,
                     uint64_t count, uint64_t seed, uint32_t stream_lo,
                     uint32_t stream_hi, uint32_t *d_out, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Measurement support                                                     */
+/* ---------------------------------------------------------------------- */
+
+/* Random-gather probe (the paper has no counterpart; it measures the
+ * hardware): `count` uniformly random 8-byte reads from d_rows[0..nrows),
+ * one 4-byte store each into d_out[0..count).  The bench uses its rate as
+ * the roofline of the naive sampler, whose cost is the same gather.
+ * flavor: 0 = read-only path (ld.global.nc), 1 = L2-only (ld.global.cg),
+ * 2 = streaming (ld.global.cs).  Contents of d_out are meaningless. */
+int wrs_diag_random_gather(const wrs_row *d_rows, uint64_t nrows, uint64_t count,
+                           uint64_t seed, int flavor, uint32_t *d_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -49,8 +49,8 @@ class Config(ctypes.Structure):
 
 class Layout(ctypes.Structure):
     _fields_ = [("lh", ctypes.c_uint64), ("ckl", ctypes.c_uint64), ("ckh", ctypes.c_uint64),
-                ("splits", ctypes.c_uint64), ("sections", ctypes.c_uint64),
-                ("total_bytes", ctypes.c_uint64)]
+                ("seg_pre", ctypes.c_uint64), ("splits", ctypes.c_uint64),
+                ("sections", ctypes.c_uint64), ("total_bytes", ctypes.c_uint64)]
 
 
 INFO_DTYPE = np.dtype([("status", "<i4"), ("scale", "<i4"), ("W", "<f8"), ("avg", "<f8"),
@@ -80,6 +80,7 @@ def lib():
                 "wrs_step_pack": (I, [U64, P, P, U64, CP, P]),
                 "wrs_step_info": (I, [U64, P, U64, CP, P, P]),
                 "wrs_sample_rows": (I, [P, U64, U64, U64, U64, U32, U32, P, P]),
+                "wrs_diag_random_gather": (I, [P, U64, U64, U64, I, P, P]),
                 "wrs_strerror": (ctypes.c_char_p, [I]),
                 "wrs_last_cuda_error": (I, []),
                 "wrs_abi_version": (I, []),
@@ -173,6 +174,12 @@ def sample_rows(rows, n: int, first: int, count: int, seed: int, out,
     (int32/uint32 [count], device)."""
     _check(lib().wrs_sample_rows(_ptr(rows), n, first, count, seed & (2**64 - 1), stream_lo,
                                  stream_hi, _ptr(out), _stream(stream)), "wrs_sample_rows")
+
+
+def diag_random_gather(rows, nrows: int, count: int, seed: int, flavor: int, out, stream=None):
+    """Enqueue the random-gather probe (measurement support, not the method)."""
+    _check(lib().wrs_diag_random_gather(_ptr(rows), nrows, count, seed, flavor, _ptr(out),
+                                        _stream(stream)), "wrs_diag_random_gather")
 
 
 def parse_info(info_tensor) -> dict:

@@ -15,6 +15,8 @@ cudaError_t launch_pack(uint64_t, wrs_row *, unsigned char *, const Layout &, ui
 cudaError_t launch_info(unsigned char *, const Layout &, wrs_build_info *, cudaStream_t);
 cudaError_t launch_sample_naive(const wrs_row *, uint64_t, uint64_t, uint64_t, uint64_t,
                                 uint32_t, uint32_t, uint32_t *, cudaStream_t);
+cudaError_t launch_random_gather(const void *, uint64_t, uint64_t, uint64_t, int, uint32_t *,
+                                 cudaStream_t);
 
 thread_local int g_last_cuda = 0;
 
@@ -97,6 +99,7 @@ int wrs_build_layout(uint64_t n, const wrs_config *cfg, wrs_layout *out) {
     out->lh = L.lh;
     out->ckl = L.ckl;
     out->ckh = L.ckh;
+    out->seg_pre = L.seg_pre;
     out->splits = L.splits;
     out->sections = L.sections;
     out->total_bytes = L.total;
@@ -180,6 +183,15 @@ int wrs_sample_rows(const wrs_row *d_rows, uint64_t n, uint64_t first, uint64_t 
     if (first + count < first) return WRS_EINVAL;
     return cuda_status(launch_sample_naive(d_rows, n, first, count, seed, stream_lo, stream_hi,
                                            d_out, (cudaStream_t)stream));
+}
+
+int wrs_diag_random_gather(const wrs_row *d_rows, uint64_t nrows, uint64_t count, uint64_t seed,
+                           int flavor, uint32_t *d_out, void *stream) {
+    if (!d_rows || nrows == 0 || ((uintptr_t)d_rows & 7u)) return WRS_EINVAL;
+    if (count && !d_out) return WRS_EINVAL;
+    if (flavor < 0 || flavor > 2) return WRS_EINVAL;
+    return cuda_status(
+        launch_random_gather(d_rows, nrows, count, seed, flavor, d_out, (cudaStream_t)stream));
 }
 
 }  // extern "C"

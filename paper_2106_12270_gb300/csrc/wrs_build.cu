@@ -6,12 +6,15 @@
 //   k_sum / k_total      a1: W = sum w_i, exact (per-exponent-band integer
 //                        sums), rounded once to FP64; avg = W/N; the scale S
 //                        of the fixed point q_i = round(w_i 2^S).
-//   k_partition          a2+a3: light iff w_i <= W/N; stable partition into
-//                        one array (lights from the front, heavies from the
-//                        back, Sec. 4.2 "weight in l and h"); single-pass
-//                        decoupled look-back over tiles for the global
-//                        ranks and the q prefix sums; one checkpoint of the
-//                        scaled deficit/excess prefix every 32 items.
+//   k_count / k_scatter  a2+a3: light iff w_i <= W/N; stable partition into
+//   / k_segscan          one array (lights from the front, heavies from the
+//                        back, Sec. 4.2 "weight in l and h").  Persistent
+//                        CTAs own contiguous segments: k_count counts each
+//                        segment's lights, k_scatter places every item and
+//                        writes a checkpoint of the q prefix sum every 32
+//                        list entries (relative to its segment), k_segscan
+//                        scans the segment sums.  No CTA waits on another,
+//                        and the result does not depend on timing.
 //   k_split              a4: for every section boundary k the Vose state
 //                        (i lights, k-i heavies closed) by a monotone search
 //                        over the checkpoints -- partial p-ary search
@@ -48,13 +51,12 @@ Layout make_layout(uint64_t n, uint32_t S) {
     L.sections = (n + S - 1) / S;
     L.params = take(sizeof(BuildParams));
     L.sum_bins = take((uint64_t)kSumMaxBlocks * kBands * sizeof(u128));
-    L.counter = take(16);
-    L.tflag = take(L.ntiles * 4);
-    L.tagg = take(L.ntiles * sizeof(TileVal));
-    L.tincl = take(L.ntiles * sizeof(TileVal));
+    L.seg_cnt = take((uint64_t)kMaxSegs * 4);
+    L.seg_sum = take((uint64_t)kMaxSegs * sizeof(SegVal));
+    L.seg_pre = take((uint64_t)(kMaxSegs + 1) * sizeof(SegVal));
     L.lh = take(n * sizeof(Entry));
-    L.ckl = take((n / 32 + 2) * sizeof(u128));
-    L.ckh = take((n / 32 + 2) * sizeof(u128));
+    L.ckl = take((n / 32 + 2) * sizeof(CkRec));
+    L.ckh = take((n / 32 + 2) * sizeof(CkRec));
     L.splits = take((L.sections + 1) * sizeof(SplitRec));
     L.total = off;
     return L;
@@ -214,6 +216,8 @@ k_total(const u128 *__restrict__ bins_in, int nblocks, uint64_t n, uint32_t sect
     if (top >= 94) Q += big_bits(big, top - 94, 1);
     P->Q = Q;
     P->Qn = Q / (u128)n;
+    P->NQn = (u128)n * P->Qn;
+    P->NQn1 = P->NQn + (u128)n;
     P->W = W;
     P->avg = avg;
     P->scale = 243 - top;
@@ -229,268 +233,274 @@ k_total(const u128 *__restrict__ bins_in, int nblocks, uint64_t n, uint32_t sect
 
 __device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
 
-__device__ __forceinline__ TileVal load_tileval(const TileVal *p) {
-    TileVal v;
-    const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(p);
-    ulonglong2 a = __ldcg(q), b = __ldcg(q + 1), c = __ldcg(q + 2);
-    v.sl = ((u128)a.y << 64) | a.x;
-    v.sh = ((u128)b.y << 64) | b.x;
-    v.nl = (uint32_t)c.x;
-    v.pad[0] = v.pad[1] = v.pad[2] = 0;
-    return v;
+// Segment g of G covers tiles [g*T/G, (g+1)*T/G) of kTile items.
+__device__ __forceinline__ void seg_tiles(uint32_t g, uint32_t G, uint64_t T, uint64_t &t0,
+                                          uint64_t &t1) {
+    t0 = (uint64_t)g * T / G;
+    t1 = (uint64_t)(g + 1) * T / G;
 }
 
-__device__ __forceinline__ void store_tileval(TileVal *p, const TileVal &v) {
-    ulonglong2 *q = reinterpret_cast<ulonglong2 *>(p);
-    __stcg(q, make_ulonglong2((uint64_t)v.sl, (uint64_t)(v.sl >> 64)));
-    __stcg(q + 1, make_ulonglong2((uint64_t)v.sh, (uint64_t)(v.sh >> 64)));
-    __stcg(q + 2, make_ulonglong2((uint64_t)v.nl, 0ull));
+// Block-wide sum of one uint32 per thread (blockDim.x a multiple of 32).
+__device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = __reduce_add_sync(0xffffffffu, v);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    uint32_t t = 0;
+    if (warp == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0u;
+        t = __reduce_add_sync(0xffffffffu, t);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) red[0] = t;
+    __syncthreads();
+    uint32_t r = red[0];
+    __syncthreads();
+    return r;
 }
 
-struct PartShared {
+// Light items per segment (one CTA per segment, coalesced 16-byte loads).
+__global__ void __launch_bounds__(kPartThreads)
+k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__ P,
+        uint32_t *__restrict__ seg_cnt, uint64_t T, uint32_t G, int aligned) {
+    __shared__ uint32_t red[32];
+    if (P->status) return;
+    const float lmax = P->light_max;
+    uint64_t t0, t1;
+    seg_tiles(blockIdx.x, G, T, t0, t1);
+    const uint64_t a = t0 * kTile, b = min(t1 * kTile, n);
+    uint32_t cnt = 0;
+    uint64_t tail = a;
+    if (aligned) {
+        const float4 *w4 = reinterpret_cast<const float4 *>(w);
+        const uint64_t b4 = b / 4;
+#pragma unroll 4
+        for (uint64_t i = a / 4 + threadIdx.x; i < b4; i += kPartThreads) {
+            float4 v = __ldg(w4 + i);
+            cnt += (v.x <= lmax) + (v.y <= lmax) + (v.z <= lmax) + (v.w <= lmax);
+        }
+        tail = b4 * 4 > a ? b4 * 4 : a;
+    }
+    for (uint64_t i = tail + threadIdx.x; i < b; i += kPartThreads) cnt += (__ldg(w + i) <= lmax);
+    cnt = block_sum_u32(cnt, red);
+    if (threadIdx.x == 0) seg_cnt[blockIdx.x] = cnt;
+}
+
+struct ScatterShared {
     float wv[kTile + kTile / 32];   // staged weights (padded, conflict-free)
     Entry e[kTile];                 // staged output entries
-    TileVal warp_tot[kPartThreads / 32];
-    TileVal prefix;                 // exclusive prefix of this tile
-    uint32_t tile;
-    uint32_t tile_nl;
-    uint32_t bad;                   // the look-back gave up: write nothing
+    u128 wsl[kPartThreads / 32], wsh[kPartThreads / 32];
+    uint32_t wnl[kPartThreads / 32];
+    u128 run_sl, run_sh;            // segment-local q sums before the tile
+    uint64_t run_l;                 // global light rank of the tile's first light
+    uint32_t red[32];
 };
 
-__device__ __forceinline__ TileVal tv_zero() {
-    TileVal v;
-    v.sl = 0; v.sh = 0; v.nl = 0;
-    v.pad[0] = v.pad[1] = v.pad[2] = 0;
-    return v;
+__device__ __forceinline__ void put_ck(CkRec *ck, uint64_t idx, uint32_t seg, u128 v) {
+    uint4 r = make_uint4(seg, (uint32_t)v, (uint32_t)(v >> 32), (uint32_t)(v >> 64));
+    *reinterpret_cast<uint4 *>(ck + idx) = r;
 }
 
-__device__ __forceinline__ void tv_add(TileVal &a, const TileVal &b) {
-    a.sl += b.sl; a.sh += b.sh; a.nl += b.nl;
-}
-
-__device__ __forceinline__ TileVal tv_warp_sum(TileVal v) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        TileVal o;
-        uint64_t a0 = __shfl_xor_sync(0xffffffffu, (uint64_t)v.sl, d);
-        uint64_t a1 = __shfl_xor_sync(0xffffffffu, (uint64_t)(v.sl >> 64), d);
-        uint64_t b0 = __shfl_xor_sync(0xffffffffu, (uint64_t)v.sh, d);
-        uint64_t b1 = __shfl_xor_sync(0xffffffffu, (uint64_t)(v.sh >> 64), d);
-        o.nl = __shfl_xor_sync(0xffffffffu, v.nl, d);
-        o.sl = ((u128)a1 << 64) | a0;
-        o.sh = ((u128)b1 << 64) | b0;
-        tv_add(v, o);
-    }
-    return v;
-}
-
-// Decoupled look-back (single-pass prefix over tiles), run by one full warp:
-// publish this tile's aggregate, then examine 32 predecessors at a time
-// (lane k looks at tile-1-k); stop at the nearest one that already published
-// its inclusive prefix and add the aggregates in between.  Every poll is
-// bounded; when a wait gives up (or another tile already failed) the warp
-// reports failure and publishes nothing more.
-__device__ TileVal lookback(uint32_t tile, const TileVal &agg, uint32_t *tflag, TileVal *tagg,
-                            TileVal *tincl, BuildParams *P, bool &failed) {
-    const int lane = threadIdx.x & 31;
-    failed = false;
-    TileVal pre = tv_zero();
-    if (tile == 0) {
-        if (lane == 0) {
-            store_tileval(&tincl[0], agg);
-            __threadfence();
-            st_release(&tflag[0], 2u);
-        }
-        return pre;
-    }
-    if (lane == 0) {
-        store_tileval(&tagg[tile], agg);
-        __threadfence();
-        st_release(&tflag[tile], 1u);
-    }
-    int64_t top = (int64_t)tile - 1;   // predecessor examined by lane 0
-    for (;;) {
-        const int64_t p = top - lane;
-        uint32_t f = 0;
-        bool gave_up = false;
-        if (p >= 0) {
-            uint32_t polls = 0;
-            for (;;) {
-                f = ld_acquire(&tflag[p]);
-                if (f != 0u) break;
-                if (++polls > kSpinLimit || ld_acquire(&P->status) != 0u) {
-                    gave_up = true;
-                    break;
-                }
-                __nanosleep(polls < 64 ? 32 : 256);
-            }
-        }
-        if (__any_sync(0xffffffffu, gave_up)) {
-            failed = true;
-            return pre;
-        }
-        const uint32_t incl = __ballot_sync(0xffffffffu, p >= 0 && f == 2u);
-        const int stop = incl ? __ffs(incl) - 1 : 32;   // nearest inclusive prefix
-        TileVal v = tv_zero();
-        if (p >= 0 && lane <= stop) v = load_tileval(f == 2u ? &tincl[p] : &tagg[p]);
-        tv_add(pre, tv_warp_sum(v));
-        if (incl) break;
-        top -= 32;
-    }
-    if (lane == 0) {
-        TileVal inc = pre;
-        tv_add(inc, agg);
-        store_tileval(&tincl[tile], inc);
-        __threadfence();
-        st_release(&tflag[tile], 2u);
-    }
-    return pre;
-}
-
+// Place every item of the segment: lights at l[rank] (entry rank), heavies at
+// h[rank] (entry n-1-rank); both stay in index order.  Every 32nd list entry
+// gets a checkpoint of the q sum before it (segment-relative).
 template <bool kAligned>
 __global__ void __launch_bounds__(kPartThreads, 3)
-k_partition(const float *__restrict__ w, uint64_t n, BuildParams *__restrict__ P,
-            uint32_t *__restrict__ counter, uint32_t *__restrict__ tflag,
-            TileVal *__restrict__ tagg, TileVal *__restrict__ tincl,
-            Entry *__restrict__ lh, u128 *__restrict__ ckl, u128 *__restrict__ ckh,
-            uint32_t ntiles) {
-    __shared__ PartShared sm;
+k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__ P,
+          const uint32_t *__restrict__ seg_cnt, Entry *__restrict__ lh, CkRec *__restrict__ ckl,
+          CkRec *__restrict__ ckh, SegVal *__restrict__ seg_sum, uint64_t T, uint32_t G) {
+    __shared__ ScatterShared sm;
     if (P->status) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid == 0) sm.tile = atomicAdd(counter, 1u);
-    __syncthreads();
-    const uint32_t tile = sm.tile;
-    const uint64_t base = (uint64_t)tile * kTile;
+    const uint32_t g = blockIdx.x;
+    uint64_t t0, t1;
+    seg_tiles(g, G, T, t0, t1);
     const int qshift = P->qshift;
     const u128 Qn = P->Qn;
     const float lmax = P->light_max;
 
-    // ---- load: coalesced 16-byte loads per warp, then a padded smem
-    // transpose so each lane owns 16 consecutive items.
-    const int wbase = warp * 512;
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        int e = wbase + r * 128 + lane * 4;
-        uint64_t g = base + e;
-        float4 v;
-        if (kAligned && g + 3 < n) {
-            v = __ldcs(reinterpret_cast<const float4 *>(w + g));
-        } else {
-            v.x = g + 0 < n ? w[g + 0] : 0.f;
-            v.y = g + 1 < n ? w[g + 1] : 0.f;
-            v.z = g + 2 < n ? w[g + 2] : 0.f;
-            v.w = g + 3 < n ? w[g + 3] : 0.f;
-        }
-        sm.wv[pad32(e + 0)] = v.x;
-        sm.wv[pad32(e + 1)] = v.y;
-        sm.wv[pad32(e + 2)] = v.z;
-        sm.wv[pad32(e + 3)] = v.w;
+    uint32_t pre = 0;
+    for (uint32_t k = tid; k < g; k += kPartThreads) pre += seg_cnt[k];
+    pre = block_sum_u32(pre, sm.red);
+    if (tid == 0) {
+        sm.run_l = pre;
+        sm.run_sl = 0;
+        sm.run_sh = 0;
     }
-    __syncwarp();
-    const int e0 = wbase + lane * kPartItems;
-    const uint64_t lim = n - base;   // valid items of this tile start below lim
 
-    // ---- classify; per-lane light count and q sums
-    uint32_t lmask = 0;
-    uint32_t cnt = 0;
-    u128 sl = 0, sh = 0;
+    const int wbase = warp * 512;
+    const int e0 = wbase + lane * kPartItems;
+    for (uint64_t tile = t0; tile < t1; ++tile) {
+        const uint64_t base = tile * kTile;
+        const uint64_t lim = n - base;   // items e of the tile are valid for e < lim
+        __syncthreads();                 // previous tile fully copied out
+        // ---- load: coalesced 16-byte loads, padded transpose to blocked
 #pragma unroll
-    for (int k = 0; k < kPartItems; ++k) {
-        float x = sm.wv[pad32(e0 + k)];
-        bool valid = (uint64_t)(e0 + k) < lim;
-        bool light = valid && x <= lmax;
-        lmask |= (uint32_t)light << k;
-        if (light) { sl += light_q(x, qshift, Qn); ++cnt; }
-        else if (valid) sh += heavy_q(x, qshift, Qn);
+        for (int r = 0; r < 4; ++r) {
+            int e = wbase + r * 128 + lane * 4;
+            float4 v;
+            if (kAligned && (uint64_t)e + 3 < lim) {
+                v = __ldcs(reinterpret_cast<const float4 *>(w + base + e));
+            } else {
+                v.x = (uint64_t)e + 0 < lim ? w[base + e + 0] : 0.f;
+                v.y = (uint64_t)e + 1 < lim ? w[base + e + 1] : 0.f;
+                v.z = (uint64_t)e + 2 < lim ? w[base + e + 2] : 0.f;
+                v.w = (uint64_t)e + 3 < lim ? w[base + e + 3] : 0.f;
+            }
+            sm.wv[pad32(e + 0)] = v.x;
+            sm.wv[pad32(e + 1)] = v.y;
+            sm.wv[pad32(e + 2)] = v.z;
+            sm.wv[pad32(e + 3)] = v.w;
+        }
+        __syncwarp();
+        // ---- classify; per-lane light count and q sums
+        uint32_t lmask = 0, cnt = 0;
+        u128 sl = 0, sh = 0;
+#pragma unroll
+        for (int k = 0; k < kPartItems; ++k) {
+            float x = sm.wv[pad32(e0 + k)];
+            bool valid = (uint64_t)(e0 + k) < lim;
+            bool light = valid && x <= lmax;
+            lmask |= (uint32_t)light << k;
+            if (light) {
+                sl += light_q(x, qshift, Qn);
+                ++cnt;
+            } else if (valid) {
+                sh += heavy_q(x, qshift, Qn);
+            }
+        }
+        uint32_t icnt = cnt;
+        u128 isl = sl, ish = sh;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t c2 = __shfl_up_sync(0xffffffffu, icnt, d);
+            u128 a2 = shfl_up_u128(isl, d), b2 = shfl_up_u128(ish, d);
+            if (lane >= d) { icnt += c2; isl += a2; ish += b2; }
+        }
+        if (lane == 31) {
+            sm.wnl[warp] = icnt;
+            sm.wsl[warp] = isl;
+            sm.wsh[warp] = ish;
+        }
+        __syncthreads();
+        // ---- ranks, staging, checkpoints
+        uint32_t wl = 0, tl = 0;
+        u128 wsl = 0, wsh = 0, tsl = 0, tsh = 0;
+#pragma unroll
+        for (int k = 0; k < kPartThreads / 32; ++k) {
+            uint32_t c = sm.wnl[k];
+            u128 a = sm.wsl[k], b = sm.wsh[k];
+            if (k < warp) { wl += c; wsl += a; wsh += b; }
+            tl += c; tsl += a; tsh += b;
+        }
+        const uint64_t run_l = sm.run_l;
+        const uint64_t run_h = base - run_l;
+        uint32_t lrank = wl + icnt - cnt;           // tile-local light rank
+        uint32_t hrank = (uint32_t)e0 - lrank;      // tile-local heavy rank
+        u128 rsl = sm.run_sl + wsl + isl - sl;      // segment-local light q before the item
+        u128 rsh = sm.run_sh + wsh + ish - sh;      // segment-local heavy q before the item
+#pragma unroll
+        for (int k = 0; k < kPartItems; ++k) {
+            if ((uint64_t)(e0 + k) >= lim) break;
+            float x = sm.wv[pad32(e0 + k)];
+            uint32_t item = (uint32_t)(base + e0 + k);
+            if ((lmask >> k) & 1u) {
+                uint64_t gr = run_l + lrank;
+                if ((gr & 31u) == 0) put_ck(ckl, gr >> 5, g, rsl);
+                sm.e[lrank] = Entry{item, x};
+                rsl += light_q(x, qshift, Qn);
+                ++lrank;
+            } else {
+                uint64_t gr = run_h + hrank;
+                if ((gr & 31u) == 0) put_ck(ckh, gr >> 5, g, rsh);
+                sm.e[kTile - 1 - hrank] = Entry{item, x};
+                rsh += heavy_q(x, qshift, Qn);
+                ++hrank;
+            }
+        }
+        __syncthreads();
+        // ---- coalesced copy-out
+        const uint64_t tvalid = lim < (uint64_t)kTile ? lim : (uint64_t)kTile;
+        const uint32_t tnh = (uint32_t)tvalid - tl;
+        uint2 *lh2 = reinterpret_cast<uint2 *>(lh);
+        const uint2 *e2 = reinterpret_cast<const uint2 *>(sm.e);
+        for (uint32_t a = tid; a < tl; a += kPartThreads) lh2[run_l + a] = e2[a];
+        for (uint32_t b = tid; b < tnh; b += kPartThreads)
+            lh2[n - 1 - (run_h + b)] = e2[kTile - 1 - b];
+        if (tid == 0) {
+            sm.run_l = run_l + tl;
+            sm.run_sl += tsl;
+            sm.run_sh += tsh;
+        }
     }
-    // warp inclusive scan of (cnt, sl, sh)
-    uint32_t icnt = cnt;
+    __syncthreads();
+    if (tid == 0) {
+        SegVal v;
+        v.sl = sm.run_sl;
+        v.sh = sm.run_sh;
+        v.nl = 0;
+        v.pad = 0;
+        seg_sum[g] = v;
+    }
+}
+
+// One CTA: exclusive scan over the segments of (light count, light q sum,
+// heavy q sum); totals nl, nh, D'(nl), E'(nh); the checkpoints that fall on
+// the very end of a list.
+__global__ void __launch_bounds__(kMaxSegs)
+k_segscan(BuildParams *__restrict__ P, const uint32_t *__restrict__ seg_cnt,
+          const SegVal *__restrict__ seg_sum, SegVal *__restrict__ seg_pre,
+          CkRec *__restrict__ ckl, CkRec *__restrict__ ckh, uint64_t n, uint32_t G) {
+    __shared__ SegVal wtot[kMaxSegs / 32];
+    if (P->status) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint64_t c = 0;
+    u128 sl = 0, sh = 0;
+    if ((uint32_t)tid < G) {
+        c = seg_cnt[tid];
+        sl = seg_sum[tid].sl;
+        sh = seg_sum[tid].sh;
+    }
+    uint64_t ic = c;
     u128 isl = sl, ish = sh;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        uint32_t c2 = __shfl_up_sync(0xffffffffu, icnt, d);
+        uint64_t c2 = __shfl_up_sync(0xffffffffu, ic, d);
         u128 a2 = shfl_up_u128(isl, d), b2 = shfl_up_u128(ish, d);
-        if (lane >= d) { icnt += c2; isl += a2; ish += b2; }
+        if (lane >= d) { ic += c2; isl += a2; ish += b2; }
     }
     if (lane == 31) {
-        sm.warp_tot[warp].nl = icnt;
-        sm.warp_tot[warp].sl = isl;
-        sm.warp_tot[warp].sh = ish;
-    }
-    // lane-exclusive prefixes within the warp
-    const uint32_t xcnt = icnt - cnt;
-    const u128 xsl = isl - sl, xsh = ish - sh;
-    __syncthreads();
-
-    // ---- tile aggregate and look-back (warp 0)
-    if (warp == 0) {
-        TileVal agg = tv_zero();
-        for (int k = 0; k < kPartThreads / 32; ++k) tv_add(agg, sm.warp_tot[k]);
-        bool failed;
-        TileVal pre = lookback(tile, agg, tflag, tagg, tincl, P, failed);
-        if (lane == 0) {
-            sm.bad = failed;
-            sm.prefix = pre;
-            sm.tile_nl = agg.nl;
-            if (failed) atomicOr(&P->status, ERR_TIMEOUT);
-            if (!failed && tile == ntiles - 1) {
-                const u128 Q = P->Q, N = (u128)n;
-                uint64_t nl = (uint64_t)pre.nl + agg.nl, nh = n - nl;
-                u128 Dtot = (u128)nl * Q - N * (pre.sl + agg.sl);
-                u128 Etot = N * (pre.sh + agg.sh) - (u128)nh * Q;
-                P->nl = nl;
-                P->nh = nh;
-                P->Dtot = Dtot;
-                P->Etot = Etot;
-                if ((nl & 31u) == 0) ckl[nl >> 5] = Dtot;
-                if ((nh & 31u) == 0) ckh[nh >> 5] = Etot;
-            }
-        }
+        wtot[warp].nl = ic;
+        wtot[warp].sl = isl;
+        wtot[warp].sh = ish;
     }
     __syncthreads();
-    if (sm.bad) return;
-
-    // ---- ranks, staging of entries, checkpoints
-    TileVal wpre = sm.prefix;
-    for (int k = 0; k < warp; ++k) tv_add(wpre, sm.warp_tot[k]);
-    const uint32_t tpre_nl = sm.prefix.nl;
-    const uint64_t pre_nh = base - tpre_nl;
-    uint32_t lrank = wpre.nl - tpre_nl + xcnt;                      // tile-local light rank
-    uint32_t hrank = (uint32_t)e0 - lrank;                          // tile-local heavy rank
-    u128 rsl = wpre.sl + xsl;                                       // light q before this item
-    u128 rsh = wpre.sh + xsh;                                       // heavy q before this item
-    const u128 Q = P->Q, N = (u128)n;
-#pragma unroll
-    for (int k = 0; k < kPartItems; ++k) {
-        if ((uint64_t)(e0 + k) >= lim) break;
-        float x = sm.wv[pad32(e0 + k)];
-        uint32_t item = (uint32_t)(base + e0 + k);
-        if ((lmask >> k) & 1u) {
-            uint64_t gr = (uint64_t)tpre_nl + lrank;
-            if ((gr & 31u) == 0) ckl[gr >> 5] = (u128)gr * Q - N * rsl;
-            sm.e[lrank] = Entry{item, x};
-            rsl += light_q(x, qshift, Qn);
-            ++lrank;
-        } else {
-            uint64_t gr = pre_nh + hrank;
-            if ((gr & 31u) == 0) ckh[gr >> 5] = N * rsh - (u128)gr * Q;
-            sm.e[kTile - 1 - hrank] = Entry{item, x};
-            rsh += heavy_q(x, qshift, Qn);
-            ++hrank;
-        }
+    uint64_t pc = ic - c;
+    u128 psl = isl - sl, psh = ish - sh;
+    for (int k = 0; k < warp; ++k) {
+        pc += wtot[k].nl;
+        psl += wtot[k].sl;
+        psh += wtot[k].sh;
     }
-    __syncthreads();
-
-    // ---- coalesced copy-out: lights ascending from the tile's light offset,
-    // heavies descending from n-1-(heavies before the tile)
-    const uint32_t tnl = sm.tile_nl;
-    const uint64_t tvalid = lim < (uint64_t)kTile ? lim : (uint64_t)kTile;
-    const uint32_t tnh = (uint32_t)tvalid - tnl;
-    uint2 *lh2 = reinterpret_cast<uint2 *>(lh);
-    const uint2 *e2 = reinterpret_cast<const uint2 *>(sm.e);
-    for (uint32_t a = tid; a < tnl; a += kPartThreads) lh2[tpre_nl + a] = e2[a];
-    for (uint32_t b = tid; b < tnh; b += kPartThreads)
-        lh2[n - 1 - (pre_nh + b)] = e2[kTile - 1 - b];
+    if ((uint32_t)tid <= G) {
+        SegVal v;
+        v.sl = psl;
+        v.sh = psh;
+        v.nl = pc;
+        v.pad = 0;
+        seg_pre[tid] = v;
+    }
+    if ((uint32_t)tid == G) {
+        // thread G holds the totals (its own value is zero)
+        const u128 Q = P->Q, N = (u128)n;
+        uint64_t nl = pc, nh = n - nl;
+        P->nl = nl;
+        P->nh = nh;
+        P->Dtot = (u128)nl * Q - N * psl;
+        P->Etot = N * psh - (u128)nh * Q;
+        if ((nl & 31u) == 0) put_ck(ckl, nl >> 5, G, 0);
+        if ((nh & 31u) == 0) put_ck(ckh, nh >> 5, G, 0);
+    }
 }
 
 // ===========================================================================
@@ -498,15 +508,31 @@ k_partition(const float *__restrict__ w, uint64_t n, BuildParams *__restrict__ P
 // ===========================================================================
 
 struct SplitCtx {
-    const u128 *ckl, *ckh;
+    const CkRec *ckl, *ckh;
+    const SegVal *seg_pre;
     const Entry *lh;
     uint64_t n, nl, nh;
-    uint64_t S;
+    u128 Q;
 };
 
 __device__ __forceinline__ u128 ld128(const u128 *p) {
     ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p));
     return ((u128)v.y << 64) | v.x;
+}
+
+// D'(32c) = 32c*Q - N*(q sum of the first 32c light entries).
+__device__ __forceinline__ u128 ck_D(const SplitCtx &C, uint64_t c) {
+    uint4 r = __ldg(reinterpret_cast<const uint4 *>(C.ckl + c));
+    u128 local = ((u128)r.w << 64) | ((u128)r.z << 32) | r.y;
+    u128 sig = ld128(&C.seg_pre[r.x].sl) + local;
+    return (u128)(32 * c) * C.Q - (u128)C.n * sig;
+}
+// E'(32c) = N*(q sum of the first 32c heavy entries) - 32c*Q.
+__device__ __forceinline__ u128 ck_E(const SplitCtx &C, uint64_t c) {
+    uint4 r = __ldg(reinterpret_cast<const uint4 *>(C.ckh + c));
+    u128 local = ((u128)r.w << 64) | ((u128)r.z << 32) | r.y;
+    u128 sig = ld128(&C.seg_pre[r.x].sh) + local;
+    return (u128)C.n * sig - (u128)(32 * c) * C.Q;
 }
 
 // P(32c) for bucket count k: monotone in c; false below the valid range of
@@ -517,7 +543,7 @@ __device__ __forceinline__ bool pred_c(const SplitCtx &C, uint64_t k, uint64_t c
     uint64_t i = 32 * c;
     if (i < lo) return false;
     if (i >= hi) return true;
-    return ld128(C.ckh + ((k - i) >> 5)) <= ld128(C.ckl + c);
+    return ck_E(C, (k - i) >> 5) <= ck_D(C, c);
 }
 
 __device__ __forceinline__ void crange(const SplitCtx &C, uint64_t k, uint64_t &clo,
@@ -534,24 +560,24 @@ __device__ void split_fine(const SplitCtx &C, const BuildParams &Pm, uint64_t k,
                            SplitRec *out, int lane) {
     uint64_t lo = k > C.nh ? k - C.nh : 0;
     uint64_t hi = k < C.nl ? k : C.nl;
-    const u128 N = (u128)C.n;
+    const uint32_t N = (uint32_t)C.n;
     uint64_t ans;
     u128 Dv, Ev;
     if (c == 0) {
         ans = 0;
         Dv = 0;
-        Ev = ld128(C.ckh + (k >> 5));
+        Ev = ck_E(C, k >> 5);
     } else {
         uint64_t lb = 32 * (c - 1);  // light base
         uint64_t hb = k - 32 * c;    // heavy base, multiple of 32
         u128 d = 0, e = 0;
         if (lb + lane < C.nl) {
             Entry en = C.lh[lb + lane];
-            d = Pm.Q - N * light_q(en.w, Pm.qshift, Pm.Qn);
+            d = Pm.Q - light_nq(en.w, Pm.qshift, N, Pm.NQn);
         }
         if (hb + lane < C.nh) {
             Entry en = C.lh[C.n - 1 - (hb + lane)];
-            e = N * heavy_q(en.w, Pm.qshift, Pm.Qn) - Pm.Q;
+            e = heavy_nq(en.w, Pm.qshift, N, Pm.NQn1) - Pm.Q;
         }
         u128 dinc = d, einc = e;
 #pragma unroll
@@ -560,8 +586,8 @@ __device__ void split_fine(const SplitCtx &C, const BuildParams &Pm, uint64_t k,
             if (lane >= s) { dinc += a; einc += b; }
         }
         u128 eexc = einc - e;
-        u128 Dbase = ld128(C.ckl + (c - 1));
-        u128 Ebase = ld128(C.ckh + (hb >> 5));
+        u128 Dbase = ck_D(C, c - 1);
+        u128 Ebase = ck_E(C, hb >> 5);
         u128 Dl = Dbase + dinc;                                   // D'(lb + 1 + lane)
         u128 Eh = Ebase + shfl_u128(eexc, 31 - lane);             // E'(k - (lb + 1 + lane))
         uint64_t i = lb + 1 + lane;
@@ -592,15 +618,17 @@ __device__ void split_fine(const SplitCtx &C, const BuildParams &Pm, uint64_t k,
 template <bool kPary>
 __global__ void __launch_bounds__(kSplitThreads)
 k_split(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
-        const u128 *__restrict__ ckl, const u128 *__restrict__ ckh,
-        SplitRec *__restrict__ splits, uint64_t n, uint64_t S, uint32_t sections) {
+        const CkRec *__restrict__ ckl, const CkRec *__restrict__ ckh,
+        const SegVal *__restrict__ seg_pre, SplitRec *__restrict__ splits, uint64_t n,
+        uint64_t S, uint32_t sections) {
     __shared__ uint64_t s_c[kSplitThreads];
     __shared__ unsigned long long s_a, s_b;
     __shared__ int s_go;
     if (P->status) return;
     const BuildParams Pm = *P;
     SplitCtx C;
-    C.ckl = ckl; C.ckh = ckh; C.lh = lh; C.n = n; C.nl = Pm.nl; C.nh = Pm.nh; C.S = S;
+    C.ckl = ckl; C.ckh = ckh; C.seg_pre = seg_pre; C.lh = lh; C.n = n; C.nl = Pm.nl;
+    C.nh = Pm.nh; C.Q = Pm.Q;
     const int tid = threadIdx.x;
     const uint64_t t0 = 1 + (uint64_t)blockIdx.x * kSplitThreads;   // first split of block
     const uint64_t t = t0 + tid;
@@ -703,7 +731,8 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
     const int tid = threadIdx.x;
     const uint32_t t = blockIdx.x;
     const uint64_t nh = P->nh;
-    const u128 Q = P->Q, Qn = P->Qn, N = (u128)n;
+    const u128 Q = P->Q, NQn = P->NQn, NQn1 = P->NQn1;
+    const uint32_t N = (uint32_t)n;
     const int qshift = P->qshift;
     const float inv_avg = P->inv_avg, Qf = P->Qf;
     const SplitRec R0 = splits[t], R1 = splits[t + 1];
@@ -734,7 +763,7 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
         uint32_t e = b0 + k;
         if (e >= K) break;
         float wv = sW[pad32(e)];
-        u128 val = (e < L) ? Q - N * light_q(wv, qshift, Qn) : N * heavy_q(wv, qshift, Qn) - Q;
+        u128 val = (e < L) ? Q - light_nq(wv, qshift, N, NQn) : heavy_nq(wv, qshift, N, NQn1) - Q;
         sP[pp8(e + 1)] = val;
         run += val;
     }
@@ -866,25 +895,30 @@ cudaError_t launch_total(const float *d_w, uint64_t n, unsigned char *ws, const 
     return cudaGetLastError();
 }
 
+uint32_t num_segments(const Layout &L) {
+    uint64_t g = (uint64_t)num_sms() * kSegPerSM;
+    if (g > (uint64_t)kMaxSegs - 1) g = kMaxSegs - 1;
+    if (g > L.ntiles) g = L.ntiles;
+    return (uint32_t)(g ? g : 1);
+}
+
 cudaError_t launch_partition(const float *d_w, uint64_t n, unsigned char *ws, const Layout &L,
                              cudaStream_t st) {
     BuildParams *P = reinterpret_cast<BuildParams *>(ws + L.params);
-    cudaError_t err = cudaMemsetAsync(ws + L.counter, 0, 16, st);
-    if (!err) err = cudaMemsetAsync(ws + L.tflag, 0, L.ntiles * 4, st);
-    if (err) return err;
-    auto *cnt = reinterpret_cast<uint32_t *>(ws + L.counter);
-    auto *flag = reinterpret_cast<uint32_t *>(ws + L.tflag);
-    auto *agg = reinterpret_cast<TileVal *>(ws + L.tagg);
-    auto *inc = reinterpret_cast<TileVal *>(ws + L.tincl);
+    auto *cnt = reinterpret_cast<uint32_t *>(ws + L.seg_cnt);
+    auto *sum = reinterpret_cast<SegVal *>(ws + L.seg_sum);
+    auto *pre = reinterpret_cast<SegVal *>(ws + L.seg_pre);
     auto *lh = reinterpret_cast<Entry *>(ws + L.lh);
-    auto *ckl = reinterpret_cast<u128 *>(ws + L.ckl);
-    auto *ckh = reinterpret_cast<u128 *>(ws + L.ckh);
-    if (((uintptr_t)d_w % 16) == 0)
-        k_partition<true><<<(unsigned)L.ntiles, kPartThreads, 0, st>>>(
-            d_w, n, P, cnt, flag, agg, inc, lh, ckl, ckh, (uint32_t)L.ntiles);
+    auto *ckl = reinterpret_cast<CkRec *>(ws + L.ckl);
+    auto *ckh = reinterpret_cast<CkRec *>(ws + L.ckh);
+    const uint32_t G = num_segments(L);
+    const int aligned = ((uintptr_t)d_w % 16) == 0;
+    k_count<<<G, kPartThreads, 0, st>>>(d_w, n, P, cnt, L.ntiles, G, aligned);
+    if (aligned)
+        k_scatter<true><<<G, kPartThreads, 0, st>>>(d_w, n, P, cnt, lh, ckl, ckh, sum, L.ntiles, G);
     else
-        k_partition<false><<<(unsigned)L.ntiles, kPartThreads, 0, st>>>(
-            d_w, n, P, cnt, flag, agg, inc, lh, ckl, ckh, (uint32_t)L.ntiles);
+        k_scatter<false><<<G, kPartThreads, 0, st>>>(d_w, n, P, cnt, lh, ckl, ckh, sum, L.ntiles, G);
+    k_segscan<<<1, kMaxSegs, 0, st>>>(P, cnt, sum, pre, ckl, ckh, n, G);
     return cudaGetLastError();
 }
 
@@ -892,17 +926,18 @@ cudaError_t launch_split(uint64_t n, unsigned char *ws, const Layout &L, uint32_
                          uint32_t method, cudaStream_t st) {
     const BuildParams *P = reinterpret_cast<const BuildParams *>(ws + L.params);
     auto *lh = reinterpret_cast<const Entry *>(ws + L.lh);
-    auto *ckl = reinterpret_cast<const u128 *>(ws + L.ckl);
-    auto *ckh = reinterpret_cast<const u128 *>(ws + L.ckh);
+    auto *ckl = reinterpret_cast<const CkRec *>(ws + L.ckl);
+    auto *ckh = reinterpret_cast<const CkRec *>(ws + L.ckh);
+    auto *pre = reinterpret_cast<const SegVal *>(ws + L.seg_pre);
     auto *sp = reinterpret_cast<SplitRec *>(ws + L.splits);
     uint32_t s = (uint32_t)L.sections;
     k_split_ends<<<1, 1, 0, st>>>(P, sp, s);
     if (s > 1) {
         unsigned blocks = (unsigned)((s - 1 + kSplitThreads - 1) / kSplitThreads);
         if (method == WRS_SPLIT_BINARY)
-            k_split<false><<<blocks, kSplitThreads, 0, st>>>(P, lh, ckl, ckh, sp, n, S, s);
+            k_split<false><<<blocks, kSplitThreads, 0, st>>>(P, lh, ckl, ckh, pre, sp, n, S, s);
         else
-            k_split<true><<<blocks, kSplitThreads, 0, st>>>(P, lh, ckl, ckh, sp, n, S, s);
+            k_split<true><<<blocks, kSplitThreads, 0, st>>>(P, lh, ckl, ckh, pre, sp, n, S, s);
     }
     return cudaGetLastError();
 }

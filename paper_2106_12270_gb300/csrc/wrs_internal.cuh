@@ -36,6 +36,8 @@ struct __align__(16) BuildParams {
     u128 Qn;           // floor(Q / N)
     u128 Dtot;         // D'(nl): total scaled light deficit
     u128 Etot;         // E'(nh): total scaled heavy excess
+    u128 NQn;          // N * Qn: largest N*q a light item may have
+    u128 NQn1;         // N * (Qn + 1): smallest N*q a heavy item may have
     double W;          // exact total weight rounded to FP64
     double avg;        // W / N
     uint64_t n;
@@ -54,13 +56,12 @@ struct __align__(16) BuildParams {
 struct Layout {
     uint64_t params;     // BuildParams
     uint64_t sum_bins;   // kSumMaxBlocks * kBands u128
-    uint64_t counter;    // uint32 tile counter (+ pad)
-    uint64_t tflag;      // ntiles uint32 flags
-    uint64_t tagg;       // ntiles TileVal (aggregate)
-    uint64_t tincl;      // ntiles TileVal (inclusive prefix)
+    uint64_t seg_cnt;    // kMaxSegs uint32 light counts per segment
+    uint64_t seg_sum;    // kMaxSegs SegVal (segment q sums)
+    uint64_t seg_pre;    // (kMaxSegs + 1) SegVal (exclusive prefixes)
     uint64_t lh;         // n Entry
-    uint64_t ckl;        // (n/32 + 2) u128
-    uint64_t ckh;        // (n/32 + 2) u128
+    uint64_t ckl;        // (n/32 + 2) CkRec
+    uint64_t ckh;        // (n/32 + 2) CkRec
     uint64_t splits;     // (s+1) SplitRec
     uint64_t total;
     uint64_t ntiles;
@@ -72,11 +73,19 @@ struct __align__(8) Entry {   // one slot of the l/h array
     float w;
 };
 
-struct __align__(16) TileVal {  // per-tile partition aggregate / prefix
-    u128 sl;      // sum of light q (adjusted)
-    u128 sh;      // sum of heavy q (adjusted)
-    uint32_t nl;  // light count
-    uint32_t pad[3];
+struct __align__(16) SegVal {   // per-segment partition sums / prefixes
+    u128 sl;      // sum of light q (clamped)
+    u128 sh;      // sum of heavy q (clamped)
+    uint64_t nl;  // light count
+    uint64_t pad;
+};
+
+// Checkpoint of a prefix sum every 32 list entries: the q sum of the entries
+// before it, relative to the start of the partition segment `seg` that holds
+// it (the segment's own prefix is in seg_pre).
+struct __align__(16) CkRec {
+    uint32_t seg;
+    uint32_t s[3];   // 96-bit local q sum (< 2^95)
 };
 
 struct __align__(16) SplitRec {  // Vose state after k_t buckets
@@ -94,6 +103,8 @@ constexpr int kPartThreads = 256;
 constexpr int kPartItems = 16;
 constexpr int kTile = kPartThreads * kPartItems;   // 4096 items per tile
 constexpr int kPackThreads = 256;
+constexpr int kSegPerSM = 4;          // partition segments (persistent CTAs) per SM
+constexpr int kMaxSegs = 1024;
 constexpr int kSplitThreads = 256;    // also p of the partial p-ary search
 
 static inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
@@ -117,31 +128,67 @@ __device__ __forceinline__ u128 shfl_u128(u128 v, int src) {
     return ((u128)hi << 64) | lo;
 }
 
-// Fixed-point value of an FP32 weight: round(w * 2^S) = m * 2^(e' + qshift),
-// rounded half up when the shift is negative.  The weight must be finite and
-// non-negative (checked by the total-weight step before any caller runs).
-__device__ __forceinline__ u128 fixed_of(float w, int qshift) {
+// v << s as a 128-bit value, for v < 2^64 and s in [0, 127].
+__device__ __forceinline__ u128 shl_u64(uint64_t v, uint32_t s) {
+    uint64_t lo, hi;
+    if (s < 64) {
+        lo = v << s;
+        hi = s ? (v >> (64 - s)) : 0ull;
+    } else {
+        lo = 0ull;
+        hi = v << (s - 64);
+    }
+    return ((u128)hi << 64) | lo;
+}
+
+// Fixed point of an FP32 weight: q = round(w * 2^S) = t << s with t < 2^24.
+// w = m * 2^(e'-150) (e' = max(biased exponent, 1)), so q = m * 2^(e' +
+// qshift); a negative exponent rounds half up.  The weight must be finite
+// (checked by the total-weight step before any caller runs); the sign bit is
+// ignored (-0 is 0).
+__device__ __forceinline__ void fixed_parts(float w, int qshift, uint32_t &t, uint32_t &s) {
     uint32_t u = __float_as_uint(w) & 0x7fffffffu;
     uint32_t e = u >> 23;
     uint32_t m = (u & 0x7fffffu) | (e ? 0x800000u : 0u);
     int sh = (int)(e ? e : 1u) + qshift;
-    if (sh >= 0)
-        return (u128)m << sh;           // sh <= 70: m * 2^sh < 2^94
-    int r = -sh;
-    if (r > 24)
-        return 0;
-    return (u128)((m + (1u << (r - 1))) >> r);
+    if (sh >= 0) {
+        t = m;
+        s = (uint32_t)sh;
+    } else {
+        int r = -sh;
+        t = r > 24 ? 0u : ((m + (1u << (r - 1))) >> r);
+        s = 0;
+    }
 }
 
-// Light weights give d' = Q - N*q >= 0 and heavy weights e' = N*q - Q > 0,
-// after clamping q into the side of Q/N its class requires.
+// q of a light item, clamped to at most Qn = floor(Q/N) so that its scaled
+// deficit d' = Q - N*q is >= 0; q of a heavy item, clamped to at least Qn+1
+// so that its scaled excess e' = N*q - Q is > 0.
 __device__ __forceinline__ u128 light_q(float w, int qshift, u128 Qn) {
-    u128 q = fixed_of(w, qshift);
+    uint32_t t, s;
+    fixed_parts(w, qshift, t, s);
+    u128 q = shl_u64(t, s);
     return q > Qn ? Qn : q;
 }
 __device__ __forceinline__ u128 heavy_q(float w, int qshift, u128 Qn) {
-    u128 q = fixed_of(w, qshift);
+    uint32_t t, s;
+    fixed_parts(w, qshift, t, s);
+    u128 q = shl_u64(t, s);
     return q <= Qn ? Qn + 1 : q;
+}
+// N*q directly (one 32x32->64 product, then a shift), with the same clamps:
+// N*q_light <= NQn = N*Qn and N*q_heavy >= NQn1 = N*(Qn+1).
+__device__ __forceinline__ u128 light_nq(float w, int qshift, uint32_t N, u128 NQn) {
+    uint32_t t, s;
+    fixed_parts(w, qshift, t, s);
+    u128 v = shl_u64((uint64_t)N * t, s);
+    return v > NQn ? NQn : v;
+}
+__device__ __forceinline__ u128 heavy_nq(float w, int qshift, uint32_t N, u128 NQn1) {
+    uint32_t t, s;
+    fixed_parts(w, qshift, t, s);
+    u128 v = shl_u64((uint64_t)N * t, s);
+    return v < NQn1 ? NQn1 : v;
 }
 
 // ---------------------------------------------------------------------------

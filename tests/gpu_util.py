@@ -49,10 +49,25 @@ class Built:
         hraw = raw[self.n - nh:][::-1]
         return li, lw, hraw[:, 0].copy(), hraw[:, 1].copy().view(np.float32)
 
+    def seg_pre(self, nseg):
+        raw = self._ws(self.layout["seg_pre"], 48 * (nseg + 1)).view(np.uint32).reshape(-1, 12)
+        out = []
+        for r in raw:
+            sl = sum(int(r[k]) << (32 * k) for k in range(4))
+            sh = sum(int(r[4 + k]) << (32 * k) for k in range(4))
+            out.append((sl, sh, int(r[8]) | int(r[9]) << 32))
+        return out
+
     def checkpoints(self, which: str):
+        """Absolute q prefix sums sigma(32c) of the light ("ckl") or heavy
+        ("ckh") list, c = 0..floor(count/32)."""
         cnt = (self.info["nl"] if which == "ckl" else self.info["nh"]) // 32 + 1
-        raw = self._ws(self.layout[which], 16 * cnt).view(np.uint64).reshape(-1, 2)
-        return [int(lo) | int(hi) << 64 for lo, hi in raw]
+        raw = self._ws(self.layout[which], 16 * cnt).view(np.uint32).reshape(-1, 4)
+        segs = raw[:, 0].astype(np.int64)
+        pre = self.seg_pre(int(segs.max()) if cnt else 0)
+        col = 0 if which == "ckl" else 1
+        return [pre[int(r[0])][col] + (int(r[1]) | int(r[2]) << 32 | int(r[3]) << 64)
+                for r in raw]
 
     def splits(self):
         s = self.layout["sections"]

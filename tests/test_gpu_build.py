@@ -82,11 +82,12 @@ def test_prefix_checkpoints_exact(kind):
         ck = b.checkpoints(which)
         ex = exact_prefix(w, lst, 32)
         assert len(ck) == len(ex)
-        for c, (val, sig) in enumerate(zip(ck, ex)):
+        for c, (sig_q, sig) in enumerate(zip(ck, ex)):
             i = 32 * c
-            # normalised deficit (lights) i - sigma*N/W; excess (heavies) sigma*N/W - i
+            # D'(i)/Q = i - N sigma_q/Q (lights), E'(i)/Q = N sigma_q/Q - i (heavies);
+            # exact: i - sigma N/W and sigma N/W - i
+            got = sign * Fraction(i * Q - n * sig_q, Q)
             want = sign * (i - sig * n / Wx)
-            got = Fraction(val, Q)
             assert abs(got - want) <= Fraction(1, 10**12) * max(1, abs(want)), (which, c)
 
 
