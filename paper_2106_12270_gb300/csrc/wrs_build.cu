@@ -287,12 +287,13 @@ k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__
 }
 
 struct ScatterShared {
-    float wv[kTile + kTile / 32];   // staged weights (padded, conflict-free)
-    Entry e[kTile];                 // staged output entries
-    u128 wsl[kPartThreads / 32], wsh[kPartThreads / 32];
-    uint32_t wnl[kPartThreads / 32];
-    u128 run_sl, run_sh;            // segment-local q sums before the tile
-    uint64_t run_l;                 // global light rank of the tile's first light
+    float wv[kTile + kTile / 32];       // staged weights (padded, conflict-free)
+    Entry e[kTile + kTile / 16];        // staged entries in list order (padded)
+    u128 wsum[kPartThreads / 32];       // per-warp q totals of the list-order pass
+    uint32_t wnl[kPartThreads / 32];    // per-warp light counts
+    u128 tile_l;                        // q sum of the tile's lights
+    u128 run_sl, run_sh;                // segment-local q sums before the tile
+    uint64_t run_l;                     // global light rank of the tile's first light
     uint32_t red[32];
 };
 
@@ -301,9 +302,18 @@ __device__ __forceinline__ void put_ck(CkRec *ck, uint64_t idx, uint32_t seg, u1
     *reinterpret_cast<uint4 *>(ck + idx) = r;
 }
 
+__device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
+
 // Place every item of the segment: lights at l[rank] (entry rank), heavies at
 // h[rank] (entry n-1-rank); both stay in index order.  Every 32nd list entry
 // gets a checkpoint of the q sum before it (segment-relative).
+//
+// Per tile: classify in input order (lane = 16 consecutive items), rank with
+// a count scan, stage the entries in list order, then compute q once per
+// entry in list order (thread = 16 consecutive slots, so light and heavy
+// slots rarely share a thread) with one block scan; the checkpoint sums are
+// snapshots of the running sum at the one slot per thread where a
+// checkpoint can fall.
 template <bool kAligned>
 __global__ void __launch_bounds__(kPartThreads, 3)
 k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__ P,
@@ -329,11 +339,12 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
     }
 
     const int wbase = warp * 512;
-    const int e0 = wbase + lane * kPartItems;
+    const int e0 = wbase + lane * kPartItems;   // this lane's first item of the tile
+    const int s0 = tid * kPartItems;            // this thread's first list slot
     for (uint64_t tile = t0; tile < t1; ++tile) {
         const uint64_t base = tile * kTile;
         const uint64_t lim = n - base;   // items e of the tile are valid for e < lim
-        __syncthreads();                 // previous tile fully copied out
+        __syncthreads();                 // previous tile fully consumed
         // ---- load: coalesced 16-byte loads, padded transpose to blocked
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -353,84 +364,103 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
             sm.wv[pad32(e + 3)] = v.w;
         }
         __syncwarp();
-        // ---- classify; per-lane light count and q sums
-        uint32_t lmask = 0, cnt = 0;
-        u128 sl = 0, sh = 0;
+        // ---- classify (input order) and count
+        uint32_t lmask = 0, vmask = 0;
 #pragma unroll
         for (int k = 0; k < kPartItems; ++k) {
             float x = sm.wv[pad32(e0 + k)];
             bool valid = (uint64_t)(e0 + k) < lim;
-            bool light = valid && x <= lmax;
-            lmask |= (uint32_t)light << k;
-            if (light) {
-                sl += light_q(x, qshift, Qn);
-                ++cnt;
-            } else if (valid) {
-                sh += heavy_q(x, qshift, Qn);
-            }
+            vmask |= (uint32_t)valid << k;
+            lmask |= (uint32_t)(valid && x <= lmax) << k;
         }
+        const uint32_t cnt = __popc(lmask);
         uint32_t icnt = cnt;
-        u128 isl = sl, ish = sh;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             uint32_t c2 = __shfl_up_sync(0xffffffffu, icnt, d);
-            u128 a2 = shfl_up_u128(isl, d), b2 = shfl_up_u128(ish, d);
-            if (lane >= d) { icnt += c2; isl += a2; ish += b2; }
+            if (lane >= d) icnt += c2;
         }
-        if (lane == 31) {
-            sm.wnl[warp] = icnt;
-            sm.wsl[warp] = isl;
-            sm.wsh[warp] = ish;
-        }
+        if (lane == 31) sm.wnl[warp] = icnt;
         __syncthreads();
-        // ---- ranks, staging, checkpoints
         uint32_t wl = 0, tl = 0;
-        u128 wsl = 0, wsh = 0, tsl = 0, tsh = 0;
 #pragma unroll
         for (int k = 0; k < kPartThreads / 32; ++k) {
             uint32_t c = sm.wnl[k];
-            u128 a = sm.wsl[k], b = sm.wsh[k];
-            if (k < warp) { wl += c; wsl += a; wsh += b; }
-            tl += c; tsl += a; tsh += b;
+            wl += (k < warp) ? c : 0u;
+            tl += c;
         }
         const uint64_t run_l = sm.run_l;
         const uint64_t run_h = base - run_l;
-        uint32_t lrank = wl + icnt - cnt;           // tile-local light rank
-        uint32_t hrank = (uint32_t)e0 - lrank;      // tile-local heavy rank
-        u128 rsl = sm.run_sl + wsl + isl - sl;      // segment-local light q before the item
-        u128 rsh = sm.run_sh + wsh + ish - sh;      // segment-local heavy q before the item
+        const uint32_t tv = lim < (uint64_t)kTile ? (uint32_t)lim : (uint32_t)kTile;
+        const uint32_t tnh = tv - tl;
+        // ---- stage entries in list order: lights at slot rank, heavies at
+        // slot kTile-1-rank
+        {
+            uint32_t lrank = wl + icnt - cnt;
+            uint32_t hrank = (uint32_t)e0 - lrank;
 #pragma unroll
-        for (int k = 0; k < kPartItems; ++k) {
-            if ((uint64_t)(e0 + k) >= lim) break;
-            float x = sm.wv[pad32(e0 + k)];
-            uint32_t item = (uint32_t)(base + e0 + k);
-            if ((lmask >> k) & 1u) {
-                uint64_t gr = run_l + lrank;
-                if ((gr & 31u) == 0) put_ck(ckl, gr >> 5, g, rsl);
-                sm.e[lrank] = Entry{item, x};
-                rsl += light_q(x, qshift, Qn);
-                ++lrank;
-            } else {
-                uint64_t gr = run_h + hrank;
-                if ((gr & 31u) == 0) put_ck(ckh, gr >> 5, g, rsh);
-                sm.e[kTile - 1 - hrank] = Entry{item, x};
-                rsh += heavy_q(x, qshift, Qn);
-                ++hrank;
+            for (int k = 0; k < kPartItems; ++k) {
+                if (!((vmask >> k) & 1u)) break;
+                Entry en{(uint32_t)(base + e0 + k), sm.wv[pad32(e0 + k)]};
+                if ((lmask >> k) & 1u) sm.e[pad16(lrank++)] = en;
+                else sm.e[pad16(kTile - 1 - hrank++)] = en;
             }
         }
         __syncthreads();
+        // ---- list-order q pass: slots [s0, s0+16) of this thread
+        const uint32_t hstart = kTile - tnh;   // first heavy slot
+        const int cl = (int)((32u - (uint32_t)(run_l & 31u)) & 31u);      // light ckpt slots = cl mod 32
+        const int ch = (int)((uint32_t)(run_h + kTile - 1) & 31u);      // heavy ckpt slots = ch mod 32
+        const int kl = (cl - s0) & 31;    // local index of this thread's light ckpt slot (if < 16)
+        const int kh = (ch - s0) & 31;
+        const int kb = (int)tl - s0;      // local index of the light/heavy boundary
+        u128 acc = 0, snap_l = 0, snap_h = 0, snap_b = 0;
+#pragma unroll
+        for (int k = 0; k < kPartItems; ++k) {
+            uint32_t slot = (uint32_t)(s0 + k);
+            if (k == kl) snap_l = acc;
+            if (k == kb) snap_b = acc;
+            u128 v = 0;
+            if (slot < tl) v = light_q(sm.e[pad16(slot)].w, qshift, Qn);
+            else if (slot >= hstart) v = heavy_q(sm.e[pad16(slot)].w, qshift, Qn);
+            acc += v;
+            if (k == kh) snap_h = acc;    // inclusive of the heavy ckpt slot
+        }
+        // block exclusive scan of the thread totals
+        u128 inc = acc;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            u128 o = shfl_up_u128(inc, d);
+            if (lane >= d) inc += o;
+        }
+        if (lane == 31) sm.wsum[warp] = inc;
+        __syncthreads();
+        u128 X = inc - acc, Tall = 0;
+#pragma unroll
+        for (int k = 0; k < kPartThreads / 32; ++k) {
+            u128 c = sm.wsum[k];
+            X += (k < warp) ? c : (u128)0;
+            Tall += c;
+        }
+        if (kb >= 0 && kb < kPartItems) sm.tile_l = X + snap_b;
+        if (tl == (uint32_t)kTile && tid == 0) sm.tile_l = Tall;
+        const u128 run_sl = sm.run_sl, run_sh = sm.run_sh;
+        if (kl < kPartItems && (uint32_t)(s0 + kl) < tl)
+            put_ck(ckl, (run_l + s0 + kl) >> 5, g, run_sl + X + snap_l);
+        if (kh < kPartItems && (uint32_t)(s0 + kh) >= hstart)
+            put_ck(ckh, (run_h + kTile - 1 - (s0 + kh)) >> 5, g, run_sh + (Tall - X - snap_h));
         // ---- coalesced copy-out
-        const uint64_t tvalid = lim < (uint64_t)kTile ? lim : (uint64_t)kTile;
-        const uint32_t tnh = (uint32_t)tvalid - tl;
         uint2 *lh2 = reinterpret_cast<uint2 *>(lh);
         const uint2 *e2 = reinterpret_cast<const uint2 *>(sm.e);
-        for (uint32_t a = tid; a < tl; a += kPartThreads) lh2[run_l + a] = e2[a];
+        for (uint32_t a = tid; a < tl; a += kPartThreads) lh2[run_l + a] = e2[pad16(a)];
         for (uint32_t b = tid; b < tnh; b += kPartThreads)
-            lh2[n - 1 - (run_h + b)] = e2[kTile - 1 - b];
+            lh2[n - 1 - (run_h + b)] = e2[pad16(kTile - 1 - b)];
+        __syncthreads();   // tile_l written
         if (tid == 0) {
+            u128 TL = sm.tile_l;
             sm.run_l = run_l + tl;
-            sm.run_sl += tsl;
-            sm.run_sh += tsh;
+            sm.run_sl = run_sl + TL;
+            sm.run_sh = run_sh + (Tall - TL);
         }
     }
     __syncthreads();
