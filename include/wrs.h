@@ -97,7 +97,7 @@ typedef struct wrs_build_info {
     double avg;       /* W / N in FP64: the bucket size (Sec. 2.2) */
     uint64_t nl;      /* number of light items, w_i <= avg */
     uint64_t nh;      /* number of heavy items, w_i > avg */
-    uint32_t Q[4];    /* bucket size in fixed point (128-bit, low limb first) */
+    uint32_t Q[4];    /* bucket in fixed point: sum of all q_i (Q[0] low word, Q[2..3] = 0) */
     float light_max;  /* largest FP32 value <= avg: light iff w_i <= light_max */
     uint32_t sections;/* number of pack sections s */
     uint64_t reserved[4];
@@ -117,17 +117,21 @@ int wrs_build_workspace_bytes(uint64_t n, const wrs_config *cfg,
  *           from the front (entry a = l[a]), heavy items in index order from
  *           the back (entry n-1-b = h[b])  (Sec. 4.2 "weight in l and h").
  *   ckl:    checkpoints of the light prefix sums, one per 32 entries: record c
- *           (16 bytes) = {uint32 seg, uint32 s[3]} where s is the 96-bit sum of
- *           the fixed-point weights q of l[0..32c) that lie in partition
+ *           (16 bytes) = {uint32 seg, uint32 pad, uint64 s} where s is the sum
+ *           of the fixed-point weights q of l[0..32c) that lie in partition
  *           segment `seg`; the sum over the earlier segments is seg_pre[seg].
  *   ckh:    the same for the heavy list h.
  *   seg_pre: segment prefixes, 48 bytes each: {uint32 sl[4], uint32 sh[4],
- *           uint64 nl, uint64 pad}: 128-bit q sums of the light and heavy
- *           items before the segment and its number of light items before it.
+ *           uint64 nl, uint64 pad}: q sums (128-bit fields, values < 2^64)
+ *           of the light and heavy items before the segment and the number
+ *           of light items before it.
  *   splits: s+1 records {uint32 i, uint32 j, uint32 pad[2], uint32 D[4],
  *           uint32 E[4]}: the Vose state after t*section_size buckets
  *           (Sec. 2.2 split).
- * With Q (wrs_build_info.Q) the bucket in fixed point and sigma the q sums:
+ * Fixed point: q_i = round(w_i * 2^S) (S = wrs_build_info.scale, so that
+ * W*2^S lies in [2^61, 2^62)); the bucket Q = wrs_build_info.Q is the exact
+ * sum of all q_i.  With sigma the q sums (light items clamped to at most
+ * floor(Q/N), heavy items to at least floor(Q/N)+1):
  *   D'(i) = i*Q - N*sigma_l(i)  (N times the light deficit before l[i]) and
  *   E'(j) = N*sigma_h(j) - j*Q  (N times the heavy excess before h[j]);
  *   split record t holds D = D'(i_t), E = E'(j_t). */

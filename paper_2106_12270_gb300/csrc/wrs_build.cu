@@ -25,14 +25,17 @@
 //                        excess prefix E' (Sec. 2.2 "pack"), staged in shared
 //                        memory (Sec. 4.2), writing rows by item index.
 //
-// Fixed point.  With Q = round(W 2^S) in [2^93, 2^94] a bucket is Q units.
-// For light items d'_a = Q - N q_a >= 0 (its deficit times N) and for heavy
+// Fixed point.  q_i = round(w_i 2^S) < 2^63 with W 2^S in [2^61, 2^62); the
+// bucket is Q = sum of all q_i (exactly, so deficits and excesses balance).
+// For light items d'_a = Q - N q_a >= 0 (N times its deficit) and for heavy
 // items e'_b = N q_b - Q > 0.  D'(i) = sum of the first i light d', E'(j) =
-// sum of the first j heavy e' (both < 2^126).  The sweep closes heavy h[j]
+// sum of the first j heavy e' (both < 2^94).  The sweep closes heavy h[j]
 // (its remaining weight fits in one bucket) iff E'(j+1) <= D'(i), else light
 // l[i]; a heavy row keeps 1 - (D'(i) - E'(j+1)) / Q of its bucket.  All of it
 // is exact integer arithmetic: the splits and every section end agree
-// exactly, and no FP64 unit is used per item.
+// exactly, and no FP64 unit is used per item.  The rounding of q costs at
+// most N/(2Q) <= 2^-32 of a bucket per item, far below the FP32 rounding of
+// the stored probabilities.
 #include <stdio.h>
 
 #include "wrs_internal.cuh"
@@ -52,6 +55,7 @@ Layout make_layout(uint64_t n, uint32_t S) {
     L.params = take(sizeof(BuildParams));
     L.sum_bins = take((uint64_t)kSumMaxBlocks * kBands * sizeof(u128));
     L.seg_cnt = take((uint64_t)kMaxSegs * 4);
+    L.seg_q = take((uint64_t)kMaxSegs * 8);
     L.seg_sum = take((uint64_t)kMaxSegs * sizeof(SegVal));
     L.seg_pre = take((uint64_t)(kMaxSegs + 1) * sizeof(SegVal));
     L.lh = take(n * sizeof(Entry));
@@ -211,20 +215,13 @@ k_total(const u128 *__restrict__ bins_in, int nblocks, uint64_t n, uint32_t sect
     uint64_t bits = ((uint64_t)(t + 873) << 52) | (mant & ((1ull << 52) - 1));
     double W = __longlong_as_double((long long)bits);
     double avg = W / (double)n;
-    // Q = round(W_exact * 2^(243 - top)) in [2^93, 2^94]
-    u128 Q = big_bits(big, top - 93, 94);
-    if (top >= 94) Q += big_bits(big, top - 94, 1);
-    P->Q = Q;
-    P->Qn = Q / (u128)n;
-    P->NQn = (u128)n * P->Qn;
-    P->NQn1 = P->NQn + (u128)n;
+    // q_i = round(w_i 2^S) with W 2^S in [2^61, 2^62): S = 211 - top
     P->W = W;
     P->avg = avg;
-    P->scale = 243 - top;
-    P->qshift = 93 - top;
+    P->scale = 211 - top;
+    P->qshift = 61 - top;
     P->light_max = __double2float_rd(avg);
     P->inv_avg = __double2float_rn(1.0 / avg);
-    P->Qf = __ull2float_rn((unsigned long long)(Q >> 62));
 }
 
 // ===========================================================================
@@ -259,17 +256,22 @@ __device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *red) {
     return r;
 }
 
-// Light items per segment (one CTA per segment, coalesced 16-byte loads).
+// Per segment (one CTA each, coalesced 16-byte loads): the number of light
+// items and the sum of q over all items (light and heavy, unclamped).
 __global__ void __launch_bounds__(kPartThreads)
 k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__ P,
-        uint32_t *__restrict__ seg_cnt, uint64_t T, uint32_t G, int aligned) {
+        uint32_t *__restrict__ seg_cnt, uint64_t *__restrict__ seg_q, uint64_t T, uint32_t G,
+        int aligned) {
     __shared__ uint32_t red[32];
+    __shared__ uint64_t redq[32];
     if (P->status) return;
     const float lmax = P->light_max;
+    const int qshift = P->qshift;
     uint64_t t0, t1;
     seg_tiles(blockIdx.x, G, T, t0, t1);
     const uint64_t a = t0 * kTile, b = min(t1 * kTile, n);
     uint32_t cnt = 0;
+    uint64_t qs = 0;
     uint64_t tail = a;
     if (aligned) {
         const float4 *w4 = reinterpret_cast<const float4 *>(w);
@@ -278,27 +280,65 @@ k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__
         for (uint64_t i = a / 4 + threadIdx.x; i < b4; i += kPartThreads) {
             float4 v = __ldg(w4 + i);
             cnt += (v.x <= lmax) + (v.y <= lmax) + (v.z <= lmax) + (v.w <= lmax);
+            qs += fixed_q(v.x, qshift) + fixed_q(v.y, qshift) + fixed_q(v.z, qshift) +
+                  fixed_q(v.w, qshift);
         }
         tail = b4 * 4 > a ? b4 * 4 : a;
     }
-    for (uint64_t i = tail + threadIdx.x; i < b; i += kPartThreads) cnt += (__ldg(w + i) <= lmax);
+    for (uint64_t i = tail + threadIdx.x; i < b; i += kPartThreads) {
+        float x = __ldg(w + i);
+        cnt += (x <= lmax);
+        qs += fixed_q(x, qshift);
+    }
+    // block sums (q: each thread's sum < 2^63, the segment's too)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, d);
+    if (lane == 0) redq[warp] = qs;
     cnt = block_sum_u32(cnt, red);
-    if (threadIdx.x == 0) seg_cnt[blockIdx.x] = cnt;
+    if (threadIdx.x == 0) {
+        uint64_t t = 0;
+        for (int k = 0; k < kPartThreads / 32; ++k) t += redq[k];
+        seg_cnt[blockIdx.x] = cnt;
+        seg_q[blockIdx.x] = t;
+    }
+}
+
+// One CTA: Q = sum of all q (the bucket in fixed point) and its derived
+// constants.
+__global__ void __launch_bounds__(kMaxSegs)
+k_qsum(BuildParams *__restrict__ P, const uint64_t *__restrict__ seg_q, uint32_t G, uint64_t n) {
+    __shared__ uint64_t red[32];
+    if (P->status) return;
+    uint64_t v = threadIdx.x < G ? seg_q[threadIdx.x] : 0ull;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    uint64_t Q = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) Q += red[k];
+    P->Q = Q;
+    P->Qn = Q / n;
+    P->NQn = (u128)P->Qn * n;
+    P->NQn1 = P->NQn + n;
+    P->Qf = __ull2float_rn(Q);
+    P->nseg = G;
 }
 
 struct ScatterShared {
     float wv[kTile + kTile / 32];       // staged weights (padded, conflict-free)
     Entry e[kTile + kTile / 16];        // staged entries in list order (padded)
-    u128 wsum[kPartThreads / 32];       // per-warp q totals of the list-order pass
+    uint64_t wsum[kPartThreads / 32];   // per-warp q totals of the list-order pass
     uint32_t wnl[kPartThreads / 32];    // per-warp light counts
-    u128 tile_l;                        // q sum of the tile's lights
-    u128 run_sl, run_sh;                // segment-local q sums before the tile
+    uint64_t tile_l;                    // q sum of the tile's lights
+    uint64_t run_sl, run_sh;            // segment-local q sums before the tile
     uint64_t run_l;                     // global light rank of the tile's first light
     uint32_t red[32];
 };
 
-__device__ __forceinline__ void put_ck(CkRec *ck, uint64_t idx, uint32_t seg, u128 v) {
-    uint4 r = make_uint4(seg, (uint32_t)v, (uint32_t)(v >> 32), (uint32_t)(v >> 64));
+__device__ __forceinline__ void put_ck(CkRec *ck, uint64_t idx, uint32_t seg, uint64_t v) {
+    uint4 r = make_uint4(seg, 0u, (uint32_t)v, (uint32_t)(v >> 32));
     *reinterpret_cast<uint4 *>(ck + idx) = r;
 }
 
@@ -326,7 +366,7 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
     uint64_t t0, t1;
     seg_tiles(g, G, T, t0, t1);
     const int qshift = P->qshift;
-    const u128 Qn = P->Qn;
+    const uint64_t Qn = P->Qn;
     const float lmax = P->light_max;
 
     uint32_t pre = 0;
@@ -409,42 +449,42 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
         __syncthreads();
         // ---- list-order q pass: slots [s0, s0+16) of this thread
         const uint32_t hstart = kTile - tnh;   // first heavy slot
-        const int cl = (int)((32u - (uint32_t)(run_l & 31u)) & 31u);      // light ckpt slots = cl mod 32
-        const int ch = (int)((uint32_t)(run_h + kTile - 1) & 31u);      // heavy ckpt slots = ch mod 32
+        const int cl = (int)((32u - (uint32_t)(run_l & 31u)) & 31u);   // light ckpt slots = cl mod 32
+        const int ch = (int)((uint32_t)(run_h + kTile - 1) & 31u);   // heavy ckpt slots = ch mod 32
         const int kl = (cl - s0) & 31;    // local index of this thread's light ckpt slot (if < 16)
         const int kh = (ch - s0) & 31;
         const int kb = (int)tl - s0;      // local index of the light/heavy boundary
-        u128 acc = 0, snap_l = 0, snap_h = 0, snap_b = 0;
+        uint64_t acc = 0, snap_l = 0, snap_h = 0, snap_b = 0;
 #pragma unroll
         for (int k = 0; k < kPartItems; ++k) {
             uint32_t slot = (uint32_t)(s0 + k);
             if (k == kl) snap_l = acc;
             if (k == kb) snap_b = acc;
-            u128 v = 0;
+            uint64_t v = 0;
             if (slot < tl) v = light_q(sm.e[pad16(slot)].w, qshift, Qn);
             else if (slot >= hstart) v = heavy_q(sm.e[pad16(slot)].w, qshift, Qn);
             acc += v;
             if (k == kh) snap_h = acc;    // inclusive of the heavy ckpt slot
         }
         // block exclusive scan of the thread totals
-        u128 inc = acc;
+        uint64_t inc = acc;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            u128 o = shfl_up_u128(inc, d);
+            uint64_t o = __shfl_up_sync(0xffffffffu, inc, d);
             if (lane >= d) inc += o;
         }
         if (lane == 31) sm.wsum[warp] = inc;
         __syncthreads();
-        u128 X = inc - acc, Tall = 0;
+        uint64_t X = inc - acc, Tall = 0;
 #pragma unroll
         for (int k = 0; k < kPartThreads / 32; ++k) {
-            u128 c = sm.wsum[k];
-            X += (k < warp) ? c : (u128)0;
+            uint64_t c = sm.wsum[k];
+            X += (k < warp) ? c : 0ull;
             Tall += c;
         }
         if (kb >= 0 && kb < kPartItems) sm.tile_l = X + snap_b;
         if (tl == (uint32_t)kTile && tid == 0) sm.tile_l = Tall;
-        const u128 run_sl = sm.run_sl, run_sh = sm.run_sh;
+        const uint64_t run_sl = sm.run_sl, run_sh = sm.run_sh;
         if (kl < kPartItems && (uint32_t)(s0 + kl) < tl)
             put_ck(ckl, (run_l + s0 + kl) >> 5, g, run_sl + X + snap_l);
         if (kh < kPartItems && (uint32_t)(s0 + kh) >= hstart)
@@ -457,7 +497,7 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
             lh2[n - 1 - (run_h + b)] = e2[pad16(kTile - 1 - b)];
         __syncthreads();   // tile_l written
         if (tid == 0) {
-            u128 TL = sm.tile_l;
+            uint64_t TL = sm.tile_l;
             sm.run_l = run_l + tl;
             sm.run_sl = run_sl + TL;
             sm.run_sh = run_sh + (Tall - TL);
@@ -481,36 +521,34 @@ __global__ void __launch_bounds__(kMaxSegs)
 k_segscan(BuildParams *__restrict__ P, const uint32_t *__restrict__ seg_cnt,
           const SegVal *__restrict__ seg_sum, SegVal *__restrict__ seg_pre,
           CkRec *__restrict__ ckl, CkRec *__restrict__ ckh, uint64_t n, uint32_t G) {
-    __shared__ SegVal wtot[kMaxSegs / 32];
+    __shared__ uint64_t wc[kMaxSegs / 32], wl[kMaxSegs / 32], wh[kMaxSegs / 32];
     if (P->status) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    uint64_t c = 0;
-    u128 sl = 0, sh = 0;
+    uint64_t c = 0, sl = 0, sh = 0;
     if ((uint32_t)tid < G) {
         c = seg_cnt[tid];
-        sl = seg_sum[tid].sl;
-        sh = seg_sum[tid].sh;
+        sl = (uint64_t)seg_sum[tid].sl;
+        sh = (uint64_t)seg_sum[tid].sh;
     }
-    uint64_t ic = c;
-    u128 isl = sl, ish = sh;
+    uint64_t ic = c, isl = sl, ish = sh;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         uint64_t c2 = __shfl_up_sync(0xffffffffu, ic, d);
-        u128 a2 = shfl_up_u128(isl, d), b2 = shfl_up_u128(ish, d);
+        uint64_t a2 = __shfl_up_sync(0xffffffffu, isl, d);
+        uint64_t b2 = __shfl_up_sync(0xffffffffu, ish, d);
         if (lane >= d) { ic += c2; isl += a2; ish += b2; }
     }
     if (lane == 31) {
-        wtot[warp].nl = ic;
-        wtot[warp].sl = isl;
-        wtot[warp].sh = ish;
+        wc[warp] = ic;
+        wl[warp] = isl;
+        wh[warp] = ish;
     }
     __syncthreads();
-    uint64_t pc = ic - c;
-    u128 psl = isl - sl, psh = ish - sh;
+    uint64_t pc = ic - c, psl = isl - sl, psh = ish - sh;
     for (int k = 0; k < warp; ++k) {
-        pc += wtot[k].nl;
-        psl += wtot[k].sl;
-        psh += wtot[k].sh;
+        pc += wc[k];
+        psl += wl[k];
+        psh += wh[k];
     }
     if ((uint32_t)tid <= G) {
         SegVal v;
@@ -522,12 +560,12 @@ k_segscan(BuildParams *__restrict__ P, const uint32_t *__restrict__ seg_cnt,
     }
     if ((uint32_t)tid == G) {
         // thread G holds the totals (its own value is zero)
-        const u128 Q = P->Q, N = (u128)n;
-        uint64_t nl = pc, nh = n - nl;
+        const uint64_t Q = P->Q;
+        const uint64_t nl = pc, nh = n - nl;
         P->nl = nl;
         P->nh = nh;
-        P->Dtot = (u128)nl * Q - N * psl;
-        P->Etot = N * psh - (u128)nh * Q;
+        P->Dtot = (u128)nl * Q - (u128)psl * n;
+        P->Etot = (u128)psh * n - (u128)nh * Q;
         if ((nl & 31u) == 0) put_ck(ckl, nl >> 5, G, 0);
         if ((nh & 31u) == 0) put_ck(ckh, nh >> 5, G, 0);
     }
@@ -542,27 +580,22 @@ struct SplitCtx {
     const SegVal *seg_pre;
     const Entry *lh;
     uint64_t n, nl, nh;
-    u128 Q;
+    uint64_t Q;
 };
-
-__device__ __forceinline__ u128 ld128(const u128 *p) {
-    ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p));
-    return ((u128)v.y << 64) | v.x;
-}
 
 // D'(32c) = 32c*Q - N*(q sum of the first 32c light entries).
 __device__ __forceinline__ u128 ck_D(const SplitCtx &C, uint64_t c) {
     uint4 r = __ldg(reinterpret_cast<const uint4 *>(C.ckl + c));
-    u128 local = ((u128)r.w << 64) | ((u128)r.z << 32) | r.y;
-    u128 sig = ld128(&C.seg_pre[r.x].sl) + local;
-    return (u128)(32 * c) * C.Q - (u128)C.n * sig;
+    uint64_t local = ((uint64_t)r.w << 32) | r.z;
+    uint64_t sig = __ldg(reinterpret_cast<const unsigned long long *>(&C.seg_pre[r.x].sl)) + local;
+    return (u128)(32 * c) * C.Q - (u128)sig * C.n;
 }
 // E'(32c) = N*(q sum of the first 32c heavy entries) - 32c*Q.
 __device__ __forceinline__ u128 ck_E(const SplitCtx &C, uint64_t c) {
     uint4 r = __ldg(reinterpret_cast<const uint4 *>(C.ckh + c));
-    u128 local = ((u128)r.w << 64) | ((u128)r.z << 32) | r.y;
-    u128 sig = ld128(&C.seg_pre[r.x].sh) + local;
-    return (u128)C.n * sig - (u128)(32 * c) * C.Q;
+    uint64_t local = ((uint64_t)r.w << 32) | r.z;
+    uint64_t sig = __ldg(reinterpret_cast<const unsigned long long *>(&C.seg_pre[r.x].sh)) + local;
+    return (u128)sig * C.n - (u128)(32 * c) * C.Q;
 }
 
 // P(32c) for bucket count k: monotone in c; false below the valid range of
@@ -603,11 +636,11 @@ __device__ void split_fine(const SplitCtx &C, const BuildParams &Pm, uint64_t k,
         u128 d = 0, e = 0;
         if (lb + lane < C.nl) {
             Entry en = C.lh[lb + lane];
-            d = Pm.Q - light_nq(en.w, Pm.qshift, N, Pm.NQn);
+            d = (u128)(Pm.Q - N * light_q(en.w, Pm.qshift, Pm.Qn));   // <= Q
         }
         if (hb + lane < C.nh) {
             Entry en = C.lh[C.n - 1 - (hb + lane)];
-            e = heavy_nq(en.w, Pm.qshift, N, Pm.NQn1) - Pm.Q;
+            e = mul_nq(N, heavy_q(en.w, Pm.qshift, Pm.Qn)) - Pm.Q;
         }
         u128 dinc = d, einc = e;
 #pragma unroll
@@ -761,7 +794,7 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
     const int tid = threadIdx.x;
     const uint32_t t = blockIdx.x;
     const uint64_t nh = P->nh;
-    const u128 Q = P->Q, NQn = P->NQn, NQn1 = P->NQn1;
+    const uint64_t Q = P->Q, Qn = P->Qn;
     const uint32_t N = (uint32_t)n;
     const int qshift = P->qshift;
     const float inv_avg = P->inv_avg, Qf = P->Qf;
@@ -793,7 +826,8 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
         uint32_t e = b0 + k;
         if (e >= K) break;
         float wv = sW[pad32(e)];
-        u128 val = (e < L) ? Q - light_nq(wv, qshift, N, NQn) : heavy_nq(wv, qshift, N, NQn1) - Q;
+        u128 val = (e < L) ? (u128)(Q - (uint64_t)N * light_q(wv, qshift, Qn))
+                           : mul_nq(N, heavy_q(wv, qshift, Qn)) - Q;
         sP[pp8(e + 1)] = val;
         run += val;
     }
@@ -846,8 +880,8 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
                 if (b > a) {
                     prob = 1.0f;      // rounding left more excess than deficit
                 } else {
-                    u128 delta = a - b;   // < Q
-                    float df = __ull2float_rn((unsigned long long)(delta >> 62));
+                    uint64_t delta = (uint64_t)(a - b);   // < Q < 2^63
+                    float df = __ull2float_rn(delta);
                     prob = fminf(fmaxf(1.0f - __fdiv_rn(df, Qf), 0.0f), 1.0f);
                 }
                 alias = sItem[L + y + 1];
@@ -888,7 +922,9 @@ __global__ void k_info(const BuildParams *__restrict__ P, wrs_build_info *__rest
     r.avg = P->avg;
     r.nl = P->nl;
     r.nh = P->nh;
-    for (int k = 0; k < 4; ++k) r.Q[k] = (uint32_t)(P->Q >> (32 * k));
+    r.Q[0] = (uint32_t)P->Q;
+    r.Q[1] = (uint32_t)(P->Q >> 32);
+    r.Q[2] = r.Q[3] = 0;
     r.light_max = P->light_max;
     r.sections = P->sections;
     for (int k = 0; k < 4; ++k) r.reserved[k] = 0;
@@ -936,6 +972,7 @@ cudaError_t launch_partition(const float *d_w, uint64_t n, unsigned char *ws, co
                              cudaStream_t st) {
     BuildParams *P = reinterpret_cast<BuildParams *>(ws + L.params);
     auto *cnt = reinterpret_cast<uint32_t *>(ws + L.seg_cnt);
+    auto *segq = reinterpret_cast<uint64_t *>(ws + L.seg_q);
     auto *sum = reinterpret_cast<SegVal *>(ws + L.seg_sum);
     auto *pre = reinterpret_cast<SegVal *>(ws + L.seg_pre);
     auto *lh = reinterpret_cast<Entry *>(ws + L.lh);
@@ -943,7 +980,8 @@ cudaError_t launch_partition(const float *d_w, uint64_t n, unsigned char *ws, co
     auto *ckh = reinterpret_cast<CkRec *>(ws + L.ckh);
     const uint32_t G = num_segments(L);
     const int aligned = ((uintptr_t)d_w % 16) == 0;
-    k_count<<<G, kPartThreads, 0, st>>>(d_w, n, P, cnt, L.ntiles, G, aligned);
+    k_count<<<G, kPartThreads, 0, st>>>(d_w, n, P, cnt, segq, L.ntiles, G, aligned);
+    k_qsum<<<1, kMaxSegs, 0, st>>>(P, segq, G, n);
     if (aligned)
         k_scatter<true><<<G, kPartThreads, 0, st>>>(d_w, n, P, cnt, lh, ckl, ckh, sum, L.ntiles, G);
     else

@@ -28,28 +28,32 @@ enum : uint32_t {
 constexpr uint32_t kSpinLimit = 1u << 20;
 
 // ---------------------------------------------------------------------------
-// Build parameters, computed on the device by the total-weight step and read
-// by every later step.  Lives at the start of the build workspace.
+// Build parameters, computed on the device by the total-weight and q-sum
+// steps and read by every later step.  Lives at the start of the workspace.
+//
+// Fixed point: q_i = round(w_i * 2^S) with S chosen so that W*2^S lies in
+// [2^61, 2^62); every q_i fits 64 bits.  The bucket Q is the exact sum of the
+// q_i, so the scaled light deficits and heavy excesses balance exactly.
 // ---------------------------------------------------------------------------
 struct __align__(16) BuildParams {
-    u128 Q;            // bucket size W*2^S in fixed point, in [2^93, 2^94]
-    u128 Qn;           // floor(Q / N)
     u128 Dtot;         // D'(nl): total scaled light deficit
     u128 Etot;         // E'(nh): total scaled heavy excess
-    u128 NQn;          // N * Qn: largest N*q a light item may have
-    u128 NQn1;         // N * (Qn + 1): smallest N*q a heavy item may have
+    u128 NQn;          // N * Qn
+    u128 NQn1;         // N * (Qn + 1)
     double W;          // exact total weight rounded to FP64
     double avg;        // W / N
+    uint64_t Q;        // sum of all q_i: one bucket in fixed point (< 2^63)
+    uint64_t Qn;       // floor(Q / N): largest q a light item may carry
     uint64_t n;
-    uint64_t nl, nh;   // written by the last partition tile
+    uint64_t nl, nh;   // written by the segment scan
     uint32_t status;   // ERR_* bits
     int32_t scale;     // S
     int32_t qshift;    // q_i = m_i * 2^(e'_i + qshift) (e' = max(biased exp, 1))
     float light_max;   // largest FP32 <= avg
     float inv_avg;     // (float)(1 / avg)
-    float Qf;          // (float)(Q >> 62)
+    float Qf;          // (float)Q
     uint32_t sections; // s
-    uint32_t pad;
+    uint32_t nseg;     // partition segments
 };
 
 // Workspace layout (all offsets 256-byte aligned).
@@ -57,7 +61,8 @@ struct Layout {
     uint64_t params;     // BuildParams
     uint64_t sum_bins;   // kSumMaxBlocks * kBands u128
     uint64_t seg_cnt;    // kMaxSegs uint32 light counts per segment
-    uint64_t seg_sum;    // kMaxSegs SegVal (segment q sums)
+    uint64_t seg_q;      // kMaxSegs uint64 q sums per segment (all items)
+    uint64_t seg_sum;    // kMaxSegs SegVal (segment clamped q sums)
     uint64_t seg_pre;    // (kMaxSegs + 1) SegVal (exclusive prefixes)
     uint64_t lh;         // n Entry
     uint64_t ckl;        // (n/32 + 2) CkRec
@@ -74,8 +79,8 @@ struct __align__(8) Entry {   // one slot of the l/h array
 };
 
 struct __align__(16) SegVal {   // per-segment partition sums / prefixes
-    u128 sl;      // sum of light q (clamped)
-    u128 sh;      // sum of heavy q (clamped)
+    u128 sl;      // sum of light q (clamped); < 2^64
+    u128 sh;      // sum of heavy q (clamped); < 2^64
     uint64_t nl;  // light count
     uint64_t pad;
 };
@@ -85,7 +90,8 @@ struct __align__(16) SegVal {   // per-segment partition sums / prefixes
 // it (the segment's own prefix is in seg_pre).
 struct __align__(16) CkRec {
     uint32_t seg;
-    uint32_t s[3];   // 96-bit local q sum (< 2^95)
+    uint32_t pad;
+    uint64_t s;   // local q sum
 };
 
 struct __align__(16) SplitRec {  // Vose state after k_t buckets
@@ -128,68 +134,34 @@ __device__ __forceinline__ u128 shfl_u128(u128 v, int src) {
     return ((u128)hi << 64) | lo;
 }
 
-// v << s as a 128-bit value, for v < 2^64 and s in [0, 127].
-__device__ __forceinline__ u128 shl_u64(uint64_t v, uint32_t s) {
-    uint64_t lo, hi;
-    if (s < 64) {
-        lo = v << s;
-        hi = s ? (v >> (64 - s)) : 0ull;
-    } else {
-        lo = 0ull;
-        hi = v << (s - 64);
-    }
-    return ((u128)hi << 64) | lo;
-}
-
-// Fixed point of an FP32 weight: q = round(w * 2^S) = t << s with t < 2^24.
-// w = m * 2^(e'-150) (e' = max(biased exponent, 1)), so q = m * 2^(e' +
-// qshift); a negative exponent rounds half up.  The weight must be finite
-// (checked by the total-weight step before any caller runs); the sign bit is
-// ignored (-0 is 0).
-__device__ __forceinline__ void fixed_parts(float w, int qshift, uint32_t &t, uint32_t &s) {
+// Fixed point of an FP32 weight: q = round(w * 2^S) < 2^63.  With
+// w = m * 2^(e'-150) (e' = max(biased exponent, 1)), q = m * 2^(e' + qshift);
+// a negative exponent rounds half up.  The weight must be finite (checked by
+// the total-weight step before any caller runs); the sign bit is ignored
+// (-0 is 0).
+__device__ __forceinline__ uint64_t fixed_q(float w, int qshift) {
     uint32_t u = __float_as_uint(w) & 0x7fffffffu;
     uint32_t e = u >> 23;
     uint32_t m = (u & 0x7fffffu) | (e ? 0x800000u : 0u);
     int sh = (int)(e ? e : 1u) + qshift;
-    if (sh >= 0) {
-        t = m;
-        s = (uint32_t)sh;
-    } else {
-        int r = -sh;
-        t = r > 24 ? 0u : ((m + (1u << (r - 1))) >> r);
-        s = 0;
-    }
+    if (sh >= 0) return (uint64_t)m << sh;   // sh <= 39 for every weight <= W
+    int r = -sh;
+    return r > 24 ? 0ull : (uint64_t)((m + (1u << (r - 1))) >> r);
 }
 
-// q of a light item, clamped to at most Qn = floor(Q/N) so that its scaled
-// deficit d' = Q - N*q is >= 0; q of a heavy item, clamped to at least Qn+1
-// so that its scaled excess e' = N*q - Q is > 0.
-__device__ __forceinline__ u128 light_q(float w, int qshift, u128 Qn) {
-    uint32_t t, s;
-    fixed_parts(w, qshift, t, s);
-    u128 q = shl_u64(t, s);
+// q of a light item clamped to at most Qn = floor(Q/N), so that its scaled
+// deficit d' = Q - N*q >= 0; q of a heavy item clamped to at least Qn+1, so
+// that its scaled excess e' = N*q - Q > 0.
+__device__ __forceinline__ uint64_t light_q(float w, int qshift, uint64_t Qn) {
+    uint64_t q = fixed_q(w, qshift);
     return q > Qn ? Qn : q;
 }
-__device__ __forceinline__ u128 heavy_q(float w, int qshift, u128 Qn) {
-    uint32_t t, s;
-    fixed_parts(w, qshift, t, s);
-    u128 q = shl_u64(t, s);
+__device__ __forceinline__ uint64_t heavy_q(float w, int qshift, uint64_t Qn) {
+    uint64_t q = fixed_q(w, qshift);
     return q <= Qn ? Qn + 1 : q;
 }
-// N*q directly (one 32x32->64 product, then a shift), with the same clamps:
-// N*q_light <= NQn = N*Qn and N*q_heavy >= NQn1 = N*(Qn+1).
-__device__ __forceinline__ u128 light_nq(float w, int qshift, uint32_t N, u128 NQn) {
-    uint32_t t, s;
-    fixed_parts(w, qshift, t, s);
-    u128 v = shl_u64((uint64_t)N * t, s);
-    return v > NQn ? NQn : v;
-}
-__device__ __forceinline__ u128 heavy_nq(float w, int qshift, uint32_t N, u128 NQn1) {
-    uint32_t t, s;
-    fixed_parts(w, qshift, t, s);
-    u128 v = shl_u64((uint64_t)N * t, s);
-    return v < NQn1 ? NQn1 : v;
-}
+// N * q as 128 bits (q < 2^63, N < 2^31).
+__device__ __forceinline__ u128 mul_nq(uint32_t N, uint64_t q) { return (u128)q * N; }
 
 // ---------------------------------------------------------------------------
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two

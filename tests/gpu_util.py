@@ -66,8 +66,7 @@ class Built:
         segs = raw[:, 0].astype(np.int64)
         pre = self.seg_pre(int(segs.max()) if cnt else 0)
         col = 0 if which == "ckl" else 1
-        return [pre[int(r[0])][col] + (int(r[1]) | int(r[2]) << 32 | int(r[3]) << 64)
-                for r in raw]
+        return [pre[int(r[0])][col] + (int(r[2]) | int(r[3]) << 32) for r in raw]
 
     def splits(self):
         s = self.layout["sections"]

@@ -2,9 +2,9 @@
 
 Every step runs through the C ABI (libwrs.so).  Tolerances:
 * total weight W, light/heavy counts, the l/h lists: bit-exact;
-* prefix-sum checkpoints: within 1e-12 (relative, at least 1 bucket) of the
-  exact rational prefix sums -- the fixed point rounds each weight to
-  2^-S with Q = W 2^S >= 2^93, so the error is below N^2 / 2^93 buckets;
+* prefix-sum checkpoints: within N (i + N) / Q buckets of the exact rational
+  prefix sums -- the fixed point rounds each weight to 2^-S (half a unit),
+  Q = sum of the rounded weights >= 2^61;
 * splits: equal to the oracle's PSA splits (FP64 binary search);
 * table: |mass_i - N w_i/W| <= 1e-5 max(1, N w_i/W) (the stated bound for
   FP32 tables) and agreement with the oracle's PSA rows.
@@ -88,7 +88,7 @@ def test_prefix_checkpoints_exact(kind):
             # exact: i - sigma N/W and sigma N/W - i
             got = sign * Fraction(i * Q - n * sig_q, Q)
             want = sign * (i - sig * n / Wx)
-            assert abs(got - want) <= Fraction(1, 10**12) * max(1, abs(want)), (which, c)
+            assert abs(got - want) <= Fraction(n * (i + n), Q), (which, c)
 
 
 @pytest.mark.parametrize("kind", KINDS)
