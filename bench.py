@@ -286,6 +286,27 @@ def run_gpu(args):
                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n,
                "ms_per_step": e2e_ms}
 
+    # sectioned sampling (Sec. 5): same draw count, samples grouped by section
+    sec = {}
+    for mode, name, rows_per in ((wrs.SAMPLE_CACHED, "cached", 8192),
+                                 (wrs.SAMPLE_LIMITED, "limited", 8192),
+                                 (wrs.SAMPLE_SMEM, "smem", 16384)):
+        nsec = wrs.sample_sections(n, rows_per)
+        cnt_t = torch.empty(nsec, dtype=torch.int64, device="cuda")
+        off_t = torch.empty(nsec, dtype=torch.int64, device="cuda")
+        wrs.sample_sectioned_rows(rows, n, count, 2, mode, rows_per, cnt_t, off_t, out)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            wrs.sample_sectioned_rows(rows, n, count, 2, mode, rows_per, cnt_t, off_t, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+        sec[name] = {"ms": ms, "samples_per_s": world * count / (ms / 1e3),
+                     "section_rows": rows_per}
+
     # random-gather probe: the naive sampler's access pattern alone (same
     # table size, same number of draws), best of the three load paths
     probe = {}
@@ -336,6 +357,7 @@ def run_gpu(args):
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
             "build_ms": build_ms, "sample_ms": sample_ms,
             "samples_per_s": world * count / (sample_ms / 1e3),
+            "sectioned_sampling": sec,
             "roofline": dominant, "build_roofline": build_roof, "sample_roofline": sample_roof,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": args.steps * (KERNELS_PER_BUILD + KERNELS_PER_SAMPLE),

@@ -197,6 +197,40 @@ int wrs_sample_rows(const wrs_row *d_rows, uint64_t n, uint64_t first,
                     uint64_t count, uint64_t seed, uint32_t stream_lo,
                     uint32_t stream_hi, uint32_t *d_out, void *stream);
 
+/* Sampling modes (Sec. 5): NAIVE draws each sample from the whole table;
+ * the sectioned modes first split the count over sections of the table and
+ * draw every section's samples inside it, so that its rows stay in cache:
+ * CACHED gathers rows through L1/L2, LIMITED additionally reserves shared
+ * memory so only one CTA runs per SM (fewer sections evict each other),
+ * SMEM copies each section's rows into shared memory first.  The three
+ * sectioned modes produce identical samples; they differ only in speed. */
+enum wrs_sample_mode {
+    WRS_SAMPLE_NAIVE = 0,
+    WRS_SAMPLE_CACHED = 1,
+    WRS_SAMPLE_LIMITED = 2,
+    WRS_SAMPLE_SMEM = 3
+};
+
+/* Number of sections for n rows with at most section_rows rows each:
+ * nsec = ceil(n / section_rows); section s covers rows
+ * [floor(s*n/nsec), floor((s+1)*n/nsec)). */
+int wrs_sample_sections(uint64_t n, uint32_t section_rows, uint64_t *nsec);
+
+/* a7: sectioned sampling (Sec. 5 "cached sectioned", "cached limited
+ * sectioned", "shared memory sectioned" sampling).  Draws `count` samples:
+ * d_counts[s] (device, nsec uint64) receives how many fall into section s
+ * (recursive binomial split keyed by (seed, tree node), normal
+ * approximation above 96 samples per node), d_offsets[s] the start of its
+ * samples in d_out; d_out[d_offsets[s] + q] is the q-th sample of section s
+ * (Walker's rule inside the section, counter (q/2, 0, s, WRS_TAG_SECTION)).
+ * The output is grouped by section, not in the order of naive sampling.
+ * section_rows: 1..2^31; SMEM mode needs section_rows <= 24576 (its rows
+ * live in shared memory). */
+int wrs_sample_sectioned_rows(const wrs_row *d_rows, uint64_t n, uint64_t count,
+                              uint64_t seed, uint32_t mode, uint32_t section_rows,
+                              uint64_t *d_counts, uint64_t *d_offsets, uint32_t *d_out,
+                              void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* Measurement support                                                     */
 /* ---------------------------------------------------------------------- */

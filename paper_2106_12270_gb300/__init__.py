@@ -28,6 +28,7 @@ __all__ = [
 
 OK, EINVAL, EZEROSUM, ENONFINITE, ENOMEM, ETIMEOUT, ECUDA, EBUSY, ENOTFOUND = range(9)
 SPLIT_PARY, SPLIT_BINARY = 0, 1
+SAMPLE_NAIVE, SAMPLE_CACHED, SAMPLE_LIMITED, SAMPLE_SMEM = 0, 1, 2, 3
 TAG_NAIVE, TAG_SECTION, TAG_COUNTS, TAG_BATCH = 0, 1, 2, 3
 ROW_BYTES = 8
 
@@ -81,6 +82,8 @@ def lib():
                 "wrs_step_info": (I, [U64, P, U64, CP, P, P]),
                 "wrs_sample_rows": (I, [P, U64, U64, U64, U64, U32, U32, P, P]),
                 "wrs_diag_random_gather": (I, [P, U64, U64, U64, I, P, P]),
+                "wrs_sample_sections": (I, [U64, U32, ctypes.POINTER(U64)]),
+                "wrs_sample_sectioned_rows": (I, [P, U64, U64, U64, U32, U32, P, P, P, P]),
                 "wrs_strerror": (ctypes.c_char_p, [I]),
                 "wrs_last_cuda_error": (I, []),
                 "wrs_abi_version": (I, []),
@@ -174,6 +177,21 @@ def sample_rows(rows, n: int, first: int, count: int, seed: int, out,
     (int32/uint32 [count], device)."""
     _check(lib().wrs_sample_rows(_ptr(rows), n, first, count, seed & (2**64 - 1), stream_lo,
                                  stream_hi, _ptr(out), _stream(stream)), "wrs_sample_rows")
+
+
+def sample_sections(n: int, section_rows: int) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().wrs_sample_sections(n, section_rows, ctypes.byref(out)), "wrs_sample_sections")
+    return out.value
+
+
+def sample_sectioned_rows(rows, n: int, count: int, seed: int, mode: int, section_rows: int,
+                          counts, offsets, out, stream=None):
+    """Enqueue sectioned sampling (Sec. 5): per-section counts/offsets
+    (int64 [nsec], device) and samples grouped by section in out."""
+    _check(lib().wrs_sample_sectioned_rows(_ptr(rows), n, count, seed & (2**64 - 1), mode,
+                                           section_rows, _ptr(counts), _ptr(offsets), _ptr(out),
+                                           _stream(stream)), "wrs_sample_sectioned_rows")
 
 
 def diag_random_gather(rows, nrows: int, count: int, seed: int, flavor: int, out, stream=None):

@@ -15,6 +15,8 @@ cudaError_t launch_pack(uint64_t, wrs_row *, unsigned char *, const Layout &, ui
 cudaError_t launch_info(unsigned char *, const Layout &, wrs_build_info *, cudaStream_t);
 cudaError_t launch_sample_naive(const wrs_row *, uint64_t, uint64_t, uint64_t, uint64_t,
                                 uint32_t, uint32_t, uint32_t *, cudaStream_t);
+cudaError_t launch_sample_sectioned(const wrs_row *, uint64_t, uint64_t, uint64_t, uint32_t,
+                                    uint64_t, uint64_t *, uint64_t *, uint32_t *, cudaStream_t);
 cudaError_t launch_random_gather(const void *, uint64_t, uint64_t, uint64_t, int, uint32_t *,
                                  cudaStream_t);
 
@@ -183,6 +185,28 @@ int wrs_sample_rows(const wrs_row *d_rows, uint64_t n, uint64_t first, uint64_t 
     if (first + count < first) return WRS_EINVAL;
     return cuda_status(launch_sample_naive(d_rows, n, first, count, seed, stream_lo, stream_hi,
                                            d_out, (cudaStream_t)stream));
+}
+
+int wrs_sample_sections(uint64_t n, uint32_t section_rows, uint64_t *nsec) {
+    if (!nsec || n == 0 || n > kMaxN || section_rows == 0) return WRS_EINVAL;
+    *nsec = (n + section_rows - 1) / section_rows;
+    return WRS_OK;
+}
+
+int wrs_sample_sectioned_rows(const wrs_row *d_rows, uint64_t n, uint64_t count, uint64_t seed,
+                              uint32_t mode, uint32_t section_rows, uint64_t *d_counts,
+                              uint64_t *d_offsets, uint32_t *d_out, void *stream) {
+    uint64_t nsec;
+    int rc = wrs_sample_sections(n, section_rows, &nsec);
+    if (rc) return rc;
+    if (!d_rows || ((uintptr_t)d_rows & 7u) || !d_counts || !d_offsets) return WRS_EINVAL;
+    if (((uintptr_t)d_counts & 7u) || ((uintptr_t)d_offsets & 7u)) return WRS_EINVAL;
+    if (count && (!d_out || ((uintptr_t)d_out & 3u))) return WRS_EINVAL;
+    if (mode < WRS_SAMPLE_CACHED || mode > WRS_SAMPLE_SMEM) return WRS_EINVAL;
+    if (mode == WRS_SAMPLE_SMEM && section_rows > 24576) return WRS_EINVAL;
+    if (nsec > 0x7fffffffull) return WRS_EINVAL;
+    return cuda_status(launch_sample_sectioned(d_rows, n, count, seed, mode, nsec, d_counts,
+                                               d_offsets, d_out, (cudaStream_t)stream));
 }
 
 int wrs_diag_random_gather(const wrs_row *d_rows, uint64_t nrows, uint64_t count, uint64_t seed,
