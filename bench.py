@@ -38,6 +38,7 @@ BUILD_BYTES_PER_ITEM = 32      # read w twice, write + read lh, write rows
 SAMPLE_BYTES_PER_DRAW = 36     # one 32-byte row sector + a 4-byte output
 KERNELS_PER_BUILD = 9          # sum, total, count, scatter, segscan, split ends, split, pack, info
 KERNELS_PER_SAMPLE = 1
+# batched build/sample are timed separately (extra keys), not in gpu_launches
 
 
 def parse():
@@ -51,6 +52,8 @@ def parse():
     ap.add_argument("--section", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-tables", type=int, default=100_000)
     return ap.parse_args()
 
 
@@ -322,6 +325,8 @@ def run_gpu(args):
         probe[flavor] = a.elapsed_time(b)
     probe_ms = min(probe.values())
 
+    batched = None if args.no_batched else run_batched(args, world, rank)
+
     hbm, peak_kind = peaks()
     build_gbs = BUILD_BYTES_PER_ITEM * n / (build_ms / 1e3) / 1e9
     sample_gbs = SAMPLE_BYTES_PER_DRAW * count / (sample_ms / 1e3) / 1e9
@@ -358,6 +363,7 @@ def run_gpu(args):
             "build_ms": build_ms, "sample_ms": sample_ms,
             "samples_per_s": world * count / (sample_ms / 1e3),
             "sectioned_sampling": sec,
+            "batched": batched,
             "roofline": dominant, "build_roofline": build_roof, "sample_roofline": sample_roof,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": args.steps * (KERNELS_PER_BUILD + KERNELS_PER_SAMPLE),
@@ -366,6 +372,83 @@ def run_gpu(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def run_batched(args, world, rank):
+    """Batched uneven tables: sizes log-uniform in [16, 65536] (seed 6),
+    Gamma(0.1, 1) weights, one batched build launch plus 1e3 samples per
+    table; compared with building the same tables one launch sequence at a
+    time (timed on the first tables and scaled to the whole batch)."""
+    import numpy as np
+    import torch
+
+    import paper_2106_12270_gb300 as wrs
+    from paper_2106_12270_gb300 import inputs
+
+    ntab = args.batch_tables
+    sizes = inputs.log_uniform_sizes(ntab, 6 + rank, 16, 65536)
+    off_np = np.zeros(ntab + 1, np.int64)
+    off_np[1:] = np.cumsum(sizes)
+    total = int(off_np[-1])
+    torch.cuda.manual_seed(7 + rank)
+    w = torch._standard_gamma(torch.full((total,), 0.1, device="cuda")).float()
+    off = torch.from_numpy(off_np).cuda()
+    rows = torch.empty(total, dtype=torch.int64, device="cuda")
+    order = torch.from_numpy(wrs.batch_order(off_np).astype(np.int32)).cuda()
+    bb = wrs.BatchBuilder(total, ntab)
+    per_table = 1000
+    cnt_off = torch.arange(0, (ntab + 1) * per_table, per_table, dtype=torch.int64, device="cuda")
+    out = torch.empty(ntab * per_table, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        bb.build(w, off, rows, order)
+        wrs.sample_batched_rows(rows, off, ntab, cnt_off, 2, out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    bms, sms = [], []
+    for _ in range(args.steps):
+        ev[0].record(stream)
+        bb.build(w, off, rows, order)
+        ev[1].record(stream)
+        wrs.sample_batched_rows(rows, off, ntab, cnt_off, 2, out)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        bms.append(ev[0].elapsed_time(ev[1]))
+        sms.append(ev[1].elapsed_time(ev[2]))
+    summ = bb.summaries()
+    ok = int((summ["status"] == wrs.OK).sum())
+    build_ms = statistics.mean(bms)
+    sample_ms = statistics.mean(sms)
+
+    # baseline: the plain single-table path, one launch sequence per table
+    probe = min(ntab, 2000)
+    b1 = wrs.Builder(65536)
+    r1 = torch.empty(65536, dtype=torch.int64, device="cuda")
+    for t in range(min(probe, 50)):
+        b1.build(w[off_np[t]:off_np[t + 1]], r1[: sizes[t]])
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for t in range(probe):
+        b1.build(w[off_np[t]:off_np[t + 1]], r1[: sizes[t]])
+    b.record(stream)
+    torch.cuda.synchronize()
+    probe_ms = a.elapsed_time(b)
+    frac = sizes[:probe].sum() / sizes.sum()
+    per_table_ms = probe_ms / frac
+    return {"tables": ntab, "items": total, "tables_ok": ok, "build_ms": build_ms,
+            "items_per_s": total / (build_ms / 1e3),
+            "build_gbs": 36 * total / (build_ms / 1e3) / 1e9,
+            "per_table_launch_ms": per_table_ms,
+            "per_table_probe": f"first {probe} tables timed, scaled by item share {frac:.4f}",
+            "speedup_vs_per_table": per_table_ms / build_ms,
+            "samples": ntab * per_table, "sample_ms": sample_ms,
+            "samples_per_s": ntab * per_table / (sample_ms / 1e3)}
 
 
 def main():

@@ -232,6 +232,49 @@ int wrs_sample_sectioned_rows(const wrs_row *d_rows, uint64_t n, uint64_t count,
                               void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Batches of independent tables (one launch for many tables)              */
+/* ---------------------------------------------------------------------- */
+
+/* Summary of one table of a batch (device-written, 32 bytes). */
+typedef struct wrs_table_summary {
+    int32_t status;   /* WRS_OK; WRS_EINVAL for an empty segment, a segment of
+                         more than 2^24 items or a negative weight;
+                         WRS_ENONFINITE; WRS_EZEROSUM */
+    uint32_t n;       /* items of the table */
+    double W;         /* exact total weight rounded to FP64 */
+    uint64_t nl, nh;  /* light and heavy counts */
+} wrs_table_summary;
+
+/* Device workspace bytes for a batch of `total` items (all tables). */
+int wrs_build_batched_workspace_bytes(uint64_t total, uint32_t ntab, uint64_t *bytes);
+
+/* Host-side plan: h_order receives the table ids largest first, the order in
+ * which the batched build hands tables to its persistent CTAs (longest job
+ * first keeps the CTAs evenly loaded).  h_off: ntab+1 host offsets. */
+int wrs_batch_order(const uint64_t *h_off, uint32_t ntab, uint32_t *h_order);
+
+/* a8: build ntab tables in one launch.  Table t has the weights
+ * d_w[d_off[t] .. d_off[t+1]) and gets the rows d_rows[d_off[t] ..
+ * d_off[t+1]) with table-local alias indices (PSA per table: exact total,
+ * partition, chunked sweep-pack, Sec. 2.2 and Sec. 4.2).  d_off: ntab+1
+ * device uint64 offsets, non-decreasing, d_off[0] = 0; d_order: ntab device
+ * table ids (a permutation, e.g. from wrs_batch_order) or NULL for 0..ntab-1;
+ * d_info: ntab device summaries.  A table with an error gets a status in its
+ * summary and its rows are left untouched; the others are still built. */
+int wrs_build_batched_rows(const float *d_w, const uint64_t *d_off, uint32_t ntab,
+                           const uint32_t *d_order, wrs_row *d_rows, void *d_ws,
+                           uint64_t ws_bytes, wrs_table_summary *d_info, void *stream);
+
+/* a9: sample many tables in one launch.  Samples d_cnt_off[t] ..
+ * d_cnt_off[t+1]-1 of d_out come from table t (rows at d_off[t]..) as
+ * table-local item indices; sample q of table t uses Philox counter
+ * (q/2, 0, t, WRS_TAG_BATCH) under key (seed_lo, seed_hi), as in
+ * wrs_sample_rows with stream (t, WRS_TAG_BATCH). */
+int wrs_sample_batched_rows(const wrs_row *d_rows, const uint64_t *d_off, uint32_t ntab,
+                            const uint64_t *d_cnt_off, uint64_t seed, uint32_t *d_out,
+                            void *stream);
+
+/* ---------------------------------------------------------------------- */
 /* Measurement support                                                     */
 /* ---------------------------------------------------------------------- */
 

@@ -83,6 +83,10 @@ def lib():
                 "wrs_sample_rows": (I, [P, U64, U64, U64, U64, U32, U32, P, P]),
                 "wrs_diag_random_gather": (I, [P, U64, U64, U64, I, P, P]),
                 "wrs_sample_sections": (I, [U64, U32, ctypes.POINTER(U64)]),
+                "wrs_build_batched_workspace_bytes": (I, [U64, U32, ctypes.POINTER(U64)]),
+                "wrs_batch_order": (I, [P, U32, P]),
+                "wrs_build_batched_rows": (I, [P, P, U32, P, P, P, U64, P, P]),
+                "wrs_sample_batched_rows": (I, [P, P, U32, P, U64, P, P]),
                 "wrs_sample_sectioned_rows": (I, [P, U64, U64, U64, U32, U32, P, P, P, P]),
                 "wrs_strerror": (ctypes.c_char_p, [I]),
                 "wrs_last_cuda_error": (I, []),
@@ -192,6 +196,52 @@ def sample_sectioned_rows(rows, n: int, count: int, seed: int, mode: int, sectio
     _check(lib().wrs_sample_sectioned_rows(_ptr(rows), n, count, seed & (2**64 - 1), mode,
                                            section_rows, _ptr(counts), _ptr(offsets), _ptr(out),
                                            _stream(stream)), "wrs_sample_sectioned_rows")
+
+
+SUMMARY_DTYPE = np.dtype([("status", "<i4"), ("n", "<u4"), ("W", "<f8"), ("nl", "<u8"),
+                          ("nh", "<u8")])
+
+
+def batch_order(off_host) -> np.ndarray:
+    """Host plan: table ids largest first (wrs_batch_order)."""
+    off = np.ascontiguousarray(off_host, np.uint64)
+    ntab = off.size - 1
+    order = np.zeros(max(ntab, 1), np.uint32)
+    _check(lib().wrs_batch_order(off.ctypes.data_as(ctypes.c_void_p), ntab,
+                                 order.ctypes.data_as(ctypes.c_void_p)), "wrs_batch_order")
+    return order[:ntab]
+
+
+class BatchBuilder:
+    """Workspace and buffers for building a batch of tables in one launch
+    (wrs_build_batched_rows); all arguments are torch tensors on the GPU."""
+
+    def __init__(self, total: int, ntab: int, device="cuda"):
+        import torch
+        out = ctypes.c_uint64()
+        _check(lib().wrs_build_batched_workspace_bytes(total, ntab, ctypes.byref(out)),
+               "wrs_build_batched_workspace_bytes")
+        self.ws = torch.empty(out.value, dtype=torch.uint8, device=device)
+        self.info = torch.zeros(max(ntab, 1) * SUMMARY_DTYPE.itemsize, dtype=torch.uint8,
+                                device=device)
+        self.ntab = ntab
+
+    def build(self, w, off, rows, order=None, stream=None):
+        _check(lib().wrs_build_batched_rows(_ptr(w), _ptr(off), self.ntab, _ptr(order),
+                                            _ptr(rows), _ptr(self.ws),
+                                            self.ws.numel(), _ptr(self.info), _stream(stream)),
+               "wrs_build_batched_rows")
+
+    def summaries(self) -> np.ndarray:
+        raw = self.info.cpu().numpy().tobytes()
+        return np.frombuffer(raw, SUMMARY_DTYPE, count=self.ntab)
+
+
+def sample_batched_rows(rows, off, ntab: int, cnt_off, seed: int, out, stream=None):
+    """Enqueue batched sampling (wrs_sample_batched_rows)."""
+    _check(lib().wrs_sample_batched_rows(_ptr(rows), _ptr(off), ntab, _ptr(cnt_off),
+                                         seed & (2**64 - 1), _ptr(out), _stream(stream)),
+           "wrs_sample_batched_rows")
 
 
 def diag_random_gather(rows, nrows: int, count: int, seed: int, flavor: int, out, stream=None):

@@ -2,6 +2,10 @@
 // kernel launches on the caller's stream.  No torch types, no exceptions.
 #include <string.h>
 
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
 #include "wrs_internal.cuh"
 
 namespace wrs {
@@ -17,6 +21,11 @@ cudaError_t launch_sample_naive(const wrs_row *, uint64_t, uint64_t, uint64_t, u
                                 uint32_t, uint32_t, uint32_t *, cudaStream_t);
 cudaError_t launch_sample_sectioned(const wrs_row *, uint64_t, uint64_t, uint64_t, uint32_t,
                                     uint64_t, uint64_t *, uint64_t *, uint32_t *, cudaStream_t);
+cudaError_t launch_build_batched(const float *, const uint64_t *, uint32_t, const uint32_t *,
+                                 uint32_t *, Entry *, wrs_row *, wrs_table_summary *,
+                                 cudaStream_t);
+cudaError_t launch_sample_batched(const wrs_row *, const uint64_t *, uint32_t, const uint64_t *,
+                                  uint64_t, uint32_t *, cudaStream_t);
 cudaError_t launch_random_gather(const void *, uint64_t, uint64_t, uint64_t, int, uint32_t *,
                                  cudaStream_t);
 
@@ -207,6 +216,53 @@ int wrs_sample_sectioned_rows(const wrs_row *d_rows, uint64_t n, uint64_t count,
     if (nsec > 0x7fffffffull) return WRS_EINVAL;
     return cuda_status(launch_sample_sectioned(d_rows, n, count, seed, mode, nsec, d_counts,
                                                d_offsets, d_out, (cudaStream_t)stream));
+}
+
+int wrs_build_batched_workspace_bytes(uint64_t total, uint32_t ntab, uint64_t *bytes) {
+    if (!bytes) return WRS_EINVAL;
+    (void)ntab;
+    *bytes = 256 + align_up(total * sizeof(Entry), 256);
+    return WRS_OK;
+}
+
+int wrs_batch_order(const uint64_t *h_off, uint32_t ntab, uint32_t *h_order) {
+    if (!h_off || (ntab && !h_order)) return WRS_EINVAL;
+    std::vector<uint32_t> idx(ntab);
+    std::iota(idx.begin(), idx.end(), 0u);
+    std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) {
+        return h_off[a + 1] - h_off[a] > h_off[b + 1] - h_off[b];
+    });
+    std::copy(idx.begin(), idx.end(), h_order);
+    return WRS_OK;
+}
+
+int wrs_build_batched_rows(const float *d_w, const uint64_t *d_off, uint32_t ntab,
+                           const uint32_t *d_order, wrs_row *d_rows, void *d_ws, uint64_t ws_bytes,
+                           wrs_table_summary *d_info, void *stream) {
+    if (ntab == 0) return WRS_OK;
+    if (!d_w || ((uintptr_t)d_w & 3u) || !d_off || ((uintptr_t)d_off & 7u) || !d_rows ||
+        ((uintptr_t)d_rows & 7u) || !d_ws || ((uintptr_t)d_ws & 255u) || !d_info)
+        return WRS_EINVAL;
+    if (ws_bytes < 256) return WRS_EINVAL;
+    // the workspace must hold one l/h entry per item; the total is on the
+    // device, so the kernel trusts ws_bytes >= 256 + 8 * total (checked by
+    // the caller through wrs_build_batched_workspace_bytes)
+    unsigned char *ws = (unsigned char *)d_ws;
+    return cuda_status(launch_build_batched(d_w, d_off, ntab, d_order,
+                                            reinterpret_cast<uint32_t *>(ws),
+                                            reinterpret_cast<Entry *>(ws + 256), d_rows, d_info,
+                                            (cudaStream_t)stream));
+}
+
+int wrs_sample_batched_rows(const wrs_row *d_rows, const uint64_t *d_off, uint32_t ntab,
+                            const uint64_t *d_cnt_off, uint64_t seed, uint32_t *d_out,
+                            void *stream) {
+    if (ntab == 0) return WRS_OK;
+    if (!d_rows || ((uintptr_t)d_rows & 7u) || !d_off || ((uintptr_t)d_off & 7u) || !d_cnt_off ||
+        ((uintptr_t)d_cnt_off & 7u) || !d_out || ((uintptr_t)d_out & 3u))
+        return WRS_EINVAL;
+    return cuda_status(launch_sample_batched(d_rows, d_off, ntab, d_cnt_off, seed, d_out,
+                                             (cudaStream_t)stream));
 }
 
 int wrs_diag_random_gather(const wrs_row *d_rows, uint64_t nrows, uint64_t count, uint64_t seed,

@@ -38,7 +38,7 @@
 // the stored probabilities.
 #include <stdio.h>
 
-#include "wrs_internal.cuh"
+#include "wrs_device.cuh"
 
 namespace wrs {
 
@@ -82,15 +82,10 @@ k_sum(const float *__restrict__ w, uint64_t n, u128 *__restrict__ bins_out,
     for (int b = 0; b < kBands; ++b) bins[b][tid] = 0;
     uint32_t bad = 0;
     auto add = [&](float x) {
-        uint32_t u = __float_as_uint(x);
-        uint32_t e = (u >> 23) & 0xffu;
-        bad |= (e == 0xffu) ? ERR_NONFINITE : 0u;
-        bad |= ((u >> 31) && (u & 0x7fffffffu)) ? ERR_NEGATIVE : 0u;
-        uint32_t ee = e ? e : 1u;
-        uint32_t m = (e == 0xffu) ? 0u : ((u & 0x7fffffu) | (e ? 0x800000u : 0u));
-        uint32_t band = (ee * 2731u) >> 16;  // ee / 24 for ee < 256
-        uint32_t sh = ee - 24u * band;
-        bins[band][tid] += (uint64_t)m << sh;
+        uint32_t band;
+        uint64_t val;
+        band_of(x, band, val, bad);
+        bins[band][tid] += val;
     };
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + tid;
@@ -123,35 +118,6 @@ k_sum(const float *__restrict__ w, uint64_t n, u128 *__restrict__ bins_out,
     if (lane == 0 && bad) atomicOr(&P->status, bad);
 }
 
-// Bits [pos, pos+cnt) of a 384-bit integer held in 12 32-bit limbs, low
-// limb first (cnt <= 128; bits outside the integer read as 0).
-__device__ static u128 big_bits(const uint32_t *big, int pos, int cnt) {
-    int li = pos >= 0 ? pos / 32 : -((31 - pos) / 32);   // floor(pos / 32)
-    int s = pos - 32 * li;                                // 0..31
-    u128 lo = 0;
-    for (int k = 0; k < 4; ++k) {
-        int idx = li + k;
-        uint32_t v = (idx >= 0 && idx < 12) ? big[idx] : 0u;
-        lo |= (u128)v << (32 * k);
-    }
-    int idx5 = li + 4;
-    uint32_t v5 = (idx5 >= 0 && idx5 < 12) ? big[idx5] : 0u;
-    u128 r = lo >> s;
-    if (s) r |= (u128)v5 << (128 - s);
-    if (cnt < 128) r &= (((u128)1) << cnt) - 1;
-    return r;
-}
-
-// Any set bit strictly below position pos?
-__device__ static int big_any_below(const uint32_t *big, int pos) {
-    for (int k = 0; k < 12 && 32 * k < pos; ++k) {
-        int nb = pos - 32 * k;   // bits of limb k that lie below pos
-        uint32_t m = nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u);
-        if (big[k] & m) return 1;
-    }
-    return 0;
-}
-
 // kBands warps: warp b reduces band b over the blocks; thread 0 then
 // assembles W exactly (units of 2^-150), rounds it to FP64 (ties to even)
 // and derives avg, the light threshold and the fixed-point scale.
@@ -173,47 +139,16 @@ k_total(const u128 *__restrict__ bins_in, int nblocks, uint64_t n, uint32_t sect
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
-    uint32_t big[12];
-    for (int k = 0; k < 12; ++k) big[k] = 0;
-    for (int b = 0; b < kBands; ++b) {
-        // big += band[b] << 24b
-        u128 v = band[b];
-        int shift = 24 * b;
-        uint64_t carry = 0;
-        for (int k = 0; k < 12; ++k) {
-            int o = 32 * k - shift;  // bit of v that lands at bit 0 of limb k
-            uint32_t part = 0;
-            if (o >= 0 && o < 128) part = (uint32_t)(v >> o);
-            else if (o < 0 && o > -32) part = (uint32_t)(v << (-o));
-            uint64_t sum = (uint64_t)big[k] + part + carry;
-            big[k] = (uint32_t)sum;
-            carry = sum >> 32;
-        }
-    }
-    int top = -1;
-    for (int k = 11; k >= 0 && top < 0; --k)
-        if (big[k]) top = 32 * k + 31 - __clz(big[k]);
     P->n = n;
     P->sections = sections;
-    if (top < 0) {
+    double W;
+    int top;
+    if (!exact_total(band, W, top)) {
         P->W = 0.0;
         P->avg = 0.0;
         atomicOr(&P->status, ERR_ZEROSUM);
         return;
     }
-    // W: 53 bits from the top, round to nearest even.
-    uint64_t mant = (uint64_t)big_bits(big, top - 52, 53);
-    int t = top;
-    if (top >= 53) {
-        int half = (int)big_bits(big, top - 53, 1);
-        int sticky = big_any_below(big, top - 53);
-        if (half && (sticky || (mant & 1u))) {
-            ++mant;
-            if (mant >> 53) { mant >>= 1; ++t; }
-        }
-    }
-    uint64_t bits = ((uint64_t)(t + 873) << 52) | (mant & ((1ull << 52) - 1));
-    double W = __longlong_as_double((long long)bits);
     double avg = W / (double)n;
     // q_i = round(w_i 2^S) with W 2^S in [2^61, 2^62): S = 211 - top
     P->W = W;
@@ -228,7 +163,6 @@ k_total(const u128 *__restrict__ bins_in, int nblocks, uint64_t n, uint32_t sect
 // a2 + a3: classify, stable partition, prefix sums (decoupled look-back)
 // ===========================================================================
 
-__device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
 
 // Segment g of G covers tiles [g*T/G, (g+1)*T/G) of kTile items.
 __device__ __forceinline__ void seg_tiles(uint32_t g, uint32_t G, uint64_t T, uint64_t &t0,
@@ -341,8 +275,6 @@ __device__ __forceinline__ void put_ck(CkRec *ck, uint64_t idx, uint32_t seg, ui
     uint4 r = make_uint4(seg, 0u, (uint32_t)v, (uint32_t)(v >> 32));
     *reinterpret_cast<uint4 *>(ck + idx) = r;
 }
-
-__device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
 
 // Place every item of the segment: lights at l[rank] (entry rank), heavies at
 // h[rank] (entry n-1-rank); both stay in index order.  Every 32nd list entry

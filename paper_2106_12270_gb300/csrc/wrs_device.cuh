@@ -1,0 +1,98 @@
+// wrs_device.cuh - device routines shared by the construction kernels
+// (single table and batched).
+#pragma once
+
+#include "wrs_internal.cuh"
+
+namespace wrs {
+
+__device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
+__device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
+
+// Exponent band of an FP32 weight for the exact sum: a weight m * 2^(e'-150)
+// (e' = max(biased exponent, 1)) is added to band e'/24 as m << (e' mod 24),
+// a value below 2^47.  Sets error bits for NaN/Inf and negative weights.
+__device__ __forceinline__ void band_of(float x, uint32_t &band, uint64_t &val, uint32_t &bad) {
+    uint32_t u = __float_as_uint(x);
+    uint32_t e = (u >> 23) & 0xffu;
+    bad |= (e == 0xffu) ? ERR_NONFINITE : 0u;
+    bad |= ((u >> 31) && (u & 0x7fffffffu)) ? ERR_NEGATIVE : 0u;
+    uint32_t ee = e ? e : 1u;
+    uint32_t m = (e == 0xffu) ? 0u : ((u & 0x7fffffu) | (e ? 0x800000u : 0u));
+    band = (ee * 2731u) >> 16;   // ee / 24 for ee < 256
+    val = (uint64_t)m << (ee - 24u * band);
+}
+
+// Bits [pos, pos+cnt) of a 384-bit integer held in 12 32-bit limbs, low
+// limb first (cnt <= 128; bits outside the integer read as 0).
+__device__ inline u128 big_bits(const uint32_t *big, int pos, int cnt) {
+    int li = pos >= 0 ? pos / 32 : -((31 - pos) / 32);   // floor(pos / 32)
+    int s = pos - 32 * li;                                // 0..31
+    u128 lo = 0;
+    for (int k = 0; k < 4; ++k) {
+        int idx = li + k;
+        uint32_t v = (idx >= 0 && idx < 12) ? big[idx] : 0u;
+        lo |= (u128)v << (32 * k);
+    }
+    int idx5 = li + 4;
+    uint32_t v5 = (idx5 >= 0 && idx5 < 12) ? big[idx5] : 0u;
+    u128 r = lo >> s;
+    if (s) r |= (u128)v5 << (128 - s);
+    if (cnt < 128) r &= (((u128)1) << cnt) - 1;
+    return r;
+}
+
+// Any set bit strictly below position pos?
+__device__ inline int big_any_below(const uint32_t *big, int pos) {
+    for (int k = 0; k < 12 && 32 * k < pos; ++k) {
+        int nb = pos - 32 * k;   // bits of limb k that lie below pos
+        uint32_t m = nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u);
+        if (big[k] & m) return 1;
+    }
+    return 0;
+}
+
+// W from the per-band sums (band b counts in units of 2^(24b-150)): the
+// exact total assembled in a 384-bit integer and rounded once to FP64, ties
+// to even.  Returns false when the total is zero; `top` is the index of the
+// total's highest set bit (units of 2^-150).
+__device__ inline bool exact_total(const u128 *band, double &W, int &top) {
+    uint32_t big[12];
+    for (int k = 0; k < 12; ++k) big[k] = 0;
+    for (int b = 0; b < kBands; ++b) {
+        u128 v = band[b];
+        int shift = 24 * b;
+        uint64_t carry = 0;
+        for (int k = 0; k < 12; ++k) {
+            int o = 32 * k - shift;  // bit of v that lands at bit 0 of limb k
+            uint32_t part = 0;
+            if (o >= 0 && o < 128) part = (uint32_t)(v >> o);
+            else if (o < 0 && o > -32) part = (uint32_t)(v << (-o));
+            uint64_t sum = (uint64_t)big[k] + part + carry;
+            big[k] = (uint32_t)sum;
+            carry = sum >> 32;
+        }
+    }
+    top = -1;
+    for (int k = 11; k >= 0 && top < 0; --k)
+        if (big[k]) top = 32 * k + 31 - __clz(big[k]);
+    if (top < 0) {
+        W = 0.0;
+        return false;
+    }
+    uint64_t mant = (uint64_t)big_bits(big, top - 52, 53);
+    int t = top;
+    if (top >= 53) {
+        int half = (int)big_bits(big, top - 53, 1);
+        int sticky = big_any_below(big, top - 53);
+        if (half && (sticky || (mant & 1u))) {
+            ++mant;
+            if (mant >> 53) { mant >>= 1; ++t; }
+        }
+    }
+    uint64_t bits = ((uint64_t)(t + 873) << 52) | (mant & ((1ull << 52) - 1));
+    W = __longlong_as_double((long long)bits);
+    return true;
+}
+
+}  // namespace wrs

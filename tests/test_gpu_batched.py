@@ -1,0 +1,114 @@
+"""Batched construction and sampling of many tables in one launch (GPU).
+
+Every table of a batch must be the very table the single-table path builds
+for the same weights (same exact arithmetic: bit-identical rows), match the
+oracle (exact W, light/heavy counts, mass within 1e-5), and its samples must
+equal the oracle's sampler on stream (table, WRS_TAG_BATCH) bit for bit.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2106_12270_gb300 as wrs
+from gpu_util import Built
+from paper_2106_12270_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def build_batch(w_np, off_np, order=True):
+    ntab = off_np.size - 1
+    w = torch.from_numpy(np.ascontiguousarray(w_np, np.float32)).cuda()
+    off = torch.from_numpy(off_np.astype(np.int64)).cuda()
+    rows = torch.zeros(max(int(off_np[-1]), 1), dtype=torch.int64, device="cuda")
+    bb = wrs.BatchBuilder(int(off_np[-1]), ntab)
+    ord_t = torch.from_numpy(wrs.batch_order(off_np).astype(np.int32)).cuda() if order else None
+    bb.build(w, off, rows, ord_t)
+    torch.cuda.synchronize()
+    return rows, bb.summaries(), off
+
+
+@pytest.fixture(scope="module")
+def batch():
+    sizes = inputs.log_uniform_sizes(300, 6, 16, 65536)
+    sizes[:4] = [1, 2, 4096, 4097]   # tiny tables and a partition-tile boundary
+    w, off = inputs.batched(sizes, 7, "gamma")
+    rows, summ, off_t = build_batch(w, off)
+    return w, off, rows, summ, off_t
+
+
+def table_rows(rows, off, t):
+    prob, alias = wrs.rows_to_numpy(rows[int(off[t]): int(off[t + 1])])
+    return prob, alias
+
+
+def test_batched_matches_oracle(batch):
+    w, off, rows, summ, _ = batch
+    for t in range(off.size - 1):
+        wt = w[off[t]: off[t + 1]]
+        if wt.sum() == 0:
+            assert summ[t]["status"] == wrs.EZEROSUM
+            continue
+        W = oracle.exact_sum(wt)
+        assert summ[t]["status"] == wrs.OK
+        assert summ[t]["W"] == W
+        l, h = oracle.classify(wt, W / wt.size)
+        assert (summ[t]["nl"], summ[t]["nh"]) == (len(l), len(h))
+        prob, alias = table_rows(rows, off, t)
+        assert np.all(alias < wt.size)
+        assert oracle.mass_error(prob.astype(np.float64), alias, wt, W) <= 1e-5
+
+
+def test_batched_equals_single_table_builds(batch):
+    w, off, rows, summ, _ = batch
+    for t in list(range(0, off.size - 1, 7)) + [2, 3]:
+        wt = w[off[t]: off[t + 1]]
+        if wt.sum() == 0:
+            continue
+        b = Built(wt)
+        prob, alias = table_rows(rows, off, t)
+        assert np.array_equal(prob.view(np.uint32), b.prob.view(np.uint32)), t
+        assert np.array_equal(alias, b.alias), t
+
+
+def test_batched_order_does_not_matter(batch):
+    w, off, rows, summ, _ = batch
+    rows2, summ2, _ = build_batch(w, off, order=False)
+    assert torch.equal(rows, rows2)
+    assert np.array_equal(summ["W"], summ2["W"])
+
+
+def test_batched_sampling_bit_exact(batch):
+    w, off, rows, summ, off_t = batch
+    ntab = off.size - 1
+    cnt = np.full(ntab, 1001, np.int64)
+    cnt[5] = 0
+    cnt_off = np.zeros(ntab + 1, np.int64)
+    cnt_off[1:] = np.cumsum(cnt)
+    out = torch.empty(int(cnt_off[-1]), dtype=torch.int32, device="cuda")
+    wrs.sample_batched_rows(rows, off_t, ntab, torch.from_numpy(cnt_off).cuda(), 99, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32)
+    for t in range(0, ntab, 11):
+        if summ[t]["status"] != wrs.OK:
+            continue
+        prob, alias = table_rows(rows, off, t)
+        want = oracle.sample_naive(prob, alias, 0, int(cnt[t]), 99, t, wrs.TAG_BATCH)
+        assert np.array_equal(got[cnt_off[t]: cnt_off[t + 1]], want), t
+
+
+def test_batched_bad_tables_do_not_spoil_others():
+    sizes = np.array([100, 0, 50, 30, 70])
+    w, off = inputs.batched(sizes, 3, "uniform")
+    w[off[2] + 5] = np.nan
+    w[off[3]: off[4]] = 0.0
+    w[off[4] + 1] = -1.0
+    rows, summ, _ = build_batch(w, off)
+    assert summ["status"].tolist() == [wrs.OK, wrs.EINVAL, wrs.ENONFINITE, wrs.EZEROSUM,
+                                       wrs.EINVAL]
+    prob, alias = table_rows(rows, off, 0)
+    W = oracle.exact_sum(w[:100])
+    assert oracle.mass_error(prob.astype(np.float64), alias, w[:100], W) <= 1e-5
