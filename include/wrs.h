@@ -275,6 +275,61 @@ int wrs_sample_batched_rows(const wrs_row *d_rows, const uint64_t *d_off, uint32
                             void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Request loop: resident tables, continuous batching                      */
+/* ---------------------------------------------------------------------- */
+/* A server owns one worker thread on the calling thread's current device.
+ * Requests are queued from any thread and served in steps: all admissible
+ * requests that have arrived are built with one batched-build launch and
+ * sampled with one sampling launch; up to max_inflight steps run on the GPU
+ * at once while new arrivals form the next step.  Builds are admitted while
+ * resident tables plus in-flight scratch stay within hbm_budget bytes (a
+ * table costs 8 bytes per item while resident and about 12 bytes per item
+ * while it is built); they are admitted in arrival order, and a build that
+ * can never fit fails with WRS_ENOMEM.  The paper has no counterpart: it is
+ * how a serving system uses the method.
+ *
+ * Results do not depend on batching: a table equals wrs_build_rows of the
+ * same weights, and the samples of a request equal wrs_sample_rows(rows, n,
+ * 0, count, seed, stream_lo, WRS_TAG_NAIVE) on that table.
+ *
+ * Buffers passed to a request must stay valid until the request is done:
+ * weights w (host or device, 1..2^24 items) and the sample output out
+ * (host or device, count uint32).  Tickets name requests; the ticket of a
+ * build also names its table. */
+typedef struct wrs_server wrs_server;
+
+typedef struct wrs_server_statistics {
+    uint64_t completed, builds, samples, releases, errors;
+    uint64_t items_built, samples_drawn, steps;
+    double mean_step_requests;
+    uint64_t resident_bytes, peak_bytes;
+    double p50_ms, p99_ms, mean_ms;   /* latency: submit to completion */
+    double wall_s;                    /* first submit to last completion */
+} wrs_server_statistics;
+
+int wrs_server_create(uint64_t hbm_budget, uint32_t max_inflight, wrs_server **out);
+int wrs_server_submit_build(wrs_server *s, const float *w, uint64_t n, int w_on_device,
+                            uint64_t *ticket);
+int wrs_server_submit_sample(wrs_server *s, uint64_t table, uint64_t count, uint64_t seed,
+                             uint32_t stream_lo, uint32_t *out, int out_on_device,
+                             uint64_t *ticket);
+int wrs_server_submit_release(wrs_server *s, uint64_t table, uint64_t *ticket);
+/* done = 1 once the request finished; status is its result (WRS_OK,
+ * WRS_ENOMEM, WRS_ENOTFOUND for an unknown or released table, a data error
+ * of the build, WRS_ECUDA). */
+int wrs_server_poll(wrs_server *s, uint64_t ticket, int *done, int *status);
+int wrs_server_wait(wrs_server *s, uint64_t ticket, int *status);
+/* Device rows of a built, resident table (valid until it is released). */
+int wrs_server_table(wrs_server *s, uint64_t table, const wrs_row **d_rows, uint64_t *n,
+                     double *W);
+/* Copy the rows of a built, resident table into dst (n rows, host or device);
+ * blocks until the copy is done.  This is the checkpoint/export path. */
+int wrs_server_export(wrs_server *s, uint64_t table, wrs_row *dst, int dst_on_device);
+int wrs_server_stats(wrs_server *s, wrs_server_statistics *out);
+/* Finish every queued request, free every table, stop the worker. */
+int wrs_server_destroy(wrs_server *s);
+
+/* ---------------------------------------------------------------------- */
 /* Measurement support                                                     */
 /* ---------------------------------------------------------------------- */
 

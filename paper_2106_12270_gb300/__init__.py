@@ -54,6 +54,17 @@ class Layout(ctypes.Structure):
                 ("sections", ctypes.c_uint64), ("total_bytes", ctypes.c_uint64)]
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("builds", ctypes.c_uint64),
+                ("samples", ctypes.c_uint64), ("releases", ctypes.c_uint64),
+                ("errors", ctypes.c_uint64), ("items_built", ctypes.c_uint64),
+                ("samples_drawn", ctypes.c_uint64), ("steps", ctypes.c_uint64),
+                ("mean_step_requests", ctypes.c_double), ("resident_bytes", ctypes.c_uint64),
+                ("peak_bytes", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("wall_s", ctypes.c_double)]
+
+
 INFO_DTYPE = np.dtype([("status", "<i4"), ("scale", "<i4"), ("W", "<f8"), ("avg", "<f8"),
                        ("nl", "<u8"), ("nh", "<u8"), ("Q", "<u4", (4,)),
                        ("light_max", "<f4"), ("sections", "<u4"), ("reserved", "<u8", (4,))])
@@ -87,6 +98,18 @@ def lib():
                 "wrs_batch_order": (I, [P, U32, P]),
                 "wrs_build_batched_rows": (I, [P, P, U32, P, P, P, U64, P, P]),
                 "wrs_sample_batched_rows": (I, [P, P, U32, P, U64, P, P]),
+                "wrs_server_create": (I, [U64, U32, ctypes.POINTER(P)]),
+                "wrs_server_submit_build": (I, [P, P, U64, I, ctypes.POINTER(U64)]),
+                "wrs_server_submit_sample": (I, [P, U64, U64, U64, U32, P, I,
+                                                 ctypes.POINTER(U64)]),
+                "wrs_server_submit_release": (I, [P, U64, ctypes.POINTER(U64)]),
+                "wrs_server_poll": (I, [P, U64, ctypes.POINTER(I), ctypes.POINTER(I)]),
+                "wrs_server_wait": (I, [P, U64, ctypes.POINTER(I)]),
+                "wrs_server_table": (I, [P, U64, ctypes.POINTER(P), ctypes.POINTER(U64),
+                                         ctypes.POINTER(ctypes.c_double)]),
+                "wrs_server_stats": (I, [P, ctypes.POINTER(ServerStats)]),
+                "wrs_server_export": (I, [P, U64, P, I]),
+                "wrs_server_destroy": (I, [P]),
                 "wrs_sample_sectioned_rows": (I, [P, U64, U64, U64, U32, U32, P, P, P, P]),
                 "wrs_strerror": (ctypes.c_char_p, [I]),
                 "wrs_last_cuda_error": (I, []),
@@ -242,6 +265,82 @@ def sample_batched_rows(rows, off, ntab: int, cnt_off, seed: int, out, stream=No
     _check(lib().wrs_sample_batched_rows(_ptr(rows), _ptr(off), ntab, _ptr(cnt_off),
                                          seed & (2**64 - 1), _ptr(out), _stream(stream)),
            "wrs_sample_batched_rows")
+
+
+class Server:
+    """Request loop over resident tables (wrs_server_*).  Weights and sample
+    outputs are torch tensors (host or device); they must stay alive until
+    the request is done, which this class ensures by holding references."""
+
+    def __init__(self, hbm_budget: int, max_inflight: int = 2):
+        h = ctypes.c_void_p()
+        _check(lib().wrs_server_create(hbm_budget, max_inflight, ctypes.byref(h)),
+               "wrs_server_create")
+        self.h = h
+        self._keep = {}
+
+    def build(self, w) -> int:
+        t = ctypes.c_uint64()
+        _check(lib().wrs_server_submit_build(self.h, _ptr(w), w.numel(), int(w.is_cuda),
+                                             ctypes.byref(t)), "wrs_server_submit_build")
+        self._keep[t.value] = w
+        return t.value
+
+    def sample(self, table: int, count: int, seed: int, out, stream_lo: int = 0) -> int:
+        t = ctypes.c_uint64()
+        _check(lib().wrs_server_submit_sample(self.h, table, count, seed & (2**64 - 1), stream_lo,
+                                              _ptr(out), int(out.is_cuda), ctypes.byref(t)),
+               "wrs_server_submit_sample")
+        self._keep[t.value] = out
+        return t.value
+
+    def release(self, table: int) -> int:
+        t = ctypes.c_uint64()
+        _check(lib().wrs_server_submit_release(self.h, table, ctypes.byref(t)),
+               "wrs_server_submit_release")
+        return t.value
+
+    def poll(self, ticket: int):
+        d, s = ctypes.c_int(), ctypes.c_int()
+        _check(lib().wrs_server_poll(self.h, ticket, ctypes.byref(d), ctypes.byref(s)),
+               "wrs_server_poll")
+        return bool(d.value), s.value
+
+    def wait(self, ticket: int) -> int:
+        s = ctypes.c_int()
+        _check(lib().wrs_server_wait(self.h, ticket, ctypes.byref(s)), "wrs_server_wait")
+        self._keep.pop(ticket, None)
+        return s.value
+
+    def table(self, table: int):
+        """(device pointer, n, W) of a built, resident table."""
+        p, n, W = ctypes.c_void_p(), ctypes.c_uint64(), ctypes.c_double()
+        _check(lib().wrs_server_table(self.h, table, ctypes.byref(p), ctypes.byref(n),
+                                      ctypes.byref(W)), "wrs_server_table")
+        return p.value, n.value, W.value
+
+    def export(self, table: int, dst):
+        """Copy a resident table's rows into dst (int64 [n], host or device)."""
+        _check(lib().wrs_server_export(self.h, table, _ptr(dst), int(dst.is_cuda)),
+               "wrs_server_export")
+        return dst
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().wrs_server_stats(self.h, ctypes.byref(st)), "wrs_server_stats")
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.h:
+            _check(lib().wrs_server_destroy(self.h), "wrs_server_destroy")
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def diag_random_gather(rows, nrows: int, count: int, seed: int, flavor: int, out, stream=None):

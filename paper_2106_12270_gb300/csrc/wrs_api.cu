@@ -22,8 +22,8 @@ cudaError_t launch_sample_naive(const wrs_row *, uint64_t, uint64_t, uint64_t, u
 cudaError_t launch_sample_sectioned(const wrs_row *, uint64_t, uint64_t, uint64_t, uint32_t,
                                     uint64_t, uint64_t *, uint64_t *, uint32_t *, cudaStream_t);
 cudaError_t launch_build_batched(const float *, const uint64_t *, uint32_t, const uint32_t *,
-                                 uint32_t *, Entry *, wrs_row *, wrs_table_summary *,
-                                 cudaStream_t);
+                                 uint32_t *, Entry *, wrs_row *, wrs_row *const *,
+                                 wrs_table_summary *, cudaStream_t);
 cudaError_t launch_sample_batched(const wrs_row *, const uint64_t *, uint32_t, const uint64_t *,
                                   uint64_t, uint32_t *, cudaStream_t);
 cudaError_t launch_random_gather(const void *, uint64_t, uint64_t, uint64_t, int, uint32_t *,
@@ -250,7 +250,8 @@ int wrs_build_batched_rows(const float *d_w, const uint64_t *d_off, uint32_t nta
     unsigned char *ws = (unsigned char *)d_ws;
     return cuda_status(launch_build_batched(d_w, d_off, ntab, d_order,
                                             reinterpret_cast<uint32_t *>(ws),
-                                            reinterpret_cast<Entry *>(ws + 256), d_rows, d_info,
+                                            reinterpret_cast<Entry *>(ws + 256), d_rows, nullptr,
+                                            d_info,
                                             (cudaStream_t)stream));
 }
 

@@ -63,7 +63,7 @@ __device__ __forceinline__ int pp8b(int e) { return e + (e >> 3); }
 __global__ void __launch_bounds__(kBT, 2)
 k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
                 const uint32_t *__restrict__ order, uint32_t ntab, uint32_t *__restrict__ counter,
-                Entry *__restrict__ lh, uint2 *__restrict__ rows,
+                Entry *__restrict__ lh, uint2 *__restrict__ rows, uint2 *const *__restrict__ row_ptrs,
                 wrs_table_summary *__restrict__ info) {
     extern __shared__ __align__(16) unsigned char bsm_raw[];
     BatchShared &sm = *reinterpret_cast<BatchShared *>(bsm_raw);
@@ -244,7 +244,7 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
         __syncthreads();
         const uint32_t N = (uint32_t)n;
         const Entry *lht = lh + base;
-        uint2 *rt = rows + base;
+        uint2 *rt = row_ptrs ? row_ptrs[t] : rows + base;
         for (;;) {
             const uint64_t i = sm.i, j = sm.j;
             if (i + j >= n) break;
@@ -398,11 +398,52 @@ k_batched_sample(const uint2 *__restrict__ rows, const uint64_t *__restrict__ of
     }
 }
 
+// Sampling requests of the request loop: request r draws samples
+// 0..count-1 of stream (seed, slo, shi) from its own table, exactly as
+// wrs_sample_rows would alone.  Request r is cut into chunks of kReqChunk
+// samples; chunk_off[r] is the first CTA of request r.
+constexpr uint64_t kReqChunk = 1u << 16;
+
+__global__ void __launch_bounds__(256)
+k_sample_requests(const SampleReq *__restrict__ req, const uint32_t *__restrict__ chunk_off,
+                  uint32_t nreq) {
+    const uint32_t blk = blockIdx.x;
+    uint32_t lo = 0, hi = nreq;   // request r with chunk_off[r] <= blk < chunk_off[r+1]
+    while (hi - lo > 1) {
+        uint32_t m = (lo + hi) >> 1;
+        if (chunk_off[m] <= blk) lo = m;
+        else hi = m;
+    }
+    const SampleReq R = req[lo];
+    const uint64_t q0 = (uint64_t)(blk - chunk_off[lo]) * kReqChunk;
+    const uint64_t q1 = min(q0 + kReqChunk, R.count);
+    const uint2 *rows = reinterpret_cast<const uint2 *>(R.rows);
+    for (uint64_t cc = (q0 >> 1) + threadIdx.x; 2 * cc < q1; cc += blockDim.x) {
+        uint4 x = philox4x32_10(make_uint4((uint32_t)cc, (uint32_t)(cc >> 32), R.slo, R.shi), R.k0,
+                                R.k1);
+        uint64_t ra, rb;
+        uint32_t ca, cb;
+        walker_split(((uint64_t)x.x << 32) | x.y, R.n, ra, ca);
+        walker_split(((uint64_t)x.z << 32) | x.w, R.n, rb, cb);
+        uint64_t q = 2 * cc;
+        R.out[q] = walker_pick((uint32_t)ra, ca, __ldg(rows + ra));
+        if (q + 1 < q1) R.out[q + 1] = walker_pick((uint32_t)rb, cb, __ldg(rows + rb));
+    }
+}
+
+cudaError_t launch_sample_requests(const SampleReq *d_req, const uint32_t *d_chunk_off,
+                                   uint32_t nreq, uint32_t nblocks, cudaStream_t st) {
+    if (nreq == 0 || nblocks == 0) return cudaSuccess;
+    k_sample_requests<<<nblocks, 256, 0, st>>>(d_req, d_chunk_off, nreq);
+    return cudaGetLastError();
+}
+
 extern int num_sms();
 
 cudaError_t launch_build_batched(const float *d_w, const uint64_t *d_off, uint32_t ntab,
                                  const uint32_t *d_order, uint32_t *d_counter, Entry *d_lh,
-                                 wrs_row *d_rows, wrs_table_summary *d_info, cudaStream_t st) {
+                                 wrs_row *d_rows, wrs_row *const *d_row_ptrs,
+                                 wrs_table_summary *d_info, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), st);
     if (e) return e;
     const int smem = (int)sizeof(BatchShared);
@@ -419,7 +460,9 @@ cudaError_t launch_build_batched(const float *d_w, const uint64_t *d_off, uint32
     unsigned blocks = (unsigned)num_sms() * (unsigned)(per_sm > 0 ? per_sm : 1);
     if (blocks > ntab) blocks = ntab ? ntab : 1;
     k_batched_build<<<blocks, kBT, smem, st>>>(d_w, d_off, d_order, ntab, d_counter, d_lh,
-                                               reinterpret_cast<uint2 *>(d_rows), d_info);
+                                               reinterpret_cast<uint2 *>(d_rows),
+                                               reinterpret_cast<uint2 *const *>(d_row_ptrs),
+                                               d_info);
     return cudaGetLastError();
 }
 

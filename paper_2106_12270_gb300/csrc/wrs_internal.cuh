@@ -101,6 +101,15 @@ struct __align__(16) SplitRec {  // Vose state after k_t buckets
     u128 E;       // E'(j)
 };
 
+// One sampling request of the request loop (device-resident descriptor).
+struct __align__(16) SampleReq {
+    const wrs_row *rows;
+    uint64_t n;
+    uint64_t count;
+    uint32_t *out;
+    uint32_t k0, k1, slo, shi;
+};
+
 // Sizes shared by host and device code.
 constexpr int kBands = 11;            // exponent bands of width 24
 constexpr int kSumThreads = 256;

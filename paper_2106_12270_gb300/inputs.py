@@ -90,3 +90,38 @@ def by_name(kind: str, n: int, seed: int) -> np.ndarray:
     if kind == "gamma":
         return gamma(n, seed, 0.1)
     raise ValueError(kind)
+
+
+def serving_stream(nreq: int, seed: int, rate_per_s: float, build_range=(1_000, 10_000_000),
+                   sample_range=(100, 1_000_000), mix=(0.10, 0.85, 0.05)):
+    """Poisson request stream: list of dicts with arrival time `t` (s) and
+    `op` in {"build", "sample", "release"}; builds carry a size (log-uniform
+    in build_range) and a weight kind ("uniform" or "zipf", 50/50), samples a
+    draw count (log-uniform in sample_range), a seed and the index of the
+    earlier build they draw from, releases the index of a build.  The first
+    request is always a build.  Which tables exist at a sample is decided by
+    the stream itself (a sample never names a released table)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    ops = []
+    live = []
+    for k in range(nreq):
+        t += rng.exponential(1.0 / rate_per_s)
+        u = rng.random()
+        if not live or u < mix[0]:
+            n = int(np.floor(np.exp(rng.uniform(math.log(build_range[0]),
+                                                 math.log(build_range[1])))))
+            ops.append({"t": t, "op": "build", "n": n,
+                        "kind": "uniform" if rng.random() < 0.5 else "zipf",
+                        "wseed": int(rng.integers(1, 2**31))})
+            live.append(len(ops) - 1)
+        elif u < mix[0] + mix[1]:
+            c = int(np.floor(np.exp(rng.uniform(math.log(sample_range[0]),
+                                                math.log(sample_range[1])))))
+            src = live[int(rng.integers(0, len(live)))]
+            ops.append({"t": t, "op": "sample", "count": c, "table": src,
+                        "seed": int(rng.integers(0, 2**63)), "stream": k})
+        else:
+            src = live.pop(int(rng.integers(0, len(live))))
+            ops.append({"t": t, "op": "release", "table": src})
+    return ops
