@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=4000)
+    ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--batch-tables", type=int, default=100_000)
     return ap.parse_args()
 
@@ -326,6 +329,7 @@ def run_gpu(args):
     probe_ms = min(probe.values())
 
     batched = None if args.no_batched else run_batched(args, world, rank)
+    serving_res = None if args.no_serving else run_serving(args, rank)
 
     hbm, peak_kind = peaks()
     build_gbs = BUILD_BYTES_PER_ITEM * n / (build_ms / 1e3) / 1e9
@@ -364,6 +368,7 @@ def run_gpu(args):
             "samples_per_s": world * count / (sample_ms / 1e3),
             "sectioned_sampling": sec,
             "batched": batched,
+            "serving": serving_res,
             "roofline": dominant, "build_roofline": build_roof, "sample_roofline": sample_roof,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": args.steps * (KERNELS_PER_BUILD + KERNELS_PER_SAMPLE),
@@ -449,6 +454,36 @@ def run_batched(args, world, rank):
             "speedup_vs_per_table": per_table_ms / build_ms,
             "samples": ntab * per_table, "sample_ms": sample_ms,
             "samples_per_s": ntab * per_table / (sample_ms / 1e3)}
+
+
+def run_serving(args, rank):
+    """Request loop: a Poisson stream (seed 5) of builds (10%, log-uniform
+    1e3..1e7 items, uniform or shuffled power law), sample requests (85%,
+    log-uniform 1e2..1e6 draws against resident tables) and releases (5%),
+    admitted under an 80 GB HBM budget; latency from submit to completion."""
+    import paper_2106_12270_gb300 as wrs
+    from paper_2106_12270_gb300 import inputs, serving
+
+    ops = inputs.serving_stream(args.serve_requests, 5 + rank, args.serve_rate)
+    srv = wrs.Server(80 << 30, 4)
+    try:
+        warm = inputs.serving_stream(200, 99, args.serve_rate, build_range=(1_000, 100_000))
+        serving.replay(srv, warm)
+        srv.close()
+        srv = wrs.Server(80 << 30, 4)
+        _, _, _, status = serving.replay(srv, ops)
+        st = srv.stats()
+    finally:
+        srv.close()
+    ok = sum(1 for v in status.values() if v == wrs.OK)
+    wall = st["wall_s"]
+    return {"requests": len(ops), "ok": ok, "arrival_rate_per_s": args.serve_rate,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+            "requests_per_s": st["completed"] / wall if wall else None,
+            "items_built_per_s": st["items_built"] / wall if wall else None,
+            "samples_per_s": st["samples_drawn"] / wall if wall else None,
+            "steps": st["steps"], "mean_step_requests": st["mean_step_requests"],
+            "peak_bytes": st["peak_bytes"], "budget_bytes": 80 << 30}
 
 
 def main():
