@@ -140,6 +140,7 @@ void wrs_server::finish(Request *r, int status, double t) {
     else if (r->kind == K_SAMPLE) ++n_sample;
     else ++n_release;
     t_last = t;
+    cv_done.notify_all();   // called with mu held; wakes wrs_server_wait
 }
 
 void wrs_server::retire() {
