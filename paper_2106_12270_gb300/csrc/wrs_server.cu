@@ -170,8 +170,13 @@ void wrs_server::retire() {
         for (Request *r : st->reqs) {
             int status = err;
             if (status == WRS_OK) {
-                if (r->kind == K_BUILD) status = tables[r->id].status;
-                else if (r->kind == K_SAMPLE) status = r->status;
+                if (r->kind == K_BUILD) {
+                    status = tables[r->id].status;
+                } else if (r->kind == K_SAMPLE) {
+                    // the table may have failed in this or an earlier step
+                    const TableRec &tr = tables[r->table];
+                    status = (tr.built && tr.status != WRS_OK) ? tr.status : r->status;
+                }
             }
             if (r->kind == K_SAMPLE && status == WRS_OK) {
                 if (!r->out_dev)
