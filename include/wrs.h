@@ -152,6 +152,27 @@ int wrs_build_rows(const float *d_w, uint64_t n, wrs_row *d_rows,
                    void *d_ws, uint64_t ws_bytes, const wrs_config *cfg,
                    wrs_build_info *d_info, void *stream);
 
+/* The same build without allocating anything (the paper has no counterpart;
+ * it serves callers that cannot allocate device memory when they build: a
+ * service whose device memory is all reserved at start-up, or code inside a
+ * framework that owns the allocator, where a cudaMalloc would break the
+ * memory plan or bring an implicit device synchronisation).  The caller
+ * still passes the weights, the rows and d_info; the workspace is a 32 MiB
+ * device array inside this library, which every GPU that loads the library
+ * holds until the process exits.
+ *  - n must be at most 3,500,000; larger n returns WRS_EINVAL and enqueues
+ *    nothing (use wrs_build_rows with a caller workspace instead).
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any
+ *    stream capture.
+ *  - Every call on a device shares the one array: calls whose work overlaps
+ *    on the GPU (different streams, or different host threads) race and give
+ *    wrong tables.  Serialise them, e.g. on one stream.  The array keeps the
+ *    last call's contents; a build never relies on it being cleared.
+ * Results are identical to wrs_build_rows. */
+int wrs_build_rows_noalloc(const float *d_w, uint64_t n, wrs_row *d_rows,
+                           const wrs_config *cfg, wrs_build_info *d_info, void *stream);
+
 /* The same build, one step per call (each enqueues its kernels; run them in
  * this order on one stream with the same workspace).  They exist so each
  * step can be checked on its own. */

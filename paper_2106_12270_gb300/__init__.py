@@ -86,6 +86,7 @@ def lib():
                 "wrs_build_workspace_bytes": (I, [U64, CP, ctypes.POINTER(U64)]),
                 "wrs_build_layout": (I, [U64, CP, ctypes.POINTER(Layout)]),
                 "wrs_build_rows": (I, [P, U64, P, P, U64, CP, P, P]),
+                "wrs_build_rows_noalloc": (I, [P, U64, P, CP, P, P]),
                 "wrs_step_total": (I, [P, U64, P, U64, CP, P]),
                 "wrs_step_partition": (I, [P, U64, P, U64, CP, P]),
                 "wrs_step_split": (I, [U64, P, U64, CP, P]),
@@ -170,6 +171,13 @@ def build_rows(w, rows, ws, info, cfg: Config | None = None, stream=None):
     n = w.numel()
     _check(lib().wrs_build_rows(_ptr(w), n, _ptr(rows), _ptr(ws), ws.numel() * ws.element_size(),
                                 _cfg(cfg), _ptr(info), _stream(stream)), "wrs_build_rows")
+
+
+def build_rows_noalloc(w, rows, info, cfg: Config | None = None, stream=None):
+    """Enqueue a full build that allocates nothing (workspace inside the
+    library; n <= 3.5 million; calls on one device must not overlap)."""
+    _check(lib().wrs_build_rows_noalloc(_ptr(w), w.numel(), _ptr(rows), _cfg(cfg), _ptr(info),
+                                        _stream(stream)), "wrs_build_rows_noalloc")
 
 
 def step_total(w, ws, cfg=None, stream=None):
