@@ -50,10 +50,16 @@ def parse():
     ap.add_argument("--n", type=int, default=100_000_000)
     ap.add_argument("--samples", type=int, default=1_000_000_000)
     ap.add_argument("--section", type=int, default=4096)
+    ap.add_argument("--dist", default="zipf",
+                    choices=["zipf", "uniform", "exponential", "gamma"],
+                    help="weights of the single table (default: shuffled power law)")
+    ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--build-only", action="store_true",
+                    help="time the build alone (no sampling legs, batched or serving)")
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--batch-tables", type=int, default=100_000)
@@ -211,11 +217,16 @@ def run_gpu(args):
 
     n, count = args.n, args.samples
     cfg = wrs.config(args.section)
-    w_host = inputs.zipf_permuted(n, 3 + rank)
+    seed = (args.seed if args.seed is not None else
+            {"zipf": 3, "uniform": 1, "exponential": 4, "gamma": 7}[args.dist]) + rank
+    w_host = inputs.by_name(args.dist, n, seed)
     w = torch.from_numpy(w_host).cuda()
     builder = wrs.Builder(n, cfg)
     rows = torch.empty(n, dtype=torch.int64, device="cuda")
-    out = torch.empty(count, dtype=torch.int32, device="cuda")
+    if args.build_only:
+        count = 0
+        args.no_batched = args.no_serving = args.no_e2e = True
+    out = torch.empty(max(count, 1), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step(evs=None):
@@ -224,7 +235,8 @@ def run_gpu(args):
         wrs.build_rows(w, rows, builder.ws, builder.info, cfg)
         if evs:
             evs[1].record(stream)
-        wrs.sample_rows(rows, n, 0, count, 2, out)
+        if not args.build_only:
+            wrs.sample_rows(rows, n, 0, count, 2, out)
         if evs:
             evs[2].record(stream)
 
@@ -294,7 +306,7 @@ def run_gpu(args):
 
     # sectioned sampling (Sec. 5): same draw count, samples grouped by section
     sec = {}
-    for mode, name, rows_per in ((wrs.SAMPLE_CACHED, "cached", 8192),
+    for mode, name, rows_per in () if args.build_only else ((wrs.SAMPLE_CACHED, "cached", 8192),
                                  (wrs.SAMPLE_LIMITED, "limited", 8192),
                                  (wrs.SAMPLE_SMEM, "smem", 16384)):
         nsec = wrs.sample_sections(n, rows_per)
@@ -316,7 +328,7 @@ def run_gpu(args):
     # random-gather probe: the naive sampler's access pattern alone (same
     # table size, same number of draws), best of the three load paths
     probe = {}
-    for flavor in (0, 1, 2):
+    for flavor in () if args.build_only else (0, 1, 2):
         wrs.diag_random_gather(rows, n, count, 7, flavor, out)
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
@@ -326,25 +338,25 @@ def run_gpu(args):
         b.record(stream)
         torch.cuda.synchronize()
         probe[flavor] = a.elapsed_time(b)
-    probe_ms = min(probe.values())
+    probe_ms = min(probe.values()) if probe else float("nan")
 
     batched = None if args.no_batched else run_batched(args, world, rank)
     serving_res = None if args.no_serving else run_serving(args, rank)
 
     hbm, peak_kind = peaks()
     build_gbs = BUILD_BYTES_PER_ITEM * n / (build_ms / 1e3) / 1e9
-    sample_gbs = SAMPLE_BYTES_PER_DRAW * count / (sample_ms / 1e3) / 1e9
+    sample_gbs = (SAMPLE_BYTES_PER_DRAW * count / (sample_ms / 1e3) / 1e9) if count else 0.0
     build_roof = {"bound": "hbm", "achieved": build_gbs, "peak": hbm, "unit": "GB/s",
                   "frac": build_gbs / hbm, "traffic": None, "kernel": "build (9 kernels)",
                   "peak_kind": peak_kind}
-    probe_gbs = SAMPLE_BYTES_PER_DRAW * count / (probe_ms / 1e3) / 1e9
+    probe_gbs = (SAMPLE_BYTES_PER_DRAW * count / (probe_ms / 1e3) / 1e9) if probe else float("nan")
     sample_roof = {"bound": "hbm", "achieved": sample_gbs, "peak": hbm, "unit": "GB/s",
                    "frac": sample_gbs / hbm, "traffic": None, "kernel": "k_sample_naive",
                    "peak_kind": peak_kind,
                    "random_gather_probe": {"achieved": probe_gbs, "unit": "GB/s",
-                                           "frac_of_probe": sample_gbs / probe_gbs,
+                                           "frac_of_probe": (sample_gbs / probe_gbs) if probe else None,
                                            "ms": {str(k): v for k, v in probe.items()}}}
-    dominant = sample_roof if sample_ms >= build_ms else build_roof
+    dominant = sample_roof if (count and sample_ms >= build_ms) else build_roof
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -360,12 +372,13 @@ def run_gpu(args):
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u128 fixed point (build), u32 (sampling)",
             "data": "synthetic",
-            "config": {"workload": "single table N=1e8, shuffled power law w=1/rank (seed 3); "
-                                   "build + 1e9 naive Walker samples (Philox seed 2)",
+            "config": {"workload": f"single table N={n}, {args.dist} weights (seed {seed}); "
+                                   f"build + {count} naive Walker samples (Philox seed 2)",
                        "n": n, "samples": count, "section_size": args.section,
+                       "dist": args.dist,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
             "build_ms": build_ms, "sample_ms": sample_ms,
-            "samples_per_s": world * count / (sample_ms / 1e3),
+            "samples_per_s": (world * count / (sample_ms / 1e3)) if count else None,
             "sectioned_sampling": sec,
             "batched": batched,
             "serving": serving_res,

@@ -48,7 +48,7 @@ struct BatchShared {
     // per-table parameters
     double W, avg;
     uint64_t Q, Qn, nl;
-    float lmax, inv_avg, Qf;
+    float lmax, inv_avg, Qf, invQ;
     int qshift;
     uint32_t status;
     uint32_t table;
@@ -173,6 +173,7 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
                 sm.Qn = Q / n;
                 sm.nl = nl;
                 sm.Qf = __ull2float_rn(Q);
+                sm.invQ = __frcp_rn(sm.Qf);
             }
             __syncthreads();
         }
@@ -323,8 +324,8 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
                                 prob = 1.0f;
                             } else {
                                 uint64_t delta = (uint64_t)(a - b);
-                                prob = fminf(fmaxf(1.0f - __fdiv_rn(__ull2float_rn(delta), sm.Qf),
-                                                   0.0f), 1.0f);
+                                prob = fminf(fmaxf(1.0f - __ull2float_rn(delta) * sm.invQ, 0.0f),
+                                             1.0f);
                             }
                             alias = sm.u.pack.item[L + y + 1];
                         } else {

@@ -257,6 +257,7 @@ k_qsum(BuildParams *__restrict__ P, const uint64_t *__restrict__ seg_q, uint32_t
     P->NQn = (u128)P->Qn * n;
     P->NQn1 = P->NQn + n;
     P->Qf = __ull2float_rn(Q);
+    P->invQ = __frcp_rn(P->Qf);
     P->nseg = G;
 }
 
@@ -313,28 +314,40 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
     const int wbase = warp * 512;
     const int e0 = wbase + lane * kPartItems;   // this lane's first item of the tile
     const int s0 = tid * kPartItems;            // this thread's first list slot
+    // coalesced 16-byte loads of one tile (the next tile is loaded while the
+    // current one is processed)
+    float4 pv[4];
+    auto load_tile = [&](uint64_t tile) {
+        const uint64_t base = tile * kTile;
+        const uint64_t lim = n - base;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int e = wbase + r * 128 + lane * 4;
+            if (kAligned && (uint64_t)e + 3 < lim) {
+                pv[r] = __ldcs(reinterpret_cast<const float4 *>(w + base + e));
+            } else {
+                pv[r].x = (uint64_t)e + 0 < lim ? w[base + e + 0] : 0.f;
+                pv[r].y = (uint64_t)e + 1 < lim ? w[base + e + 1] : 0.f;
+                pv[r].z = (uint64_t)e + 2 < lim ? w[base + e + 2] : 0.f;
+                pv[r].w = (uint64_t)e + 3 < lim ? w[base + e + 3] : 0.f;
+            }
+        }
+    };
+    if (t0 < t1) load_tile(t0);
     for (uint64_t tile = t0; tile < t1; ++tile) {
         const uint64_t base = tile * kTile;
         const uint64_t lim = n - base;   // items e of the tile are valid for e < lim
         __syncthreads();                 // previous tile fully consumed
-        // ---- load: coalesced 16-byte loads, padded transpose to blocked
+        // ---- padded transpose to blocked, then start loading the next tile
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             int e = wbase + r * 128 + lane * 4;
-            float4 v;
-            if (kAligned && (uint64_t)e + 3 < lim) {
-                v = __ldcs(reinterpret_cast<const float4 *>(w + base + e));
-            } else {
-                v.x = (uint64_t)e + 0 < lim ? w[base + e + 0] : 0.f;
-                v.y = (uint64_t)e + 1 < lim ? w[base + e + 1] : 0.f;
-                v.z = (uint64_t)e + 2 < lim ? w[base + e + 2] : 0.f;
-                v.w = (uint64_t)e + 3 < lim ? w[base + e + 3] : 0.f;
-            }
-            sm.wv[pad32(e + 0)] = v.x;
-            sm.wv[pad32(e + 1)] = v.y;
-            sm.wv[pad32(e + 2)] = v.z;
-            sm.wv[pad32(e + 3)] = v.w;
+            sm.wv[pad32(e + 0)] = pv[r].x;
+            sm.wv[pad32(e + 1)] = pv[r].y;
+            sm.wv[pad32(e + 2)] = pv[r].z;
+            sm.wv[pad32(e + 3)] = pv[r].w;
         }
+        if (tile + 1 < t1) load_tile(tile + 1);
         __syncwarp();
         // ---- classify (input order) and count
         uint32_t lmask = 0, vmask = 0;
@@ -729,7 +742,7 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
     const uint64_t Q = P->Q, Qn = P->Qn;
     const uint32_t N = (uint32_t)n;
     const int qshift = P->qshift;
-    const float inv_avg = P->inv_avg, Qf = P->Qf;
+    const float inv_avg = P->inv_avg, invQ = P->invQ;
     const SplitRec R0 = splits[t], R1 = splits[t + 1];
     const uint32_t i0 = R0.i, j0 = R0.j;
     const uint32_t L = R1.i - R0.i, H = R1.j - R0.j, K = L + H;
@@ -813,8 +826,7 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
                     prob = 1.0f;      // rounding left more excess than deficit
                 } else {
                     uint64_t delta = (uint64_t)(a - b);   // < Q < 2^63
-                    float df = __ull2float_rn(delta);
-                    prob = fminf(fmaxf(1.0f - __fdiv_rn(df, Qf), 0.0f), 1.0f);
+                    prob = fminf(fmaxf(1.0f - __ull2float_rn(delta) * invQ, 0.0f), 1.0f);
                 }
                 alias = sItem[L + y + 1];
             } else {

@@ -52,8 +52,10 @@ struct __align__(16) BuildParams {
     float light_max;   // largest FP32 <= avg
     float inv_avg;     // (float)(1 / avg)
     float Qf;          // (float)Q
+    float invQ;        // 1 / Qf: a heavy row keeps 1 - delta * invQ
     uint32_t sections; // s
     uint32_t nseg;     // partition segments
+    uint32_t pad0;
 };
 
 // Workspace layout (all offsets 256-byte aligned).
