@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--impl", choices=["wrs", "reference"], default="wrs")
     ap.add_argument("--n", type=int, default=100_000_000)
     ap.add_argument("--samples", type=int, default=1_000_000_000)
-    ap.add_argument("--section", type=int, default=4096)
+    ap.add_argument("--section", type=int, default=1024)
     ap.add_argument("--dist", default="zipf",
                     choices=["zipf", "uniform", "exponential", "gamma"],
                     help="weights of the single table (default: shuffled power law)")

@@ -74,7 +74,7 @@ typedef struct wrs_row {
 /* Tuning knobs of the build. */
 typedef struct wrs_config {
     /* Buckets per pack section ("N/s items per section", Sec. 2.2); one CTA
-     * packs one section.  Multiple of 256 in [256, 8192]; default 4096. */
+     * packs one section.  Multiple of 256 in [256, 8192]; default 1024. */
     uint32_t section_size;
     /* Split search (Sec. 4.1): WRS_SPLIT_PARY (partial p-ary search,
      * Algorithm 1; default) or WRS_SPLIT_BINARY (one binary search per

@@ -125,7 +125,7 @@ def lib():
     return _lib
 
 
-def config(section_size: int = 4096, split_method: int = SPLIT_PARY) -> Config:
+def config(section_size: int = 1024, split_method: int = SPLIT_PARY) -> Config:
     c = Config()
     lib().wrs_config_default(ctypes.byref(c))
     c.section_size = section_size

@@ -88,7 +88,7 @@ int wrs_abi_version(void) { return 1; }
 void wrs_config_default(wrs_config *cfg) {
     if (!cfg) return;
     memset(cfg, 0, sizeof *cfg);
-    cfg->section_size = 4096;
+    cfg->section_size = 1024;
     cfg->split_method = WRS_SPLIT_PARY;
 }
 

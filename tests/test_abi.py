@@ -71,5 +71,5 @@ def test_layout_is_aligned_and_ordered(lib):
         assert all(o % 256 == 0 for o in offs)
         assert offs == sorted(offs) and offs[-1] < L["total_bytes"]
         assert L["ckl"] - L["lh"] >= 8 * n
-        assert L["sections"] == (n + 4095) // 4096
+        assert L["sections"] == (n + 1023) // 1024
         assert wrs.build_workspace_bytes(n) == L["total_bytes"]
