@@ -56,6 +56,7 @@ Layout make_layout(uint64_t n, uint32_t S) {
     L.sum_bins = take((uint64_t)kSumMaxBlocks * kBands * sizeof(u128));
     L.seg_cnt = take((uint64_t)kMaxSegs * 4);
     L.seg_q = take((uint64_t)kMaxSegs * 8);
+    L.seg_loff = take((uint64_t)(kMaxSegs + 1) * 8);
     L.seg_sum = take((uint64_t)kMaxSegs * sizeof(SegVal));
     L.seg_pre = take((uint64_t)(kMaxSegs + 1) * sizeof(SegVal));
     L.lh = take(n * sizeof(Entry));
@@ -164,46 +165,31 @@ k_total(const u128 *__restrict__ bins_in, int nblocks, uint64_t n, uint32_t sect
 // ===========================================================================
 
 
-// Segment g of G covers tiles [g*T/G, (g+1)*T/G) of kTile items.
-__device__ __forceinline__ void seg_tiles(uint32_t g, uint32_t G, uint64_t T, uint64_t &t0,
-                                          uint64_t &t1) {
-    t0 = (uint64_t)g * T / G;
-    t1 = (uint64_t)(g + 1) * T / G;
+// The partition works on chunks of kChunk items; a warp owns a contiguous
+// run of chunks (a sub-segment).  Sub-segment s of NS covers chunks
+// [s*C/NS, (s+1)*C/NS) of the C chunks.
+__device__ __forceinline__ void sub_range(uint32_t s, uint32_t NS, uint64_t C, uint64_t n,
+                                          uint64_t &a, uint64_t &b) {
+    uint64_t c0 = (uint64_t)s * C / NS, c1 = (uint64_t)(s + 1) * C / NS;
+    a = c0 * kChunk;
+    b = min(c1 * kChunk, n);
+    if (a > b) a = b;
 }
 
-// Block-wide sum of one uint32 per thread (blockDim.x a multiple of 32).
-__device__ __forceinline__ uint32_t block_sum_u32(uint32_t v, uint32_t *red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    v = __reduce_add_sync(0xffffffffu, v);
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    uint32_t t = 0;
-    if (warp == 0) {
-        t = lane < (int)(blockDim.x >> 5) ? red[lane] : 0u;
-        t = __reduce_add_sync(0xffffffffu, t);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) red[0] = t;
-    __syncthreads();
-    uint32_t r = red[0];
-    __syncthreads();
-    return r;
-}
-
-// Per segment (one CTA each, coalesced 16-byte loads): the number of light
-// items and the sum of q over all items (light and heavy, unclamped).
+// Per sub-segment (one warp each, coalesced 16-byte loads): the number of
+// light items and the sum of q over all its items (unclamped).
 __global__ void __launch_bounds__(kPartThreads)
 k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__ P,
-        uint32_t *__restrict__ seg_cnt, uint64_t *__restrict__ seg_q, uint64_t T, uint32_t G,
+        uint32_t *__restrict__ seg_cnt, uint64_t *__restrict__ seg_q, uint64_t C, uint32_t NS,
         int aligned) {
-    __shared__ uint32_t red[32];
-    __shared__ uint64_t redq[32];
     if (P->status) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t s = blockIdx.x * (kPartThreads / 32) + (threadIdx.x >> 5);
+    if (s >= NS) return;
     const float lmax = P->light_max;
     const int qshift = P->qshift;
-    uint64_t t0, t1;
-    seg_tiles(blockIdx.x, G, T, t0, t1);
-    const uint64_t a = t0 * kTile, b = min(t1 * kTile, n);
+    uint64_t a, b;
+    sub_range(s, NS, C, n, a, b);
     uint32_t cnt = 0;
     uint64_t qs = 0;
     uint64_t tail = a;
@@ -211,7 +197,7 @@ k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__
         const float4 *w4 = reinterpret_cast<const float4 *>(w);
         const uint64_t b4 = b / 4;
 #pragma unroll 4
-        for (uint64_t i = a / 4 + threadIdx.x; i < b4; i += kPartThreads) {
+        for (uint64_t i = a / 4 + lane; i < b4; i += 32) {
             float4 v = __ldg(w4 + i);
             cnt += (v.x <= lmax) + (v.y <= lmax) + (v.z <= lmax) + (v.w <= lmax);
             qs += fixed_q(v.x, qshift) + fixed_q(v.y, qshift) + fixed_q(v.z, qshift) +
@@ -219,110 +205,131 @@ k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__
         }
         tail = b4 * 4 > a ? b4 * 4 : a;
     }
-    for (uint64_t i = tail + threadIdx.x; i < b; i += kPartThreads) {
+    for (uint64_t i = tail + lane; i < b; i += 32) {
         float x = __ldg(w + i);
         cnt += (x <= lmax);
         qs += fixed_q(x, qshift);
     }
-    // block sums (q: each thread's sum < 2^63, the segment's too)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, d);
-    if (lane == 0) redq[warp] = qs;
-    cnt = block_sum_u32(cnt, red);
-    if (threadIdx.x == 0) {
-        uint64_t t = 0;
-        for (int k = 0; k < kPartThreads / 32; ++k) t += redq[k];
-        seg_cnt[blockIdx.x] = cnt;
-        seg_q[blockIdx.x] = t;
+    if (lane == 0) {
+        seg_cnt[s] = cnt;
+        seg_q[s] = qs;
     }
 }
 
-// One CTA: Q = sum of all q (the bucket in fixed point) and its derived
-// constants.
-__global__ void __launch_bounds__(kMaxSegs)
-k_qsum(BuildParams *__restrict__ P, const uint64_t *__restrict__ seg_q, uint32_t G, uint64_t n) {
-    __shared__ uint64_t red[32];
-    if (P->status) return;
-    uint64_t v = threadIdx.x < G ? seg_q[threadIdx.x] : 0ull;
+// Block-wide exclusive scan of up to kScanPer values per thread (1024
+// threads); returns this thread's exclusive prefix and the total.
+template <typename T>
+__device__ __forceinline__ void block_scan_1024(T v, T &excl, T &total, T *wtot) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T inc = v;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    for (int d = 1; d < 32; d <<= 1) {
+        T o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) wtot[warp] = inc;
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    uint64_t Q = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) Q += red[k];
-    P->Q = Q;
-    P->Qn = Q / n;
-    P->NQn = (u128)P->Qn * n;
-    P->NQn1 = P->NQn + n;
-    P->Qf = __ull2float_rn(Q);
-    P->invQ = __frcp_rn(P->Qf);
-    P->nseg = G;
+    T pre = 0, tot = 0;
+    for (int k = 0; k < 32; ++k) {
+        T c = wtot[k];
+        pre += (k < warp) ? c : (T)0;
+        tot += c;
+    }
+    __syncthreads();
+    excl = pre + inc - v;
+    total = tot;
 }
 
-struct ScatterShared {
-    float wv[kTile + kTile / 32];       // staged weights (padded, conflict-free)
-    Entry e[kTile + kTile / 16];        // staged entries in list order (padded)
-    uint64_t wsum[kPartThreads / 32];   // per-warp q totals of the list-order pass
-    uint32_t wnl[kPartThreads / 32];    // per-warp light counts
-    uint64_t tile_l;                    // q sum of the tile's lights
-    uint64_t run_sl, run_sh;            // segment-local q sums before the tile
-    uint64_t run_l;                     // global light rank of the tile's first light
-    uint32_t red[32];
-};
+// One CTA (1024 threads): Q = sum of all q, its derived constants, and the
+// global light offset of every sub-segment (exclusive scan of the counts).
+__global__ void __launch_bounds__(1024)
+k_qsum(BuildParams *__restrict__ P, const uint32_t *__restrict__ seg_cnt,
+       const uint64_t *__restrict__ seg_q, uint64_t *__restrict__ seg_loff, uint32_t NS,
+       uint64_t n) {
+    __shared__ uint64_t wtot[32];
+    if (P->status) return;
+    constexpr int kPer = kMaxSegs / 1024;
+    const uint32_t s0 = threadIdx.x * kPer;
+    uint64_t c[kPer], qs = 0, cs = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        uint32_t sidx = s0 + k;
+        c[k] = sidx < NS ? seg_cnt[sidx] : 0;
+        qs += sidx < NS ? seg_q[sidx] : 0;
+        cs += c[k];
+    }
+    uint64_t qe, Q, ce, ctot;
+    block_scan_1024(qs, qe, Q, wtot);
+    block_scan_1024(cs, ce, ctot, wtot);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        uint32_t sidx = s0 + k;
+        if (sidx <= NS) seg_loff[sidx] = ce;
+        ce += c[k];
+    }
+    if (threadIdx.x == 0) {
+        P->Q = Q;
+        P->Qn = Q / n;
+        P->NQn = (u128)P->Qn * n;
+        P->NQn1 = P->NQn + n;
+        P->Qf = __ull2float_rn(Q);
+        P->invQ = __frcp_rn(P->Qf);
+        P->nseg = NS;
+    }
+    (void)qe;
+}
 
 __device__ __forceinline__ void put_ck(CkRec *ck, uint64_t idx, uint32_t seg, uint64_t v) {
     uint4 r = make_uint4(seg, 0u, (uint32_t)v, (uint32_t)(v >> 32));
     *reinterpret_cast<uint4 *>(ck + idx) = r;
 }
 
-// Place every item of the segment: lights at l[rank] (entry rank), heavies at
-// h[rank] (entry n-1-rank); both stay in index order.  Every 32nd list entry
-// gets a checkpoint of the q sum before it (segment-relative).
+struct WarpStage {
+    float wv[kChunk + kChunk / 32];     // staged weights (padded, conflict-free)
+    Entry e[kChunk + kChunk / 16];      // staged entries in list order (padded)
+};
+
+// Place every item: lights at l[rank] (entry rank), heavies at h[rank]
+// (entry n-1-rank); both stay in index order.  Every 32nd list entry gets a
+// checkpoint of the q sum before it, relative to its sub-segment.
 //
-// Per tile: classify in input order (lane = 16 consecutive items), rank with
-// a count scan, stage the entries in list order, then compute q once per
-// entry in list order (thread = 16 consecutive slots, so light and heavy
-// slots rarely share a thread) with one block scan; the checkpoint sums are
-// snapshots of the running sum at the one slot per thread where a
-// checkpoint can fall.
+// Each warp works alone on its sub-segment, chunk by chunk (no CTA barrier):
+// classify in input order (lane = 16 consecutive items), rank with a warp
+// count scan, stage the chunk's entries in list order in the warp's shared
+// memory, then compute q once per entry in list order (lane = 16
+// consecutive slots) with one warp scan; checkpoint sums are snapshots of
+// the running sum at the one slot per lane where a checkpoint can fall.  The
+// next chunk's weights are loaded while the current one is processed.
 template <bool kAligned>
-__global__ void __launch_bounds__(kPartThreads, 3)
+__global__ void __launch_bounds__(kPartThreads, 4)
 k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__ P,
-          const uint32_t *__restrict__ seg_cnt, Entry *__restrict__ lh, CkRec *__restrict__ ckl,
-          CkRec *__restrict__ ckh, SegVal *__restrict__ seg_sum, uint64_t T, uint32_t G) {
-    __shared__ ScatterShared sm;
+          const uint64_t *__restrict__ seg_loff, Entry *__restrict__ lh, CkRec *__restrict__ ckl,
+          CkRec *__restrict__ ckh, SegVal *__restrict__ seg_sum, uint64_t C, uint32_t NS) {
+    __shared__ WarpStage stage[kPartThreads / 32];
     if (P->status) return;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t g = blockIdx.x;
-    uint64_t t0, t1;
-    seg_tiles(g, G, T, t0, t1);
+    const int lane = threadIdx.x & 31;
+    const uint32_t s = blockIdx.x * (kPartThreads / 32) + (threadIdx.x >> 5);
+    if (s >= NS) return;
+    WarpStage &sm = stage[threadIdx.x >> 5];
     const int qshift = P->qshift;
     const uint64_t Qn = P->Qn;
     const float lmax = P->light_max;
-
-    uint32_t pre = 0;
-    for (uint32_t k = tid; k < g; k += kPartThreads) pre += seg_cnt[k];
-    pre = block_sum_u32(pre, sm.red);
-    if (tid == 0) {
-        sm.run_l = pre;
-        sm.run_sl = 0;
-        sm.run_sh = 0;
-    }
-
-    const int wbase = warp * 512;
-    const int e0 = wbase + lane * kPartItems;   // this lane's first item of the tile
-    const int s0 = tid * kPartItems;            // this thread's first list slot
-    // coalesced 16-byte loads of one tile (the next tile is loaded while the
-    // current one is processed)
+    uint64_t a, b;
+    sub_range(s, NS, C, n, a, b);
+    uint64_t run_l = seg_loff[s];       // global rank of the next light
+    uint64_t run_h = a - run_l;         // global rank of the next heavy
+    uint64_t run_sl = 0, run_sh = 0;    // sub-segment-local q sums so far
+    const int e0 = lane * kPartItems;   // this lane's first item of the chunk
+    const int s0 = lane * kPartItems;   // this lane's first list slot
     float4 pv[4];
-    auto load_tile = [&](uint64_t tile) {
-        const uint64_t base = tile * kTile;
+    auto load_chunk = [&](uint64_t base) {
         const uint64_t lim = n - base;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            int e = wbase + r * 128 + lane * 4;
+            int e = r * 128 + lane * 4;
             if (kAligned && (uint64_t)e + 3 < lim) {
                 pv[r] = __ldcs(reinterpret_cast<const float4 *>(w + base + e));
             } else {
@@ -333,21 +340,19 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
             }
         }
     };
-    if (t0 < t1) load_tile(t0);
-    for (uint64_t tile = t0; tile < t1; ++tile) {
-        const uint64_t base = tile * kTile;
-        const uint64_t lim = n - base;   // items e of the tile are valid for e < lim
-        __syncthreads();                 // previous tile fully consumed
-        // ---- padded transpose to blocked, then start loading the next tile
+    if (a < b) load_chunk(a);
+    for (uint64_t base = a; base < b; base += kChunk) {
+        const uint64_t lim = b - base;   // items e of the chunk are valid for e < lim
+        __syncwarp();                    // previous chunk fully consumed
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            int e = wbase + r * 128 + lane * 4;
+            int e = r * 128 + lane * 4;
             sm.wv[pad32(e + 0)] = pv[r].x;
             sm.wv[pad32(e + 1)] = pv[r].y;
             sm.wv[pad32(e + 2)] = pv[r].z;
             sm.wv[pad32(e + 3)] = pv[r].w;
         }
-        if (tile + 1 < t1) load_tile(tile + 1);
+        if (base + kChunk < b) load_chunk(base + kChunk);
         __syncwarp();
         // ---- classify (input order) and count
         uint32_t lmask = 0, vmask = 0;
@@ -365,40 +370,30 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
             uint32_t c2 = __shfl_up_sync(0xffffffffu, icnt, d);
             if (lane >= d) icnt += c2;
         }
-        if (lane == 31) sm.wnl[warp] = icnt;
-        __syncthreads();
-        uint32_t wl = 0, tl = 0;
-#pragma unroll
-        for (int k = 0; k < kPartThreads / 32; ++k) {
-            uint32_t c = sm.wnl[k];
-            wl += (k < warp) ? c : 0u;
-            tl += c;
-        }
-        const uint64_t run_l = sm.run_l;
-        const uint64_t run_h = base - run_l;
-        const uint32_t tv = lim < (uint64_t)kTile ? (uint32_t)lim : (uint32_t)kTile;
+        const uint32_t tl = __shfl_sync(0xffffffffu, icnt, 31);       // lights of the chunk
+        const uint32_t tv = lim < (uint64_t)kChunk ? (uint32_t)lim : (uint32_t)kChunk;
         const uint32_t tnh = tv - tl;
         // ---- stage entries in list order: lights at slot rank, heavies at
-        // slot kTile-1-rank
+        // slot kChunk-1-rank
         {
-            uint32_t lrank = wl + icnt - cnt;
+            uint32_t lrank = icnt - cnt;
             uint32_t hrank = (uint32_t)e0 - lrank;
 #pragma unroll
             for (int k = 0; k < kPartItems; ++k) {
                 if (!((vmask >> k) & 1u)) break;
                 Entry en{(uint32_t)(base + e0 + k), sm.wv[pad32(e0 + k)]};
                 if ((lmask >> k) & 1u) sm.e[pad16(lrank++)] = en;
-                else sm.e[pad16(kTile - 1 - hrank++)] = en;
+                else sm.e[pad16(kChunk - 1 - hrank++)] = en;
             }
         }
-        __syncthreads();
-        // ---- list-order q pass: slots [s0, s0+16) of this thread
-        const uint32_t hstart = kTile - tnh;   // first heavy slot
+        __syncwarp();
+        // ---- list-order q pass: slots [s0, s0+16) of this lane
+        const uint32_t hstart = kChunk - tnh;   // first heavy slot
         const int cl = (int)((32u - (uint32_t)(run_l & 31u)) & 31u);   // light ckpt slots = cl mod 32
-        const int ch = (int)((uint32_t)(run_h + kTile - 1) & 31u);   // heavy ckpt slots = ch mod 32
-        const int kl = (cl - s0) & 31;    // local index of this thread's light ckpt slot (if < 16)
+        const int ch = (int)((uint32_t)(run_h + kChunk - 1) & 31u);  // heavy ckpt slots = ch mod 32
+        const int kl = (cl - s0) & 31;
         const int kh = (ch - s0) & 31;
-        const int kb = (int)tl - s0;      // local index of the light/heavy boundary
+        const int kb = (int)tl - s0;
         uint64_t acc = 0, snap_l = 0, snap_h = 0, snap_b = 0;
 #pragma unroll
         for (int k = 0; k < kPartItems; ++k) {
@@ -411,108 +406,89 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
             acc += v;
             if (k == kh) snap_h = acc;    // inclusive of the heavy ckpt slot
         }
-        // block exclusive scan of the thread totals
         uint64_t inc = acc;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             uint64_t o = __shfl_up_sync(0xffffffffu, inc, d);
             if (lane >= d) inc += o;
         }
-        if (lane == 31) sm.wsum[warp] = inc;
-        __syncthreads();
-        uint64_t X = inc - acc, Tall = 0;
-#pragma unroll
-        for (int k = 0; k < kPartThreads / 32; ++k) {
-            uint64_t c = sm.wsum[k];
-            X += (k < warp) ? c : 0ull;
-            Tall += c;
-        }
-        if (kb >= 0 && kb < kPartItems) sm.tile_l = X + snap_b;
-        if (tl == (uint32_t)kTile && tid == 0) sm.tile_l = Tall;
-        const uint64_t run_sl = sm.run_sl, run_sh = sm.run_sh;
+        const uint64_t X = inc - acc;
+        const uint64_t Tall = __shfl_sync(0xffffffffu, inc, 31);
+        // q sum of the chunk's lights: from the lane that holds slot tl
+        const int owner = tl >= (uint32_t)kChunk ? 31 : (int)(tl / kPartItems);
+        uint64_t TLcand = (kb >= 0 && kb < kPartItems) ? X + snap_b : Tall;
+        const uint64_t TL = tl >= (uint32_t)kChunk ? Tall : __shfl_sync(0xffffffffu, TLcand, owner);
         if (kl < kPartItems && (uint32_t)(s0 + kl) < tl)
-            put_ck(ckl, (run_l + s0 + kl) >> 5, g, run_sl + X + snap_l);
+            put_ck(ckl, (run_l + s0 + kl) >> 5, s, run_sl + X + snap_l);
         if (kh < kPartItems && (uint32_t)(s0 + kh) >= hstart)
-            put_ck(ckh, (run_h + kTile - 1 - (s0 + kh)) >> 5, g, run_sh + (Tall - X - snap_h));
+            put_ck(ckh, (run_h + kChunk - 1 - (s0 + kh)) >> 5, s, run_sh + (Tall - X - snap_h));
         // ---- coalesced copy-out
         uint2 *lh2 = reinterpret_cast<uint2 *>(lh);
         const uint2 *e2 = reinterpret_cast<const uint2 *>(sm.e);
-        for (uint32_t a = tid; a < tl; a += kPartThreads) lh2[run_l + a] = e2[pad16(a)];
-        for (uint32_t b = tid; b < tnh; b += kPartThreads)
-            lh2[n - 1 - (run_h + b)] = e2[pad16(kTile - 1 - b)];
-        __syncthreads();   // tile_l written
-        if (tid == 0) {
-            uint64_t TL = sm.tile_l;
-            sm.run_l = run_l + tl;
-            sm.run_sl = run_sl + TL;
-            sm.run_sh = run_sh + (Tall - TL);
-        }
+        for (uint32_t q = lane; q < tl; q += 32) lh2[run_l + q] = e2[pad16(q)];
+        for (uint32_t q = lane; q < tnh; q += 32)
+            lh2[n - 1 - (run_h + q)] = e2[pad16(kChunk - 1 - q)];
+        run_l += tl;
+        run_h += tnh;
+        run_sl += TL;
+        run_sh += Tall - TL;
     }
-    __syncthreads();
-    if (tid == 0) {
+    if (lane == 0) {
         SegVal v;
-        v.sl = sm.run_sl;
-        v.sh = sm.run_sh;
+        v.sl = run_sl;
+        v.sh = run_sh;
         v.nl = 0;
         v.pad = 0;
-        seg_sum[g] = v;
+        seg_sum[s] = v;
     }
 }
 
-// One CTA: exclusive scan over the segments of (light count, light q sum,
-// heavy q sum); totals nl, nh, D'(nl), E'(nh); the checkpoints that fall on
-// the very end of a list.
-__global__ void __launch_bounds__(kMaxSegs)
-k_segscan(BuildParams *__restrict__ P, const uint32_t *__restrict__ seg_cnt,
+// One CTA (1024 threads): exclusive scan over the sub-segments of (light q
+// sum, heavy q sum); totals nl, nh, D'(nl), E'(nh); the checkpoints that fall
+// on the very end of a list.
+__global__ void __launch_bounds__(1024)
+k_segscan(BuildParams *__restrict__ P, const uint64_t *__restrict__ seg_loff,
           const SegVal *__restrict__ seg_sum, SegVal *__restrict__ seg_pre,
-          CkRec *__restrict__ ckl, CkRec *__restrict__ ckh, uint64_t n, uint32_t G) {
-    __shared__ uint64_t wc[kMaxSegs / 32], wl[kMaxSegs / 32], wh[kMaxSegs / 32];
+          CkRec *__restrict__ ckl, CkRec *__restrict__ ckh, uint64_t n, uint32_t NS) {
+    __shared__ uint64_t wtot[32];
     if (P->status) return;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    uint64_t c = 0, sl = 0, sh = 0;
-    if ((uint32_t)tid < G) {
-        c = seg_cnt[tid];
-        sl = (uint64_t)seg_sum[tid].sl;
-        sh = (uint64_t)seg_sum[tid].sh;
-    }
-    uint64_t ic = c, isl = sl, ish = sh;
+    constexpr int kPer = kMaxSegs / 1024;
+    const uint32_t s0 = threadIdx.x * kPer;
+    uint64_t sl[kPer], sh[kPer], tsl = 0, tsh = 0;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        uint64_t c2 = __shfl_up_sync(0xffffffffu, ic, d);
-        uint64_t a2 = __shfl_up_sync(0xffffffffu, isl, d);
-        uint64_t b2 = __shfl_up_sync(0xffffffffu, ish, d);
-        if (lane >= d) { ic += c2; isl += a2; ish += b2; }
+    for (int k = 0; k < kPer; ++k) {
+        uint32_t sidx = s0 + k;
+        sl[k] = sidx < NS ? (uint64_t)seg_sum[sidx].sl : 0;
+        sh[k] = sidx < NS ? (uint64_t)seg_sum[sidx].sh : 0;
+        tsl += sl[k];
+        tsh += sh[k];
     }
-    if (lane == 31) {
-        wc[warp] = ic;
-        wl[warp] = isl;
-        wh[warp] = ish;
+    uint64_t el, Ltot, eh, Htot;
+    block_scan_1024(tsl, el, Ltot, wtot);
+    block_scan_1024(tsh, eh, Htot, wtot);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        uint32_t sidx = s0 + k;
+        if (sidx <= NS) {
+            SegVal v;
+            v.sl = el;
+            v.sh = eh;
+            v.nl = seg_loff[sidx];
+            v.pad = 0;
+            seg_pre[sidx] = v;
+        }
+        el += sl[k];
+        eh += sh[k];
     }
-    __syncthreads();
-    uint64_t pc = ic - c, psl = isl - sl, psh = ish - sh;
-    for (int k = 0; k < warp; ++k) {
-        pc += wc[k];
-        psl += wl[k];
-        psh += wh[k];
-    }
-    if ((uint32_t)tid <= G) {
-        SegVal v;
-        v.sl = psl;
-        v.sh = psh;
-        v.nl = pc;
-        v.pad = 0;
-        seg_pre[tid] = v;
-    }
-    if ((uint32_t)tid == G) {
-        // thread G holds the totals (its own value is zero)
+    if (threadIdx.x == 0) {
         const uint64_t Q = P->Q;
-        const uint64_t nl = pc, nh = n - nl;
+        const uint64_t nl = seg_loff[NS], nh = n - nl;
         P->nl = nl;
         P->nh = nh;
-        P->Dtot = (u128)nl * Q - (u128)psl * n;
-        P->Etot = (u128)psh * n - (u128)nh * Q;
-        if ((nl & 31u) == 0) put_ck(ckl, nl >> 5, G, 0);
-        if ((nh & 31u) == 0) put_ck(ckh, nh >> 5, G, 0);
+        P->Dtot = (u128)nl * Q - (u128)Ltot * n;
+        P->Etot = (u128)Htot * n - (u128)nh * Q;
+        if ((nl & 31u) == 0) put_ck(ckl, nl >> 5, NS, 0);
+        if ((nh & 31u) == 0) put_ck(ckh, nh >> 5, NS, 0);
     }
 }
 
@@ -797,11 +773,18 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
     }
     __syncthreads();
 
-    // phase 3: merge path.  A(x) = D'(i0+x) = D0 + P[x] (x <= L);
-    // B(y) = E'(j0+y+1) = E0 + P[L+y+1] - P[L] (y < H).
-    const u128 PL = sP[pp8(L)];
-    auto Av = [&](uint32_t x) { return D0 + sP[pp8(x)]; };
-    auto Bv = [&](uint32_t y) { return E0 + (sP[pp8(L + y + 1)] - PL); };
+    // keys relative to D0: lights A'(x) = P[x] = A(x) - D0 >= 0, heavies
+    // B'(y) = E0 - D0 + P[L+y+1] - P[L] = B(y) - D0 (may be negative), stored
+    // in place as two's complement; B(y) <= A(x) iff B'(y) <= A'(x) signed.
+    typedef __int128 i128;
+    {
+        const u128 shift = (E0 - D0) - sP[pp8(L)];
+        __syncthreads();   // every thread has read P[L] before it changes
+        for (uint32_t y = tid; y < H; y += kPackThreads) sP[pp8(L + y + 1)] += shift;
+        __syncthreads();
+    }
+    auto Av = [&](uint32_t x) { return (i128)sP[pp8(x)]; };
+    auto Bv = [&](uint32_t y) { return (i128)sP[pp8(L + y + 1)]; };
     const uint32_t d0 = b0;
     if (d0 >= K) return;
     uint32_t lo = d0 > H ? d0 - H : 0, hi = d0 < L ? d0 : L;
@@ -812,8 +795,8 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
         else lo = m + 1;
     }
     uint32_t x = lo, y = d0 - lo;
-    u128 a = Av(x);                 // D'(i0 + x)
-    u128 b = y < H ? Bv(y) : 0;     // E'(j0 + y + 1)
+    i128 a = Av(x);                 // D'(i0 + x) - D0
+    i128 b = y < H ? Bv(y) : 0;     // E'(j0 + y + 1) - D0
     const uint32_t dend = min(d0 + per, K);
     for (uint32_t d = d0; d < dend; ++d) {
         bool heavy = (y < H) && (x == L || b <= a);
@@ -905,10 +888,11 @@ cudaError_t launch_total(const float *d_w, uint64_t n, unsigned char *ws, const 
     return cudaGetLastError();
 }
 
-uint32_t num_segments(const Layout &L) {
-    uint64_t g = (uint64_t)num_sms() * kSegPerSM;
+uint32_t num_segments(uint64_t n) {
+    const uint64_t C = (n + kChunk - 1) / kChunk;
+    uint64_t g = (uint64_t)num_sms() * kSegPerSM * (kPartThreads / 32);
     if (g > (uint64_t)kMaxSegs - 1) g = kMaxSegs - 1;
-    if (g > L.ntiles) g = L.ntiles;
+    if (g > C) g = C;
     return (uint32_t)(g ? g : 1);
 }
 
@@ -917,20 +901,24 @@ cudaError_t launch_partition(const float *d_w, uint64_t n, unsigned char *ws, co
     BuildParams *P = reinterpret_cast<BuildParams *>(ws + L.params);
     auto *cnt = reinterpret_cast<uint32_t *>(ws + L.seg_cnt);
     auto *segq = reinterpret_cast<uint64_t *>(ws + L.seg_q);
+    auto *loff = reinterpret_cast<uint64_t *>(ws + L.seg_loff);
     auto *sum = reinterpret_cast<SegVal *>(ws + L.seg_sum);
     auto *pre = reinterpret_cast<SegVal *>(ws + L.seg_pre);
     auto *lh = reinterpret_cast<Entry *>(ws + L.lh);
     auto *ckl = reinterpret_cast<CkRec *>(ws + L.ckl);
     auto *ckh = reinterpret_cast<CkRec *>(ws + L.ckh);
-    const uint32_t G = num_segments(L);
+    const uint64_t C = (n + kChunk - 1) / kChunk;
+    const uint32_t NS = num_segments(n);
+    const unsigned blocks = (NS + kPartThreads / 32 - 1) / (kPartThreads / 32);
     const int aligned = ((uintptr_t)d_w % 16) == 0;
-    k_count<<<G, kPartThreads, 0, st>>>(d_w, n, P, cnt, segq, L.ntiles, G, aligned);
-    k_qsum<<<1, kMaxSegs, 0, st>>>(P, segq, G, n);
+    k_count<<<blocks, kPartThreads, 0, st>>>(d_w, n, P, cnt, segq, C, NS, aligned);
+    k_qsum<<<1, 1024, 0, st>>>(P, cnt, segq, loff, NS, n);
     if (aligned)
-        k_scatter<true><<<G, kPartThreads, 0, st>>>(d_w, n, P, cnt, lh, ckl, ckh, sum, L.ntiles, G);
+        k_scatter<true><<<blocks, kPartThreads, 0, st>>>(d_w, n, P, loff, lh, ckl, ckh, sum, C, NS);
     else
-        k_scatter<false><<<G, kPartThreads, 0, st>>>(d_w, n, P, cnt, lh, ckl, ckh, sum, L.ntiles, G);
-    k_segscan<<<1, kMaxSegs, 0, st>>>(P, cnt, sum, pre, ckl, ckh, n, G);
+        k_scatter<false><<<blocks, kPartThreads, 0, st>>>(d_w, n, P, loff, lh, ckl, ckh, sum, C,
+                                                          NS);
+    k_segscan<<<1, 1024, 0, st>>>(P, loff, sum, pre, ckl, ckh, n, NS);
     return cudaGetLastError();
 }
 

@@ -64,6 +64,7 @@ struct Layout {
     uint64_t sum_bins;   // kSumMaxBlocks * kBands u128
     uint64_t seg_cnt;    // kMaxSegs uint32 light counts per segment
     uint64_t seg_q;      // kMaxSegs uint64 q sums per segment (all items)
+    uint64_t seg_loff;   // (kMaxSegs + 1) uint64 global light rank at each segment start
     uint64_t seg_sum;    // kMaxSegs SegVal (segment clamped q sums)
     uint64_t seg_pre;    // (kMaxSegs + 1) SegVal (exclusive prefixes)
     uint64_t lh;         // n Entry
@@ -120,8 +121,9 @@ constexpr int kPartThreads = 256;
 constexpr int kPartItems = 16;
 constexpr int kTile = kPartThreads * kPartItems;   // 4096 items per tile
 constexpr int kPackThreads = 256;
-constexpr int kSegPerSM = 4;          // partition segments (persistent CTAs) per SM
-constexpr int kMaxSegs = 1024;
+constexpr int kSegPerSM = 4;          // partition CTAs per SM (8 warps, one sub-segment each)
+constexpr int kMaxSegs = 8192;        // sub-segments (a multiple of 1024)
+constexpr int kChunk = 512;           // items a partition warp handles at a time
 constexpr int kSplitThreads = 256;    // also p of the partial p-ary search
 
 static inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
