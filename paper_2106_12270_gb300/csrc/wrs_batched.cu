@@ -141,7 +141,7 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
             __syncthreads();
             continue;
         }
-        const int qshift = sm.qshift;
+        const QScale qsc = qscale(sm.qshift);
         const float lmax = sm.lmax;
 
         // ---- Q = sum of q over the table, and the light count
@@ -150,7 +150,7 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
             uint32_t c = 0;
             for (uint64_t a = tid; a < n; a += kBT) {
                 float x = __ldg(wt + a);
-                qs += fixed_q(x, qshift);
+                qs += fixed_q(x, qsc);
                 c += x <= lmax;
             }
 #pragma unroll
@@ -269,8 +269,8 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
                 uint32_t e = b0 + k;
                 if (e >= LH) break;
                 float wv = sm.u.pack.w[pad32(e)];
-                u128 val = (e < L) ? (u128)(Q - (uint64_t)N * light_q(wv, qshift, Qn))
-                                   : mul_nq(N, heavy_q(wv, qshift, Qn)) - Q;
+                u128 val = (e < L) ? (u128)(Q - (uint64_t)N * light_q(wv, qsc, Qn))
+                                   : mul_nq(N, heavy_q(wv, qsc, Qn)) - Q;
                 sm.u.pack.P[pp8b(e + 1)] = val;
                 run += val;
             }
@@ -300,7 +300,7 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
                 uint32_t lo = d > H ? d - H : 0, hi = d < L ? d : L;
                 while (lo < hi) {
                     uint32_t m = (lo + hi) >> 1;
-                    bool p = (d - m == 0) || (m == L) || (Bv(d - m - 1) <= Av(m));
+                    bool p = (d - m == 0) || (m == L) || sweep_le(Bv(d - m - 1), Av(m));
                     if (p) hi = m;
                     else lo = m + 1;
                 }
@@ -314,17 +314,21 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
                 u128 b = y < H ? Bv(y) : 0;
                 const uint32_t dend = min(d0 + per_out, K);
                 for (uint32_t d = d0; d < dend; ++d) {
-                    bool heavy = (y < H) && (x == L || b <= a);
+                    bool heavy = (y < H) && (x == L || sweep_le(b, a));
                     uint32_t item, alias;
                     float prob;
                     if (heavy) {
                         item = sm.u.pack.item[L + y];
                         if (j + y + 1 < nh) {
-                            if (b > a) {
+                            if (!sweep_le(b, a)) {
                                 prob = 1.0f;
                             } else {
-                                uint64_t delta = (uint64_t)(a - b);
-                                prob = fminf(fmaxf(1.0f - __ull2float_rn(delta) * sm.invQ, 0.0f),
+                                // kept fraction 1 - (A - B) 2^15 / Q on the rounded prefixes
+                                const int64_t delta =
+                                    (int64_t)((a >> kKeyShift) - (b >> kKeyShift));
+                                prob = fminf(fmaxf(1.0f - __ll2float_rn(delta) *
+                                                              (sm.invQ * (float)(1u << kKeyShift)),
+                                                   0.0f),
                                              1.0f);
                             }
                             alias = sm.u.pack.item[L + y + 1];

@@ -29,16 +29,19 @@
 // bucket is Q = sum of all q_i (exactly, so deficits and excesses balance).
 // For light items d'_a = Q - N q_a >= 0 (N times its deficit) and for heavy
 // items e'_b = N q_b - Q > 0.  D'(i) = sum of the first i light d', E'(j) =
-// sum of the first j heavy e' (both < 2^94).  The sweep closes heavy h[j]
-// (its remaining weight fits in one bucket) iff E'(j+1) <= D'(i), else light
-// l[i]; a heavy row keeps 1 - (D'(i) - E'(j+1)) / Q of its bucket.  All of it
-// is exact integer arithmetic: the splits and every section end agree
+// sum of the first j heavy e' (both < 2^95), exact in 128-bit integers.  The
+// sweep closes heavy h[j] (its remaining weight fits in one bucket) iff
+// E'(j+1) <= D'(i), both rounded down to multiples of 2^15 (sweep_le: a
+// bucket is >= 2^61 units), else light l[i]; a heavy row keeps 1 - (D'(i) -
+// E'(j+1)) / Q of its bucket, on the same rounded prefixes.  The split search
+// and the pack use this one rule, so the splits and every section end agree
 // exactly, and no FP64 unit is used per item.  The rounding of q costs at
 // most N/(2Q) <= 2^-32 of a bucket per item, far below the FP32 rounding of
 // the stored probabilities.
 #include <stdio.h>
 
 #include "wrs_device.cuh"
+
 
 namespace wrs {
 
@@ -187,7 +190,7 @@ k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__
     const uint32_t s = blockIdx.x * (kPartThreads / 32) + (threadIdx.x >> 5);
     if (s >= NS) return;
     const float lmax = P->light_max;
-    const int qshift = P->qshift;
+    const QScale qsc = qscale(P->qshift);
     uint64_t a, b;
     sub_range(s, NS, C, n, a, b);
     uint32_t cnt = 0;
@@ -200,15 +203,15 @@ k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__
         for (uint64_t i = a / 4 + lane; i < b4; i += 32) {
             float4 v = __ldg(w4 + i);
             cnt += (v.x <= lmax) + (v.y <= lmax) + (v.z <= lmax) + (v.w <= lmax);
-            qs += fixed_q(v.x, qshift) + fixed_q(v.y, qshift) + fixed_q(v.z, qshift) +
-                  fixed_q(v.w, qshift);
+            qs += fixed_q(v.x, qsc) + fixed_q(v.y, qsc) + fixed_q(v.z, qsc) +
+                  fixed_q(v.w, qsc);
         }
         tail = b4 * 4 > a ? b4 * 4 : a;
     }
     for (uint64_t i = tail + lane; i < b; i += 32) {
         float x = __ldg(w + i);
         cnt += (x <= lmax);
-        qs += fixed_q(x, qshift);
+        qs += fixed_q(x, qsc);
     }
     cnt = __reduce_add_sync(0xffffffffu, cnt);
 #pragma unroll
@@ -314,7 +317,7 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
     const uint32_t s = blockIdx.x * (kPartThreads / 32) + (threadIdx.x >> 5);
     if (s >= NS) return;
     WarpStage &sm = stage[threadIdx.x >> 5];
-    const int qshift = P->qshift;
+    const QScale qsc = qscale(P->qshift);
     const uint64_t Qn = P->Qn;
     const float lmax = P->light_max;
     uint64_t a, b;
@@ -377,13 +380,15 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
         // slot kChunk-1-rank
         {
             uint32_t lrank = icnt - cnt;
-            uint32_t hrank = (uint32_t)e0 - lrank;
+            uint32_t hslot = kChunk - 1 - ((uint32_t)e0 - lrank);
 #pragma unroll
             for (int k = 0; k < kPartItems; ++k) {
-                if (!((vmask >> k) & 1u)) break;
-                Entry en{(uint32_t)(base + e0 + k), sm.wv[pad32(e0 + k)]};
-                if ((lmask >> k) & 1u) sm.e[pad16(lrank++)] = en;
-                else sm.e[pad16(kChunk - 1 - hrank++)] = en;
+                const bool lt = (lmask >> k) & 1u;
+                const uint32_t slot = lt ? lrank : hslot;
+                if ((vmask >> k) & 1u)
+                    sm.e[pad16(slot)] = Entry{(uint32_t)(base + e0 + k), sm.wv[pad32(e0 + k)]};
+                lrank += lt;
+                hslot -= !lt;
             }
         }
         __syncwarp();
@@ -394,15 +399,15 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
         const int kl = (cl - s0) & 31;
         const int kh = (ch - s0) & 31;
         const int kb = (int)tl - s0;
+        const uint64_t Qn1 = Qn + 1;
         uint64_t acc = 0, snap_l = 0, snap_h = 0, snap_b = 0;
 #pragma unroll
         for (int k = 0; k < kPartItems; ++k) {
-            uint32_t slot = (uint32_t)(s0 + k);
+            const uint32_t slot = (uint32_t)(s0 + k);
             if (k == kl) snap_l = acc;
             if (k == kb) snap_b = acc;
-            uint64_t v = 0;
-            if (slot < tl) v = light_q(sm.e[pad16(slot)].w, qshift, Qn);
-            else if (slot >= hstart) v = heavy_q(sm.e[pad16(slot)].w, qshift, Qn);
+            const uint64_t q = fixed_q(sm.e[pad16(slot)].w, qsc);
+            const uint64_t v = slot < tl ? min(q, Qn) : (slot >= hstart ? max(q, Qn1) : 0ull);
             acc += v;
             if (k == kh) snap_h = acc;    // inclusive of the heavy ckpt slot
         }
@@ -527,7 +532,7 @@ __device__ __forceinline__ bool pred_c(const SplitCtx &C, uint64_t k, uint64_t c
     uint64_t i = 32 * c;
     if (i < lo) return false;
     if (i >= hi) return true;
-    return ck_E(C, (k - i) >> 5) <= ck_D(C, c);
+    return sweep_le(ck_E(C, (k - i) >> 5), ck_D(C, c));
 }
 
 __device__ __forceinline__ void crange(const SplitCtx &C, uint64_t k, uint64_t &clo,
@@ -557,11 +562,11 @@ __device__ void split_fine(const SplitCtx &C, const BuildParams &Pm, uint64_t k,
         u128 d = 0, e = 0;
         if (lb + lane < C.nl) {
             Entry en = C.lh[lb + lane];
-            d = (u128)(Pm.Q - N * light_q(en.w, Pm.qshift, Pm.Qn));   // <= Q
+            d = (u128)(Pm.Q - N * light_q(en.w, qscale(Pm.qshift), Pm.Qn));   // <= Q
         }
         if (hb + lane < C.nh) {
             Entry en = C.lh[C.n - 1 - (hb + lane)];
-            e = mul_nq(N, heavy_q(en.w, Pm.qshift, Pm.Qn)) - Pm.Q;
+            e = mul_nq(N, heavy_q(en.w, qscale(Pm.qshift), Pm.Qn)) - Pm.Q;
         }
         u128 dinc = d, einc = e;
 #pragma unroll
@@ -575,7 +580,7 @@ __device__ void split_fine(const SplitCtx &C, const BuildParams &Pm, uint64_t k,
         u128 Dl = Dbase + dinc;                                   // D'(lb + 1 + lane)
         u128 Eh = Ebase + shfl_u128(eexc, 31 - lane);             // E'(k - (lb + 1 + lane))
         uint64_t i = lb + 1 + lane;
-        bool ok = i >= lo && i <= hi && (i == hi || Eh <= Dl);
+        bool ok = i >= lo && i <= hi && (i == hi || sweep_le(Eh, Dl));
         uint32_t bal = __ballot_sync(0xffffffffu, ok);
         int first = bal ? __ffs(bal) - 1 : 31;
         ans = lb + 1 + first;
@@ -686,151 +691,180 @@ __global__ void k_split_ends(const BuildParams *__restrict__ P, SplitRec *__rest
 // a5: pack
 // ===========================================================================
 
-// Shared memory of one pack CTA for a section of up to S buckets:
-//   P[K+1] (u128 prefix of the section's d' (lights first) then e'
-//   (heavies), one pad slot every 8 entries against bank conflicts),
-//   item[K+1] (uint32), w[K+1 padded] (float).
-__host__ __device__ inline uint32_t pack_p_slots(uint32_t S) { return S + 1 + (S + 1) / 8 + 1; }
-__host__ __device__ inline uint32_t pack_smem_bytes(uint32_t S) {
-    uint32_t K1 = S + 1;
-    uint32_t b = 16 * pack_p_slots(S);          // P
-    b += 4 * K1;                                // item
-    b += 4 * (K1 + K1 / 32 + 1);                // w (padded)
-    return (b + 15) & ~15u;
+// Pack (Sec. 2.2 "pack", staged in shared memory as in Sec. 4.2): each
+// section of up to S buckets is swept by one CTA of S/kPer threads, each
+// owning kPer consecutive positions of the sweep.
+//
+// The sweep closes heavy h[j] before light l[i] iff its excess prefix does
+// not exceed the deficit prefix, compared at a resolution of 2^kKeyShift
+// units (wrs_internal.cuh, sweep_le): floor(E'(j+1) / 2^15) <= floor(D'(i) /
+// 2^15).  Inside a section the keys are those floors relative to the
+// section start, as 64-bit integers:
+//   A(x) = floor(D'(i0+x) / 2^15) - floor(D0 / 2^15)   in [0, 2^61]
+//   B(y) = floor(E'(j0+y+1) / 2^15) - floor(D0 / 2^15) > -2^48
+// (B(0) > -Q because the split took the smallest i; B is capped at 2^62,
+// above every A: a capped heavy cannot close in the section.)  The prefix
+// sums themselves are exact (128-bit); only the stored keys are rounded, the
+// same way everywhere, so the table does not depend on the section size.
+constexpr int kKeyCap62 = 62;
+
+// Shared memory: sK (keys: slot x = A(x), slot L+y+1 = B(y)) and sE (the
+// section's entries: lights, heavies, then the first heavy after the
+// section); both pad one 8-byte slot in 16 against bank conflicts.
+__host__ __device__ inline uint32_t pk16(uint32_t e) { return e + (e >> 4); }
+__host__ __device__ inline uint32_t pack_per(uint32_t S) { return S <= 4096 ? 8 : 16; }
+__host__ __device__ inline uint32_t pack_slots(uint32_t S) { return pk16(S + 1) + 1; }
+__host__ __device__ inline uint32_t pack_smem_bytes(uint32_t S) { return 16 * pack_slots(S); }
+
+// floor((c + p) / 2^15) for the 128-bit two's-complement sum c + p, capped
+// at 2^62 (the true value is above -2^48).
+__device__ __forceinline__ int64_t sweep_key(u128 c, u128 p) {
+    const __int128 v = (__int128)(c + p) >> kKeyShift;
+    return v < ((__int128)1 << kKeyCap62) ? (int64_t)v : ((int64_t)1 << kKeyCap62);
 }
 
-__device__ __forceinline__ uint32_t pp8(uint32_t e) { return e + (e >> 3); }
-
-__global__ void __launch_bounds__(kPackThreads)
+template <int kPer>
+__global__ void __launch_bounds__(512)
 k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
        const SplitRec *__restrict__ splits, uint2 *__restrict__ rows, uint64_t n,
        uint32_t S) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ u128 s_w[16];
     if (P->status) return;
-    const uint32_t K1 = S + 1;
-    u128 *sP = reinterpret_cast<u128 *>(smem);
-    uint32_t *sItem = reinterpret_cast<uint32_t *>(smem + 16 * pack_p_slots(S));
-    float *sW = reinterpret_cast<float *>(smem + 16 * pack_p_slots(S) + 4 * K1);
+    int64_t *sK = reinterpret_cast<int64_t *>(smem);
+    uint2 *sE = reinterpret_cast<uint2 *>(smem + 8 * pack_slots(S));
 
-    const int tid = threadIdx.x;
+    const uint32_t T = blockDim.x;
+    const uint32_t tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
     const uint32_t t = blockIdx.x;
     const uint64_t nh = P->nh;
     const uint64_t Q = P->Q, Qn = P->Qn;
     const uint32_t N = (uint32_t)n;
-    const int qshift = P->qshift;
-    const float inv_avg = P->inv_avg, invQ = P->invQ;
+    const QScale qsc = qscale(P->qshift);
+    const float inv_avg = P->inv_avg;
+    const float invQk = P->invQ * (float)(1u << kKeyShift);   // 1/Q per key unit
     const SplitRec R0 = splits[t], R1 = splits[t + 1];
     const uint32_t i0 = R0.i, j0 = R0.j;
     const uint32_t L = R1.i - R0.i, H = R1.j - R0.j, K = L + H;
     const uint32_t extra = (R1.j < nh) ? 1u : 0u;
-    const u128 D0 = R0.D, E0 = R0.E;
     if (R1.i < R0.i || R1.j < R0.j || K > S || R1.i > P->nl || R1.j > nh) {
         if (tid == 0) atomicOr(const_cast<uint32_t *>(&P->status), ERR_INTERNAL);
         return;   // inconsistent splits: write nothing
     }
 
     // phase 1: coalesced load of the section's lights, heavies and the next
-    // heavy item (the alias of the last rows)
-    for (uint32_t e = tid; e < K + extra; e += kPackThreads) {
-        Entry en = (e < L) ? lh[(uint64_t)i0 + e] : lh[n - 1 - ((uint64_t)j0 + (e - L))];
-        sItem[e] = en.item;
-        sW[pad32(e)] = en.w;
+    // heavy item (the alias of the last rows), all loads in flight at once
+    {
+        const uint2 *lh2 = reinterpret_cast<const uint2 *>(lh);
+        uint2 v[kPer + 1];
+#pragma unroll
+        for (int r = 0; r <= kPer; ++r) {
+            const uint32_t e = tid + r * T;
+            if (e < K + extra)
+                v[r] = __ldcs(lh2 + (e < L ? (uint64_t)i0 + e : n - 1 - ((uint64_t)j0 + (e - L))));
+        }
+#pragma unroll
+        for (int r = 0; r <= kPer; ++r) {
+            const uint32_t e = tid + r * T;
+            if (e < K + extra) sE[pk16(e)] = v[r];
+        }
     }
     __syncthreads();
 
-    // phase 2: blocked values (d' for lights, e' for heavies) written to
-    // P[e+1], then a block exclusive scan in place: P[e] = sum of values < e
-    const uint32_t per = (S + kPackThreads - 1) / kPackThreads;
-    const uint32_t b0 = tid * per;
+    // value of position e: d' = Q - N q for a light, e' = N q - Q for a heavy
+    auto value = [&](uint32_t e) -> u128 {
+        const float wv = __uint_as_float(sE[pk16(e)].y);
+        return (e < L) ? (u128)(Q - (uint64_t)N * light_q(wv, qsc, Qn))
+                       : mul_nq(N, heavy_q(wv, qsc, Qn)) - Q;
+    };
+    // phase 2: block scan of the exact thread sums
+    const uint32_t b0 = tid * kPer;
     u128 run = 0;
-    for (uint32_t k = 0; k < per; ++k) {
-        uint32_t e = b0 + k;
-        if (e >= K) break;
-        float wv = sW[pad32(e)];
-        u128 val = (e < L) ? (u128)(Q - (uint64_t)N * light_q(wv, qshift, Qn))
-                           : mul_nq(N, heavy_q(wv, qshift, Qn)) - Q;
-        sP[pp8(e + 1)] = val;
-        run += val;
-    }
-    __shared__ u128 s_wsum[kPackThreads / 32];
-    const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k)
+        if (b0 + k < K) run += value(b0 + k);
     u128 inc = run;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        u128 o = shfl_up_u128(inc, d);
+        const u128 o = shfl_up_u128(inc, d);
         if (lane >= d) inc += o;
     }
-    if (lane == 31) s_wsum[warp] = inc;
+    if (lane == 31) s_w[warp] = inc;
     __syncthreads();
-    u128 pre = inc - run;
-    for (int k = 0; k < warp; ++k) pre += s_wsum[k];
-    if (tid == 0) sP[0] = 0;
-    for (uint32_t k = 0; k < per; ++k) {
-        uint32_t e = b0 + k;
-        if (e >= K) break;
-        pre += sP[pp8(e + 1)];
-        sP[pp8(e + 1)] = pre;
+
+    // phase 3: keys.  With P(e) the exact prefix of the values: D'(i0+x) =
+    // D0 + P(x), so A(x) = floor((D0 mod 2^15 + P(x)) / 2^15); E'(j0+y+1) =
+    // E0 + P(L+y+1) - P(L) with P(L) = D1 - D0 (the section's light deficit,
+    // fixed by the split), so B(y) = floor((E0 - D1 + D0 mod 2^15 +
+    // P(L+y+1)) / 2^15).
+    {
+        u128 pre = inc - run;
+        for (int k = 0; k < warp; ++k) pre += s_w[k];
+        const u128 d0l = R0.D & (u128)((1u << kKeyShift) - 1);
+        const u128 cl = d0l, ch = R0.E - R1.D + d0l;
+        bool bad = false;
+        if (tid == 0) sK[pk16(0)] = 0;
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            const uint32_t e = b0 + k;
+            if (e < K) {
+                pre += value(e);
+                sK[pk16(e + 1)] = sweep_key(e < L ? cl : ch, pre);
+                // the section's own sums must meet the split's: D1 - D0
+                // after the last light, E1 - E0 + D1 - D0 at the end
+                if (e + 1 == L) bad |= pre != R1.D - R0.D;
+                if (e + 1 == K && H) bad |= pre != (R1.E - R0.E) + (R1.D - R0.D);
+            }
+        }
+        if (bad) atomicOr(const_cast<uint32_t *>(&P->status), ERR_INTERNAL);
     }
     __syncthreads();
 
-    // keys relative to D0: lights A'(x) = P[x] = A(x) - D0 >= 0, heavies
-    // B'(y) = E0 - D0 + P[L+y+1] - P[L] = B(y) - D0 (may be negative), stored
-    // in place as two's complement; B(y) <= A(x) iff B'(y) <= A'(x) signed.
-    typedef __int128 i128;
-    {
-        const u128 shift = (E0 - D0) - sP[pp8(L)];
-        __syncthreads();   // every thread has read P[L] before it changes
-        for (uint32_t y = tid; y < H; y += kPackThreads) sP[pp8(L + y + 1)] += shift;
-        __syncthreads();
-    }
-    auto Av = [&](uint32_t x) { return (i128)sP[pp8(x)]; };
-    auto Bv = [&](uint32_t y) { return (i128)sP[pp8(L + y + 1)]; };
+    // phase 4: merge path.  The number x of lights closed before position d0
+    // is the smallest x with B(d0-x-1) <= A(x) (or x = L, or x = d0).
+    auto Av = [&](uint32_t x) { return sK[pk16(x)]; };
+    auto Bv = [&](uint32_t y) { return sK[pk16(L + y + 1)]; };
     const uint32_t d0 = b0;
-    if (d0 >= K) return;
-    uint32_t lo = d0 > H ? d0 - H : 0, hi = d0 < L ? d0 : L;
-    while (lo < hi) {   // smallest x with (d0-x == 0) || x == L || B(d0-x-1) <= A(x)
-        uint32_t m = (lo + hi) >> 1;
-        bool p = (d0 - m == 0) || (m == L) || (Bv(d0 - m - 1) <= Av(m));
-        if (p) hi = m;
-        else lo = m + 1;
-    }
-    uint32_t x = lo, y = d0 - lo;
-    i128 a = Av(x);                 // D'(i0 + x) - D0
-    i128 b = y < H ? Bv(y) : 0;     // E'(j0 + y + 1) - D0
-    const uint32_t dend = min(d0 + per, K);
-    for (uint32_t d = d0; d < dend; ++d) {
-        bool heavy = (y < H) && (x == L || b <= a);
-        uint32_t item, alias;
-        float prob;
-        if (heavy) {
-            item = sItem[L + y];
-            if ((uint64_t)j0 + y + 1 < nh) {
-                if (b > a) {
-                    prob = 1.0f;      // rounding left more excess than deficit
-                } else {
-                    uint64_t delta = (uint64_t)(a - b);   // < Q < 2^63
-                    prob = fminf(fmaxf(1.0f - __ull2float_rn(delta) * invQ, 0.0f), 1.0f);
-                }
-                alias = sItem[L + y + 1];
-            } else {
-                prob = 1.0f;          // last heavy item keeps its whole bucket
-                alias = item;
-            }
-            ++y;
-            if (y < H) b = Bv(y);
-        } else {
-            item = sItem[x];
-            if ((uint64_t)j0 + y < nh) {
-                prob = fminf(sW[pad32(x)] * inv_avg, 1.0f);
-                alias = sItem[L + y];
-            } else {
-                prob = 1.0f;          // no heavy item left to fill the bucket
-                alias = item;
-            }
-            ++x;
-            a = Av(x);
+    if (d0 < K) {
+        uint32_t lo = d0 > H ? d0 - H : 0, hi = d0 < L ? d0 : L;
+        while (lo < hi) {
+            const uint32_t m = (lo + hi) >> 1;
+            const bool p = (d0 - m == 0) || (m == L) || (Bv(d0 - m - 1) <= Av(m));
+            if (p) hi = m;
+            else lo = m + 1;
         }
-        rows[item] = make_uint2(__float_as_uint(prob), alias);
+        uint32_t x = lo, y = d0 - lo;
+        int64_t a = Av(x);
+        int64_t b = y < H ? Bv(y) : 0;
+        // one output per step: close heavy y (b <= a, or no light left) or
+        // light x.  The next heavy in the list fills the bucket's rest: list
+        // offset y+1 for a heavy, y for a light (sE slot K holds the first
+        // heavy after the section); without one the item keeps its bucket.
+        // A heavy keeps 1 - (A - B) 2^15 / Q of its bucket.
+        const uint32_t hleft = (uint32_t)min(nh - (uint64_t)j0, (uint64_t)K + 1);
+#pragma unroll
+        for (int k = 0; k < kPer; ++k) {
+            if (d0 + k < K) {
+                const bool heavy = (y < H) && (x == L || b <= a);
+                const uint32_t pos = heavy ? L + y : x;
+                const uint32_t nxt = heavy ? y + 1 : y;
+                const bool has = nxt < hleft;
+                const uint32_t alias = sE[pk16(has ? L + nxt : pos)].x;
+                float prob;
+                if (heavy) {
+                    prob = b > a ? 1.0f
+                                 : fminf(fmaxf(1.0f - __ll2float_rn(a - b) * invQk, 0.0f), 1.0f);
+                } else {
+                    prob = fminf(__uint_as_float(sE[pk16(x)].y) * inv_avg, 1.0f);
+                }
+                if (!has) prob = 1.0f;
+                rows[sE[pk16(pos)].x] = make_uint2(__float_as_uint(prob), alias);
+                const int64_t v = sK[pk16(heavy ? L + y + 2 : x + 1)];
+                if (heavy) { ++y; b = v; }
+                else { ++x; a = v; }
+            }
+        }
     }
 }
 
@@ -942,22 +976,30 @@ cudaError_t launch_split(uint64_t n, unsigned char *ws, const Layout &L, uint32_
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack(uint64_t n, wrs_row *d_rows, unsigned char *ws, const Layout &L,
-                        uint32_t S, cudaStream_t st) {
+template <int kPer>
+static cudaError_t launch_pack_t(uint64_t n, wrs_row *d_rows, unsigned char *ws, const Layout &L,
+                                 uint32_t S, cudaStream_t st) {
     const BuildParams *P = reinterpret_cast<const BuildParams *>(ws + L.params);
-    uint32_t smem = pack_smem_bytes(S);
+    const uint32_t smem = pack_smem_bytes(S);
     static uint32_t configured = 0;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_pack<kPer>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e) return e;
         configured = smem;
     }
-    k_pack<<<(unsigned)L.sections, kPackThreads, smem, st>>>(
+    const uint32_t threads = (S + kPer - 1) / kPer;   // S is a multiple of 256: whole warps
+    k_pack<kPer><<<(unsigned)L.sections, threads, smem, st>>>(
         P, reinterpret_cast<const Entry *>(ws + L.lh),
         reinterpret_cast<const SplitRec *>(ws + L.splits), reinterpret_cast<uint2 *>(d_rows), n,
         S);
     return cudaGetLastError();
+}
+
+cudaError_t launch_pack(uint64_t n, wrs_row *d_rows, unsigned char *ws, const Layout &L,
+                        uint32_t S, cudaStream_t st) {
+    return pack_per(S) == 8 ? launch_pack_t<8>(n, d_rows, ws, L, S, st)
+                            : launch_pack_t<16>(n, d_rows, ws, L, S, st);
 }
 
 cudaError_t launch_info(unsigned char *ws, const Layout &L, wrs_build_info *d_info,

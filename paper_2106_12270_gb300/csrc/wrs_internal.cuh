@@ -147,32 +147,57 @@ __device__ __forceinline__ u128 shfl_u128(u128 v, int src) {
     return ((u128)hi << 64) | lo;
 }
 
-// Fixed point of an FP32 weight: q = round(w * 2^S) < 2^63.  With
-// w = m * 2^(e'-150) (e' = max(biased exponent, 1)), q = m * 2^(e' + qshift);
-// a negative exponent rounds half up.  The weight must be finite (checked by
-// the total-weight step before any caller runs); the sign bit is ignored
-// (-0 is 0).
-__device__ __forceinline__ uint64_t fixed_q(float w, int qshift) {
-    uint32_t u = __float_as_uint(w) & 0x7fffffffu;
-    uint32_t e = u >> 23;
-    uint32_t m = (u & 0x7fffffu) | (e ? 0x800000u : 0u);
-    int sh = (int)(e ? e : 1u) + qshift;
-    if (sh >= 0) return (uint64_t)m << sh;   // sh <= 39 for every weight <= W
-    int r = -sh;
-    return r > 24 ? 0ull : (uint64_t)((m + (1u << (r - 1))) >> r);
+// Fixed point of an FP32 weight: q = round(w * 2^S) < 2^63, halves rounded
+// up.  S = qshift + 150 lies in [-97, 210] (the total W is in [2^-149,
+// 2^159)); 2^S is applied as two exact power-of-two factors, so x = w * 2^S
+// is exact unless it falls below the FP32 normal range, where it is far
+// below 1/2 and q = 0 however it rounds (x < 2^62: no overflow).  Then
+// q = floor(x + 1/2) with the addition rounded down: from 2^23 on x is a
+// multiple of 1/2 and the sum is exact or rounds back to the integer x;
+// below, floor(x + 1/2) is itself a float <= x + 1/2, so rounding down never
+// crosses it.  Needs IEEE subnormals (no flush to zero).  The weight must be
+// finite and not negative (checked by the total-weight step before any caller
+// runs; -0 gives 0).
+struct QScale {
+    float c1, c2;   // 2^min(S, 127), 2^(S - min(S, 127))
+};
+__device__ __forceinline__ QScale qscale(int qshift) {
+    const int S = qshift + 150;
+    const int s1 = S < 127 ? S : 127;
+    QScale r;
+    r.c1 = __int_as_float((s1 + 127) << 23);
+    r.c2 = __int_as_float((S - s1 + 127) << 23);
+    return r;
+}
+__device__ __forceinline__ uint64_t fixed_q(float w, QScale qs) {
+    const float x = __fmul_rn(__fmul_rn(w, qs.c1), qs.c2);
+    return __float2ull_rd(__fadd_rd(x, 0.5f));
 }
 
 // q of a light item clamped to at most Qn = floor(Q/N), so that its scaled
 // deficit d' = Q - N*q >= 0; q of a heavy item clamped to at least Qn+1, so
 // that its scaled excess e' = N*q - Q > 0.
-__device__ __forceinline__ uint64_t light_q(float w, int qshift, uint64_t Qn) {
-    uint64_t q = fixed_q(w, qshift);
+__device__ __forceinline__ uint64_t light_q(float w, QScale qs, uint64_t Qn) {
+    uint64_t q = fixed_q(w, qs);
     return q > Qn ? Qn : q;
 }
-__device__ __forceinline__ uint64_t heavy_q(float w, int qshift, uint64_t Qn) {
-    uint64_t q = fixed_q(w, qshift);
+__device__ __forceinline__ uint64_t heavy_q(float w, QScale qs, uint64_t Qn) {
+    uint64_t q = fixed_q(w, qs);
     return q <= Qn ? Qn + 1 : q;
 }
+// The sweep's comparison (Sec. 2.2): heavy h[j] closes before light l[i]
+// iff its excess prefix E'(j+1) does not exceed the deficit prefix D'(i).
+// Both are compared rounded down to multiples of 2^kKeyShift: a bucket is
+// Q >= 2^61 units, so this differs from the unrounded comparison only when
+// the two agree to 2^-46 of a bucket, ties stay ties, and the 64-bit keys of
+// the pack kernel implement it exactly.  Every kernel (split, pack, batched)
+// uses this one rule, so the table does not depend on the section size or
+// the code path.
+constexpr int kKeyShift = 15;
+__device__ __forceinline__ bool sweep_le(u128 E, u128 D) {
+    return (E >> kKeyShift) <= (D >> kKeyShift);
+}
+
 // N * q as 128 bits (q < 2^63, N < 2^31).
 __device__ __forceinline__ u128 mul_nq(uint32_t N, uint64_t q) { return (u128)q * N; }
 

@@ -91,6 +91,43 @@ def test_prefix_checkpoints_exact(kind):
             assert abs(got - want) <= Fraction(n * (i + n), Q), (which, c)
 
 
+def fixed_point_q(w, S):
+    """q_i = floor(w_i 2^S + 1/2): each weight rounded to the fixed point,
+    halves up, in exact rational arithmetic."""
+    scale = Fraction(2) ** S
+    half = Fraction(1, 2)
+    return [int((Fraction(float(x)) * scale + half) // 1) for x in w]
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_fixed_point_exact(kind):
+    """The fixed point bit for bit: the scale puts W 2^S in [2^61, 2^62),
+    Q is the sum of the rounded weights, and every checkpoint is the exact sum
+    of the clamped q (lights at most floor(Q/N), heavies at least that + 1)."""
+    n = 20011
+    w = inputs.by_name(kind, n, 17)
+    b = Built(w)
+    S = b.info["scale"]
+    Wx = sum((Fraction(float(x)) for x in w), Fraction(0))
+    assert 2**61 <= Wx * Fraction(2) ** S < 2**62
+    q = fixed_point_q(w, S)
+    Q = sum(q)
+    assert b.info["Q"] == Q
+    Qn = Q // n
+    li, _, hi, _ = b.lists()
+    for which, lst, clamp in (("ckl", li, lambda v: min(v, Qn)),
+                              ("ckh", hi, lambda v: max(v, Qn + 1))):
+        ck = b.checkpoints(which)
+        acc, want = 0, []
+        for a, idx in enumerate(lst):
+            if a % 32 == 0:
+                want.append(acc)
+            acc += clamp(q[int(idx)])
+        if len(lst) % 32 == 0:
+            want.append(acc)
+        assert ck == want, which
+
+
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("section", [256, 1024, 4096])
 @pytest.mark.parametrize("method", [wrs.SPLIT_PARY, wrs.SPLIT_BINARY])
