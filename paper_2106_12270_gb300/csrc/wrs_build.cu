@@ -190,7 +190,7 @@ k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__
     const uint32_t s = blockIdx.x * (kPartThreads / 32) + (threadIdx.x >> 5);
     if (s >= NS) return;
     const float lmax = P->light_max;
-    const QScale qsc = qscale(P->qshift);
+    const int qshift = P->qshift;
     uint64_t a, b;
     sub_range(s, NS, C, n, a, b);
     uint32_t cnt = 0;
@@ -203,15 +203,15 @@ k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__
         for (uint64_t i = a / 4 + lane; i < b4; i += 32) {
             float4 v = __ldg(w4 + i);
             cnt += (v.x <= lmax) + (v.y <= lmax) + (v.z <= lmax) + (v.w <= lmax);
-            qs += fixed_q(v.x, qsc) + fixed_q(v.y, qsc) + fixed_q(v.z, qsc) +
-                  fixed_q(v.w, qsc);
+            qs += fixed_q_bits(v.x, qshift) + fixed_q_bits(v.y, qshift) +
+                  fixed_q_bits(v.z, qshift) + fixed_q_bits(v.w, qshift);
         }
         tail = b4 * 4 > a ? b4 * 4 : a;
     }
     for (uint64_t i = tail + lane; i < b; i += 32) {
         float x = __ldg(w + i);
         cnt += (x <= lmax);
-        qs += fixed_q(x, qsc);
+        qs += fixed_q_bits(x, qshift);
     }
     cnt = __reduce_add_sync(0xffffffffu, cnt);
 #pragma unroll

@@ -174,6 +174,21 @@ __device__ __forceinline__ uint64_t fixed_q(float w, QScale qs) {
     return __float2ull_rd(__fadd_rd(x, 0.5f));
 }
 
+// The same q from the weight's bits, in integer operations only: with w =
+// m 2^(e'-150) (e' = max(biased exponent, 1)), q = m 2^(e' + qshift), a
+// negative exponent rounding half up (qshift = S - 150).  Equal to fixed_q
+// for every finite non-negative weight; the kernels use whichever form keeps
+// their busiest pipe free.
+__device__ __forceinline__ uint64_t fixed_q_bits(float w, int qshift) {
+    const uint32_t u = __float_as_uint(w) & 0x7fffffffu;
+    const uint32_t e = u >> 23;
+    const uint32_t m = (u & 0x7fffffu) | (e ? 0x800000u : 0u);
+    const int sh = (int)(e ? e : 1u) + qshift;
+    if (sh >= 0) return (uint64_t)m << sh;   // sh <= 39 for every weight <= W
+    const int r = -sh;
+    return r > 24 ? 0ull : (uint64_t)((m + (1u << (r - 1))) >> r);
+}
+
 // q of a light item clamped to at most Qn = floor(Q/N), so that its scaled
 // deficit d' = Q - N*q >= 0; q of a heavy item clamped to at least Qn+1, so
 // that its scaled excess e' = N*q - Q > 0.
