@@ -300,21 +300,23 @@ int wrs_sample_batched_rows(const wrs_row *d_rows, const uint64_t *d_off, uint32
 /* ---------------------------------------------------------------------- */
 /* A server owns one worker thread on the calling thread's current device.
  * Requests are queued from any thread and served in steps: all admissible
- * requests that have arrived are built with one batched-build launch and
- * sampled with one sampling launch; up to max_inflight steps run on the GPU
- * at once while new arrivals form the next step.  Builds are admitted while
- * resident tables plus in-flight scratch stay within hbm_budget bytes (a
- * table costs 8 bytes per item while resident and about 12 bytes per item
- * while it is built); they are admitted in arrival order, and a build that
- * can never fit fails with WRS_ENOMEM.  The paper has no counterpart: it is
- * how a serving system uses the method.
+ * requests that have arrived are built -- tables below 2^17 items with one
+ * batched-build launch, larger ones each with the multi-CTA pipeline of
+ * wrs_build_rows (section size 1024, p-ary splits) -- and sampled with one
+ * sampling launch; up to max_inflight steps run on the GPU at once while new
+ * arrivals form the next step.  Builds are admitted while resident tables
+ * plus in-flight scratch stay within hbm_budget bytes (a table costs 8 bytes
+ * per item while resident and about 12-14 bytes per item while it is
+ * built); they are admitted in arrival order, and a build that can never fit
+ * fails with WRS_ENOMEM.  The paper has no counterpart: it is how a serving
+ * system uses the method.
  *
  * Results do not depend on batching: a table equals wrs_build_rows of the
  * same weights, and the samples of a request equal wrs_sample_rows(rows, n,
  * 0, count, seed, stream_lo, WRS_TAG_NAIVE) on that table.
  *
  * Buffers passed to a request must stay valid until the request is done:
- * weights w (host or device, 1..2^24 items) and the sample output out
+ * weights w (host or device, 1..2^31-1 items) and the sample output out
  * (host or device, count uint32).  Tickets name requests; the ticket of a
  * build also names its table. */
 typedef struct wrs_server wrs_server;

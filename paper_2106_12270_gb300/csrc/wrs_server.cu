@@ -7,10 +7,12 @@
 //     keep their arrival order, samples and releases are never held back by
 //     a waiting build;
 //   * each step gathers every admissible request that has arrived, builds all
-//     of its tables with one batched-build launch and draws all of its
-//     samples with one request-sampling launch, on two streams; a sample of a
-//     table built in an earlier step that is still running waits for that
-//     table's event on the GPU, not on the host;
+//     of its small tables with one batched-build launch (one CTA per table)
+//     and each large table (kLargeBuild items or more) with the multi-CTA
+//     single-table pipeline, and draws all of its samples with one
+//     request-sampling launch, on two streams; a sample of a table built in
+//     an earlier step that is still running waits for that table's event on
+//     the GPU, not on the host;
 //   * up to max_inflight steps are on the GPU at once, and requests that
 //     arrive meanwhile go into the next step, so new work overlaps running
 //     work (continuous batching, not a queue drained one batch at a time).
@@ -37,9 +39,21 @@ cudaError_t launch_build_batched(const float *, const uint64_t *, uint32_t, cons
                                  wrs_table_summary *, cudaStream_t);
 cudaError_t launch_sample_requests(const SampleReq *, const uint32_t *, uint32_t, uint32_t,
                                    cudaStream_t);
+cudaError_t launch_total(const float *, uint64_t, unsigned char *, const Layout &, cudaStream_t);
+cudaError_t launch_partition(const float *, uint64_t, unsigned char *, const Layout &,
+                             cudaStream_t);
+cudaError_t launch_split(uint64_t, unsigned char *, const Layout &, uint32_t, uint32_t,
+                         cudaStream_t);
+cudaError_t launch_pack(uint64_t, wrs_row *, unsigned char *, const Layout &, uint32_t,
+                        cudaStream_t);
+cudaError_t launch_info(unsigned char *, const Layout &, wrs_build_info *, cudaStream_t);
 int cuda_status(cudaError_t e);
 
-constexpr uint64_t kMaxBatchItems = 1ull << 24;   // larger tables use the single-table path
+// A table this large is built by the multi-CTA single-table pipeline: one CTA
+// of the batched kernel would sweep it alone for milliseconds.
+constexpr uint64_t kLargeBuild = 1ull << 17;
+constexpr uint32_t kLargeSection = 1024;
+constexpr uint64_t kMaxServerItems = (1ull << 31) - 1;
 constexpr uint64_t kReqChunkH = 1u << 16;         // samples per CTA of the request sampler
 constexpr uint32_t kMaxReqPerStep = 8192;
 
@@ -91,6 +105,9 @@ struct Step {
     cudaEvent_t done = nullptr, built = nullptr;
     std::vector<Request *> reqs;
     std::vector<uint64_t> tables;   // built in this step, in summary order
+    std::vector<uint64_t> ltables;  // large tables built in this step, in linfo order
+    std::vector<void *> lscratch;   // their weights + workspaces
+    wrs_build_info *linfo = nullptr;    // pinned
     void *scratch = nullptr;
     uint64_t scratch_bytes = 0;
     int slot = -1;
@@ -167,6 +184,16 @@ void wrs_server::retire() {
             tr.nh = s.nh;
             if (tr.status == WRS_OK) items_built += tr.n;
         }
+        for (size_t k = 0; k < st->ltables.size(); ++k) {
+            TableRec &tr = tables[st->ltables[k]];
+            const wrs_build_info &b = st->linfo[k];
+            tr.built = true;
+            tr.status = err != WRS_OK ? err : b.status;
+            tr.W = b.W;
+            tr.nl = b.nl;
+            tr.nh = b.nh;
+            if (tr.status == WRS_OK) items_built += tr.n;
+        }
         for (Request *r : st->reqs) {
             int status = err;
             if (status == WRS_OK) {
@@ -186,15 +213,18 @@ void wrs_server::retire() {
             finish(r, status, t);
         }
         // failed builds give their memory back
-        for (uint64_t id : st->tables) {
-            TableRec &tr = tables[id];
-            if (tr.status != WRS_OK && !tr.gone) {
-                tr.gone = true;
-                cudaFreeAsync(tr.rows, s_sample);
-                resident -= tr.bytes;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (uint64_t id : pass ? st->ltables : st->tables) {
+                TableRec &tr = tables[id];
+                if (tr.status != WRS_OK && !tr.gone) {
+                    tr.gone = true;
+                    cudaFreeAsync(tr.rows, s_sample);
+                    resident -= tr.bytes;
+                }
             }
         }
         if (st->scratch) cudaFreeAsync(st->scratch, s_sample);
+        for (void *p : st->lscratch) cudaFreeAsync(p, s_sample);
         transient -= st->scratch_bytes;
         slots[st->slot].busy = false;
         cudaEventDestroy(st->done);
@@ -206,7 +236,7 @@ void wrs_server::retire() {
 
 bool wrs_server::launch_step() {
     int slot = -1;
-    std::vector<Request *> builds, samples, releases;
+    std::vector<Request *> builds, large, samples, releases;
     uint64_t build_items = 0, sample_total = 0, host_samples = 0, scratch = 0;
     {
         std::lock_guard<std::mutex> lk(mu);
@@ -223,7 +253,12 @@ bool wrs_server::launch_step() {
             queue.pop_front();
             if (taken >= kMaxReqPerStep) { keep.push_back(r); continue; }
             if (r->kind == K_BUILD) {
-                uint64_t rows_b = 8 * r->n, scr = 12 * r->n + 4096;
+                // transient: weights + l/h array (batched), or weights + the
+                // single-table workspace (large)
+                uint64_t rows_b = 8 * r->n,
+                         scr = r->n >= kLargeBuild
+                                   ? 4 * r->n + make_layout(r->n, kLargeSection).total + 4096
+                                   : 12 * r->n + 4096;
                 if (rows_b + scr > budget) { finish(r, WRS_ENOMEM, t); continue; }
                 if (builds_blocked || resident + transient + scratch + rows_b + scr > budget) {
                     builds_blocked = true;   // keep arrival order among builds
@@ -236,8 +271,12 @@ bool wrs_server::launch_step() {
                 tr.n = r->n;
                 tr.bytes = rows_b;
                 tables[r->id] = tr;
-                builds.push_back(r);
-                build_items += r->n;
+                if (r->n >= kLargeBuild) {
+                    large.push_back(r);
+                } else {
+                    builds.push_back(r);
+                    build_items += r->n;
+                }
                 ++taken;
             } else {
                 auto it = tables.find(r->table);
@@ -271,7 +310,7 @@ bool wrs_server::launch_step() {
             }
         }
         queue.swap(keep);
-        if (builds.empty() && samples.empty() && releases.empty()) return false;
+        if (builds.empty() && large.empty() && samples.empty() && releases.empty()) return false;
         slots[slot].busy = true;
         transient += scratch;
         peak = std::max(peak, resident + transient);
@@ -284,9 +323,11 @@ bool wrs_server::launch_step() {
     Slot &sl = slots[slot];
     // pinned staging: offsets, row pointers, summaries, request descriptors
     const uint32_t nb = (uint32_t)builds.size(), ns = (uint32_t)samples.size();
+    const uint32_t nlg = (uint32_t)large.size();
     uint64_t need_pin = align_up(8 * (nb + 1), 64) + align_up(8 * nb, 64) +
                         align_up(sizeof(wrs_table_summary) * nb, 64) +
-                        align_up(sizeof(SampleReq) * ns, 64) + align_up(4 * (ns + 1), 64);
+                        align_up(sizeof(SampleReq) * ns, 64) + align_up(4 * (ns + 1), 64) +
+                        align_up(sizeof(wrs_build_info) * nlg, 64);
     if (need_pin > sl.pin_bytes) {
         if (sl.pin) cudaFreeHost(sl.pin);
         sl.pin_bytes = std::max<uint64_t>(need_pin, 1 << 20);
@@ -307,12 +348,15 @@ bool wrs_server::launch_step() {
     SampleReq *h_req = (SampleReq *)pp;
     pp += align_up(sizeof(SampleReq) * ns, 64);
     uint32_t *h_chunk = (uint32_t *)pp;
+    pp += align_up(4 * (ns + 1), 64);
+    st->linfo = (wrs_build_info *)pp;
     // device scratch for the step
     uint64_t dev_bytes = 256 + align_up(4 * build_items, 256) + align_up(8 * build_items, 256) +
                          align_up(8 * (nb + 1), 256) + align_up(8 * nb, 256) +
                          align_up(sizeof(wrs_table_summary) * nb, 256) +
                          align_up(sizeof(SampleReq) * ns, 256) + align_up(4 * (ns + 1), 256) +
-                         align_up(4 * host_samples, 256);
+                         align_up(4 * host_samples, 256) +
+                         align_up(sizeof(wrs_build_info) * nlg, 256);
     unsigned char *d = nullptr;
     if (!e) e = cudaMallocFromPoolAsync((void **)&d, dev_bytes, pool, s_build);
     st->scratch = d;
@@ -331,6 +375,41 @@ bool wrs_server::launch_step() {
     SampleReq *d_req = (SampleReq *)take(sizeof(SampleReq) * ns);
     uint32_t *d_chunk = (uint32_t *)take(4 * (ns + 1));
     uint32_t *d_stage = (uint32_t *)take(4 * host_samples);
+    wrs_build_info *d_linfo = (wrs_build_info *)take(sizeof(wrs_build_info) * nlg);
+    // ---- large builds: the single-table pipeline, one after another
+    for (uint32_t k = 0; k < nlg && !e; ++k) {
+        Request *r = large[k];
+        const Layout L = make_layout(r->n, kLargeSection);
+        uint64_t bytes;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            bytes = tables[r->id].bytes;
+        }
+        wrs_row *rp = nullptr;
+        unsigned char *lw = nullptr;
+        e = cudaMallocFromPoolAsync((void **)&rp, bytes, pool, s_build);
+        if (!e) e = cudaMallocFromPoolAsync((void **)&lw, align_up(4 * r->n, 256) + L.total, pool,
+                                            s_build);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            tables[r->id].rows = rp;
+        }
+        st->ltables.push_back(r->id);
+        if (lw) st->lscratch.push_back(lw);
+        if (e) break;
+        float *wk = (float *)lw;
+        unsigned char *ws = lw + align_up(4 * r->n, 256);
+        e = cudaMemcpyAsync(wk, r->w, 4 * r->n,
+                            r->w_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s_build);
+        if (!e) e = launch_total(wk, r->n, ws, L, s_build);
+        if (!e) e = launch_partition(wk, r->n, ws, L, s_build);
+        if (!e) e = launch_split(r->n, ws, L, kLargeSection, WRS_SPLIT_PARY, s_build);
+        if (!e) e = launch_pack(r->n, rp, ws, L, kLargeSection, s_build);
+        if (!e) e = launch_info(ws, L, d_linfo + k, s_build);
+    }
+    if (!e && nlg)
+        e = cudaMemcpyAsync(st->linfo, d_linfo, sizeof(wrs_build_info) * nlg,
+                            cudaMemcpyDeviceToHost, s_build);
     // ---- builds
     if (!e && nb) {
         h_off[0] = 0;
@@ -363,10 +442,13 @@ bool wrs_server::launch_step() {
         if (!e)
             e = cudaMemcpyAsync(st->summ, d_summ, sizeof(wrs_table_summary) * nb,
                                 cudaMemcpyDeviceToHost, s_build);
-        if (!e) e = cudaEventCreateWithFlags(&st->built, cudaEventDisableTiming);
+    }
+    if (!e && (nb || nlg)) {
+        e = cudaEventCreateWithFlags(&st->built, cudaEventDisableTiming);
         if (!e) e = cudaEventRecord(st->built, s_build);
         std::lock_guard<std::mutex> lk(mu);
         for (uint32_t k = 0; k < nb; ++k) tables[builds[k]->id].ready = st->built;
+        for (uint32_t k = 0; k < nlg; ++k) tables[large[k]->id].ready = st->built;
     }
     // ---- samples (wait on the GPU for tables still being built)
     if (!e && ns) {
@@ -428,6 +510,7 @@ bool wrs_server::launch_step() {
     }
     std::lock_guard<std::mutex> lk(mu);
     st->reqs = builds;
+    st->reqs.insert(st->reqs.end(), large.begin(), large.end());
     st->reqs.insert(st->reqs.end(), samples.begin(), samples.end());
     st->reqs.insert(st->reqs.end(), releases.begin(), releases.end());
     ++steps;
@@ -508,7 +591,7 @@ static int submit(wrs_server *s, Request *r, uint64_t *ticket) {
 
 int wrs_server_submit_build(wrs_server *s, const float *w, uint64_t n, int w_on_device,
                             uint64_t *ticket) {
-    if (!s || !w || !ticket || n == 0 || n > kMaxBatchItems) return WRS_EINVAL;
+    if (!s || !w || !ticket || n == 0 || n > kMaxServerItems) return WRS_EINVAL;
     Request *r = new Request();
     r->kind = K_BUILD;
     r->w = w;

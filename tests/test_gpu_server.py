@@ -139,3 +139,27 @@ def test_unknown_released_and_bad_tables():
         assert srv.wait(srv.build(z)) == wrs.EZEROSUM
     finally:
         srv.close()
+
+
+def test_large_builds_single_table_path():
+    """Tables of 2^17 items and more take the multi-CTA pipeline: the same
+    rows as a single build, data errors reported per table, memory given
+    back on release."""
+    srv = wrs.Server(1 << 30, 2)
+    try:
+        sizes = [(1 << 17) - 1, 1 << 17, 700_001]
+        ws = [inputs.by_name("exponential", n, 60 + n) for n in sizes]
+        tks = [srv.build(torch.from_numpy(w).cuda()) for w in ws]
+        bad = inputs.uniform(1 << 18, 9)
+        bad[12345] = np.nan
+        tbad = srv.build(torch.from_numpy(bad).cuda())
+        for tk in tks:
+            assert srv.wait(tk) == wrs.OK
+        assert srv.wait(tbad) == wrs.ENONFINITE
+        for w, tk in zip(ws, tks):
+            assert torch.equal(served_rows(srv, tk, w.size), Built(w).rows_t.cpu())
+        before = srv.stats()["resident_bytes"]
+        assert srv.wait(srv.release(tks[2])) == wrs.OK
+        assert srv.stats()["resident_bytes"] == before - 8 * sizes[2]
+    finally:
+        srv.close()
