@@ -36,7 +36,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 BUILD_BYTES_PER_ITEM = 32      # read w twice, write + read lh, write rows
 SAMPLE_BYTES_PER_DRAW = 36     # one 32-byte row sector + a 4-byte output
-KERNELS_PER_BUILD = 9          # sum, total, count, scatter, segscan, split ends, split, pack, info
+KERNELS_PER_BUILD = 10         # sum, total, count, qsum, scatter, segscan, split ends, split, pack, info
 KERNELS_PER_SAMPLE = 1
 # batched build/sample are timed separately (extra keys), not in gpu_launches
 

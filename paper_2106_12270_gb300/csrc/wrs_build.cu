@@ -724,10 +724,10 @@ __device__ __forceinline__ int64_t sweep_key(u128 c, u128 p) {
 }
 
 template <int kPer>
-__global__ void __launch_bounds__(512)
-k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
-       const SplitRec *__restrict__ splits, uint2 *__restrict__ rows, uint64_t n,
-       uint32_t S) {
+__device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
+                                             const Entry *__restrict__ lh,
+                                             const SplitRec *__restrict__ splits,
+                                             uint2 *__restrict__ rows, uint64_t n, uint32_t S) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ u128 s_w[16];
     if (P->status) return;
@@ -772,18 +772,32 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
     }
     __syncthreads();
 
-    // value of position e: d' = Q - N q for a light, e' = N q - Q for a heavy
-    auto value = [&](uint32_t e) -> u128 {
-        const float wv = __uint_as_float(sE[pk16(e)].y);
-        return (e < L) ? (u128)(Q - (uint64_t)N * light_q(wv, qsc, Qn))
-                       : mul_nq(N, heavy_q(wv, qsc, Qn)) - Q;
-    };
-    // phase 2: block scan of the exact thread sums
+    // phase 2: the clamped fixed point q of each owned position (kept in
+    // registers) and the thread's exact value sum: sum over lights of d' = Q
+    // - N q and over heavies of e' = N q - Q, i.e. (nl - nh) Q + N (sum of
+    // heavy q - sum of light q); then a block scan of the thread sums.
     const uint32_t b0 = tid * kPer;
-    u128 run = 0;
+    uint64_t qv[kPer];
+    uint64_t sql = 0, sqh = 0;
+    uint32_t nlt = 0, nht = 0;
 #pragma unroll
-    for (int k = 0; k < kPer; ++k)
-        if (b0 + k < K) run += value(b0 + k);
+    for (int k = 0; k < kPer; ++k) {
+        const uint32_t e = b0 + k;
+        qv[k] = 0;
+        if (e < K) {
+            const uint64_t q = fixed_q(__uint_as_float(sE[pk16(e)].y), qsc);
+            if (e < L) {
+                qv[k] = q > Qn ? Qn : q;
+                sql += qv[k];
+                ++nlt;
+            } else {
+                qv[k] = q <= Qn ? Qn + 1 : q;
+                sqh += qv[k];
+                ++nht;
+            }
+        }
+    }
+    const u128 run = (u128)nlt * Q - (u128)nht * Q + (u128)N * sqh - (u128)N * sql;
     u128 inc = run;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -802,22 +816,25 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
         u128 pre = inc - run;
         for (int k = 0; k < warp; ++k) pre += s_w[k];
         const u128 d0l = R0.D & (u128)((1u << kKeyShift) - 1);
-        const u128 cl = d0l, ch = R0.E - R1.D + d0l;
-        bool bad = false;
+        const u128 ch = R0.E - R1.D + d0l;
         if (tid == 0) sK[pk16(0)] = 0;
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             const uint32_t e = b0 + k;
             if (e < K) {
-                pre += value(e);
-                sK[pk16(e + 1)] = sweep_key(e < L ? cl : ch, pre);
-                // the section's own sums must meet the split's: D1 - D0
-                // after the last light, E1 - E0 + D1 - D0 at the end
-                if (e + 1 == L) bad |= pre != R1.D - R0.D;
-                if (e + 1 == K && H) bad |= pre != (R1.E - R0.E) + (R1.D - R0.D);
+                if (e < L) {
+                    pre += (u128)(Q - (uint64_t)N * qv[k]);
+                    sK[pk16(e + 1)] = (int64_t)((pre + d0l) >> kKeyShift);   // < 2^61
+                } else {
+                    pre += mul_nq(N, qv[k]) - Q;
+                    sK[pk16(e + 1)] = sweep_key(ch, pre);
+                }
             }
         }
-        if (bad) atomicOr(const_cast<uint32_t *>(&P->status), ERR_INTERNAL);
+        // the section's own sums must meet the split's: the thread holding
+        // position K-1 has P(K) = D1 - D0 + E1 - E0
+        if (b0 < K && b0 + kPer >= K && pre != (R1.D - R0.D) + (R1.E - R0.E))
+            atomicOr(const_cast<uint32_t *>(&P->status), ERR_INTERNAL);
     }
     __syncthreads();
 
@@ -866,6 +883,20 @@ k_pack(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
             }
         }
     }
+}
+
+// Sections of up to 4096 buckets: 8 positions per thread, at most 48
+// registers (10 CTAs of 128 threads per SM at S = 1024).
+__global__ void __maxnreg__(48)
+k_pack8(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
+        const SplitRec *__restrict__ splits, uint2 *__restrict__ rows, uint64_t n, uint32_t S) {
+    pack_section<8>(P, lh, splits, rows, n, S);
+}
+// Larger sections: 16 positions per thread, 512 threads.
+__global__ void __launch_bounds__(512)
+k_pack16(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
+         const SplitRec *__restrict__ splits, uint2 *__restrict__ rows, uint64_t n, uint32_t S) {
+    pack_section<16>(P, lh, splits, rows, n, S);
 }
 
 // ===========================================================================
@@ -977,19 +1008,21 @@ cudaError_t launch_split(uint64_t n, unsigned char *ws, const Layout &L, uint32_
 }
 
 template <int kPer>
-static cudaError_t launch_pack_t(uint64_t n, wrs_row *d_rows, unsigned char *ws, const Layout &L,
+static cudaError_t launch_pack_t(void (*kern)(const BuildParams *, const Entry *, const SplitRec *,
+                                              uint2 *, uint64_t, uint32_t),
+                                 uint64_t n, wrs_row *d_rows, unsigned char *ws, const Layout &L,
                                  uint32_t S, cudaStream_t st) {
     const BuildParams *P = reinterpret_cast<const BuildParams *>(ws + L.params);
     const uint32_t smem = pack_smem_bytes(S);
     static uint32_t configured = 0;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_pack<kPer>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e) return e;
         configured = smem;
     }
     const uint32_t threads = (S + kPer - 1) / kPer;   // S is a multiple of 256: whole warps
-    k_pack<kPer><<<(unsigned)L.sections, threads, smem, st>>>(
+    kern<<<(unsigned)L.sections, threads, smem, st>>>(
         P, reinterpret_cast<const Entry *>(ws + L.lh),
         reinterpret_cast<const SplitRec *>(ws + L.splits), reinterpret_cast<uint2 *>(d_rows), n,
         S);
@@ -998,8 +1031,8 @@ static cudaError_t launch_pack_t(uint64_t n, wrs_row *d_rows, unsigned char *ws,
 
 cudaError_t launch_pack(uint64_t n, wrs_row *d_rows, unsigned char *ws, const Layout &L,
                         uint32_t S, cudaStream_t st) {
-    return pack_per(S) == 8 ? launch_pack_t<8>(n, d_rows, ws, L, S, st)
-                            : launch_pack_t<16>(n, d_rows, ws, L, S, st);
+    return pack_per(S) == 8 ? launch_pack_t<8>(k_pack8, n, d_rows, ws, L, S, st)
+                            : launch_pack_t<16>(k_pack16, n, d_rows, ws, L, S, st);
 }
 
 cudaError_t launch_info(unsigned char *ws, const Layout &L, wrs_build_info *d_info,
