@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the host-side mass check of the timed table")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--build-only", action="store_true",
@@ -225,7 +227,7 @@ def run_gpu(args):
     rows = torch.empty(n, dtype=torch.int64, device="cuda")
     if args.build_only:
         count = 0
-        args.no_batched = args.no_serving = args.no_e2e = True
+        args.no_batched = args.no_serving = args.no_e2e = args.no_accuracy = True
     out = torch.empty(max(count, 1), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -303,6 +305,24 @@ def run_gpu(args):
         e2e = {"value": world * n / (e2e_ms / 1e3), "unit": "items/s",
                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n,
                "ms_per_step": e2e_ms}
+
+    # accuracy of the timed table: the reconstructed mass of every item
+    # against N w_i / W in FP64 (plain numpy on the host; the stated bound is
+    # |mass_i - N w_i/W| <= 1e-5 max(1, N w_i/W))
+    accuracy = None
+    if not args.no_accuracy:
+        import numpy as np
+        raw = rows.cpu().numpy().view(np.uint32).reshape(-1, 2)
+        prob = raw[:, 0].view(np.float32).astype(np.float64)
+        mass = prob + np.bincount(raw[:, 1], weights=1.0 - prob, minlength=n)
+        wd = w_host.astype(np.float64)
+        expect = wd * (n / float(np.sum(wd)))
+        err = np.abs(mass - expect) / np.maximum(1.0, expect)
+        accuracy = {"max_mass_error": float(err.max()), "mean_mass_error": float(err.mean()),
+                    "bound": 1e-5, "items_checked": n,
+                    "prefix_arithmetic": "exact 128-bit fixed-point prefix sums; sweep "
+                                         "compares them at 2^-15 units (2^-46 of a bucket)"}
+        del raw, prob, mass, wd, expect, err
 
     # sectioned sampling (Sec. 5): same draw count, samples grouped by section
     sec = {}
@@ -383,7 +403,7 @@ def run_gpu(args):
             "batched": batched,
             "serving": serving_res,
             "roofline": dominant, "build_roofline": build_roof, "sample_roofline": sample_roof,
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "cpu_baseline": cpu, "e2e": e2e, "accuracy": accuracy, "clocks": clk,
             "gpu_launches": args.steps * (KERNELS_PER_BUILD + KERNELS_PER_SAMPLE),
         }
         print(json.dumps(line), flush=True)
@@ -419,11 +439,17 @@ def run_batched(args, world, rank):
     out = torch.empty(ntab * per_table, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step():
-        bb.build(w, off, rows, order)
-        wrs.sample_batched_rows(rows, off, ntab, cnt_off, 2, out)
+    def step(st=None):
+        bb.build(w, off, rows, order, stream=st)
+        wrs.sample_batched_rows(rows, off, ntab, cnt_off, 2, out, stream=st)
 
     for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # segment-to-block tiling picked by the autotuner (times every candidate
+    # on this batch; later builds use the fastest)
+    best, cand = bb.autotune(w, off, rows, order, force=True)
+    for _ in range(2):
         step()
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -441,6 +467,21 @@ def run_batched(args, world, rank):
     ok = int((summ["status"] == wrs.OK).sum())
     build_ms = statistics.mean(bms)
     sample_ms = statistics.mean(sms)
+
+    # the same step captured once as a CUDA graph and replayed
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step(torch.cuda.current_stream())
+    g.replay()
+    torch.cuda.synchronize()
+    gms = []
+    for _ in range(args.steps):
+        ev[0].record(stream)
+        g.replay()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        gms.append(ev[0].elapsed_time(ev[1]))
+    graph_ms = statistics.mean(gms)
 
     # baseline: the plain single-table path, one launch sequence per table
     probe = min(ntab, 2000)
@@ -466,7 +507,12 @@ def run_batched(args, world, rank):
             "per_table_probe": f"first {probe} tables timed, scaled by item share {frac:.4f}",
             "speedup_vs_per_table": per_table_ms / build_ms,
             "samples": ntab * per_table, "sample_ms": sample_ms,
-            "samples_per_s": ntab * per_table / (sample_ms / 1e3)}
+            "samples_per_s": ntab * per_table / (sample_ms / 1e3),
+            "tuning": {"best": best,
+                       "candidates": [{k: c[k] for k in ("threads", "chunk", "ms")}
+                                      for c in cand]},
+            "graph_step_ms": graph_ms,
+            "graph_items_per_s": total / (graph_ms / 1e3)}
 
 
 def run_serving(args, rank):

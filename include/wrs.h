@@ -286,6 +286,39 @@ int wrs_build_batched_rows(const float *d_w, const uint64_t *d_off, uint32_t nta
                            const uint32_t *d_order, wrs_row *d_rows, void *d_ws,
                            uint64_t ws_bytes, wrs_table_summary *d_info, void *stream);
 
+/* Tiling of the batched build.  The table does not depend on it (chunk ends
+ * are splits of the same sweep), only the time does. */
+typedef struct wrs_batch_tuning {
+    uint32_t threads;      /* threads of a CTA: 256 or 512 */
+    uint32_t chunk;        /* buckets swept per chunk: 512, 1024, 2048 or 4096 */
+    uint32_t ctas_per_sm;  /* resident CTAs per SM; 0 = as many as fit */
+    float ms;              /* measured time of one build (wrs_batch_autotune) */
+    uint32_t reserved[4];
+} wrs_batch_tuning;
+
+/* The default tiling: 256 threads, chunks of 1024 buckets, full occupancy. */
+int wrs_batch_tuning_default(wrs_batch_tuning *t);
+
+/* wrs_build_batched_rows with an explicit tiling (NULL = the default).
+ * WRS_EINVAL for a tiling outside the listed values. */
+int wrs_build_batched_rows_tuned(const float *d_w, const uint64_t *d_off, uint32_t ntab,
+                                 const uint32_t *d_order, wrs_row *d_rows, void *d_ws,
+                                 uint64_t ws_bytes, wrs_table_summary *d_info,
+                                 const wrs_batch_tuning *tuning, void *stream);
+
+/* Autotuner for the batched build: builds this batch once with every
+ * candidate tiling (threads x chunk), times each with CUDA events on
+ * `stream` (best of two runs after a warm-up), and returns the fastest in
+ * *best; `all` (room for up to *nall entries, may be NULL) receives every
+ * candidate with its time and *nall their number.  The buffers hold a valid
+ * build afterwards.  The choice is cached per batch shape (number of tables
+ * and total items); a later call with the same shape returns the cached
+ * choice without timing unless `force` is nonzero.  Synchronises `stream`. */
+int wrs_batch_autotune(const float *d_w, const uint64_t *d_off, uint32_t ntab,
+                       const uint32_t *d_order, wrs_row *d_rows, void *d_ws, uint64_t ws_bytes,
+                       wrs_table_summary *d_info, void *stream, int force,
+                       wrs_batch_tuning *best, wrs_batch_tuning *all, uint32_t *nall);
+
 /* a9: sample many tables in one launch.  Samples d_cnt_off[t] ..
  * d_cnt_off[t+1]-1 of d_out come from table t (rows at d_off[t]..) as
  * table-local item indices; sample q of table t uses Philox counter

@@ -23,7 +23,7 @@ from . import _build
 __all__ = [
     "WrsError", "lib", "config", "build_workspace_bytes", "build_layout", "build_rows",
     "step_total", "step_partition", "step_split", "step_pack", "step_info", "sample_rows",
-    "parse_info", "INFO_BYTES", "ROW_BYTES", "Builder", "rows_to_numpy",
+    "parse_info", "INFO_BYTES", "BatchTuning", "ROW_BYTES", "Builder", "rows_to_numpy",
 ]
 
 OK, EINVAL, EZEROSUM, ENONFINITE, ENOMEM, ETIMEOUT, ECUDA, EBUSY, ENOTFOUND = range(9)
@@ -52,6 +52,17 @@ class Layout(ctypes.Structure):
     _fields_ = [("lh", ctypes.c_uint64), ("ckl", ctypes.c_uint64), ("ckh", ctypes.c_uint64),
                 ("seg_pre", ctypes.c_uint64), ("splits", ctypes.c_uint64),
                 ("sections", ctypes.c_uint64), ("total_bytes", ctypes.c_uint64)]
+
+
+class BatchTuning(ctypes.Structure):
+    """Tiling of the batched build (wrs_batch_tuning)."""
+    _fields_ = [("threads", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
+                ("ctas_per_sm", ctypes.c_uint32), ("ms", ctypes.c_float),
+                ("reserved", ctypes.c_uint32 * 4)]
+
+    def as_dict(self) -> dict:
+        return {"threads": self.threads, "chunk": self.chunk, "ctas_per_sm": self.ctas_per_sm,
+                "ms": self.ms}
 
 
 class ServerStats(ctypes.Structure):
@@ -98,6 +109,12 @@ def lib():
                 "wrs_build_batched_workspace_bytes": (I, [U64, U32, ctypes.POINTER(U64)]),
                 "wrs_batch_order": (I, [P, U32, P]),
                 "wrs_build_batched_rows": (I, [P, P, U32, P, P, P, U64, P, P]),
+                "wrs_build_batched_rows_tuned": (I, [P, P, U32, P, P, P, U64, P,
+                                                     ctypes.POINTER(BatchTuning), P]),
+                "wrs_batch_tuning_default": (I, [ctypes.POINTER(BatchTuning)]),
+                "wrs_batch_autotune": (I, [P, P, U32, P, P, P, U64, P, P, I,
+                                           ctypes.POINTER(BatchTuning),
+                                           ctypes.POINTER(BatchTuning), ctypes.POINTER(U32)]),
                 "wrs_sample_batched_rows": (I, [P, P, U32, P, U64, P, P]),
                 "wrs_server_create": (I, [U64, U32, ctypes.POINTER(P)]),
                 "wrs_server_submit_build": (I, [P, P, U64, I, ctypes.POINTER(U64)]),
@@ -256,12 +273,29 @@ class BatchBuilder:
         self.info = torch.zeros(max(ntab, 1) * SUMMARY_DTYPE.itemsize, dtype=torch.uint8,
                                 device=device)
         self.ntab = ntab
+        self.tuning = None   # None: the default tiling
 
     def build(self, w, off, rows, order=None, stream=None):
-        _check(lib().wrs_build_batched_rows(_ptr(w), _ptr(off), self.ntab, _ptr(order),
-                                            _ptr(rows), _ptr(self.ws),
-                                            self.ws.numel(), _ptr(self.info), _stream(stream)),
-               "wrs_build_batched_rows")
+        """Enqueue the batched build with the current tiling (self.tuning)."""
+        t = ctypes.byref(self.tuning) if self.tuning is not None else None
+        _check(lib().wrs_build_batched_rows_tuned(_ptr(w), _ptr(off), self.ntab, _ptr(order),
+                                                  _ptr(rows), _ptr(self.ws), self.ws.numel(),
+                                                  _ptr(self.info), t, _stream(stream)),
+               "wrs_build_batched_rows_tuned")
+
+    def autotune(self, w, off, rows, order=None, stream=None, force=False):
+        """Time every candidate tiling on this batch (wrs_batch_autotune), keep
+        the fastest for later builds; returns (best, all candidates) as dicts.
+        The rows hold a valid build afterwards."""
+        best = BatchTuning()
+        cand = (BatchTuning * 16)()
+        nall = ctypes.c_uint32(16)
+        _check(lib().wrs_batch_autotune(_ptr(w), _ptr(off), self.ntab, _ptr(order), _ptr(rows),
+                                        _ptr(self.ws), self.ws.numel(), _ptr(self.info),
+                                        _stream(stream), int(force), ctypes.byref(best), cand,
+                                        ctypes.byref(nall)), "wrs_batch_autotune")
+        self.tuning = best
+        return best.as_dict(), [cand[k].as_dict() for k in range(min(nall.value, 16))]
 
     def summaries(self) -> np.ndarray:
         raw = self.info.cpu().numpy().tobytes()

@@ -4,6 +4,8 @@
 
 #include <algorithm>
 #include <numeric>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "wrs_internal.cuh"
@@ -21,9 +23,7 @@ cudaError_t launch_sample_naive(const wrs_row *, uint64_t, uint64_t, uint64_t, u
                                 uint32_t, uint32_t, uint32_t *, cudaStream_t);
 cudaError_t launch_sample_sectioned(const wrs_row *, uint64_t, uint64_t, uint64_t, uint32_t,
                                     uint64_t, uint64_t *, uint64_t *, uint32_t *, cudaStream_t);
-cudaError_t launch_build_batched(const float *, const uint64_t *, uint32_t, const uint32_t *,
-                                 uint32_t *, Entry *, wrs_row *, wrs_row *const *,
-                                 wrs_table_summary *, cudaStream_t);
+
 cudaError_t launch_sample_batched(const wrs_row *, const uint64_t *, uint32_t, const uint64_t *,
                                   uint64_t, uint32_t *, cudaStream_t);
 cudaError_t launch_random_gather(const void *, uint64_t, uint64_t, uint64_t, int, uint32_t *,
@@ -236,14 +236,24 @@ int wrs_batch_order(const uint64_t *h_off, uint32_t ntab, uint32_t *h_order) {
     return WRS_OK;
 }
 
-int wrs_build_batched_rows(const float *d_w, const uint64_t *d_off, uint32_t ntab,
-                           const uint32_t *d_order, wrs_row *d_rows, void *d_ws, uint64_t ws_bytes,
-                           wrs_table_summary *d_info, void *stream) {
+int wrs_batch_tuning_default(wrs_batch_tuning *t) {
+    if (!t) return WRS_EINVAL;
+    memset(t, 0, sizeof *t);
+    t->threads = 256;
+    t->chunk = 1024;
+    return WRS_OK;
+}
+
+int wrs_build_batched_rows_tuned(const float *d_w, const uint64_t *d_off, uint32_t ntab,
+                                 const uint32_t *d_order, wrs_row *d_rows, void *d_ws,
+                                 uint64_t ws_bytes, wrs_table_summary *d_info,
+                                 const wrs_batch_tuning *tuning, void *stream) {
     if (ntab == 0) return WRS_OK;
     if (!d_w || ((uintptr_t)d_w & 3u) || !d_off || ((uintptr_t)d_off & 7u) || !d_rows ||
         ((uintptr_t)d_rows & 7u) || !d_ws || ((uintptr_t)d_ws & 255u) || !d_info)
         return WRS_EINVAL;
     if (ws_bytes < 256) return WRS_EINVAL;
+    if (tuning && !batch_tuning_valid(*tuning)) return WRS_EINVAL;
     // the workspace must hold one l/h entry per item; the total is on the
     // device, so the kernel trusts ws_bytes >= 256 + 8 * total (checked by
     // the caller through wrs_build_batched_workspace_bytes)
@@ -251,8 +261,100 @@ int wrs_build_batched_rows(const float *d_w, const uint64_t *d_off, uint32_t nta
     return cuda_status(launch_build_batched(d_w, d_off, ntab, d_order,
                                             reinterpret_cast<uint32_t *>(ws),
                                             reinterpret_cast<Entry *>(ws + 256), d_rows, nullptr,
-                                            d_info,
-                                            (cudaStream_t)stream));
+                                            d_info, tuning, (cudaStream_t)stream));
+}
+
+int wrs_build_batched_rows(const float *d_w, const uint64_t *d_off, uint32_t ntab,
+                           const uint32_t *d_order, wrs_row *d_rows, void *d_ws, uint64_t ws_bytes,
+                           wrs_table_summary *d_info, void *stream) {
+    return wrs_build_batched_rows_tuned(d_w, d_off, ntab, d_order, d_rows, d_ws, ws_bytes, d_info,
+                                        nullptr, stream);
+}
+
+}  // extern "C"
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::pair<uint32_t, uint64_t>, wrs_batch_tuning> g_tune_cache;
+}  // namespace
+
+extern "C" {
+
+int wrs_batch_autotune(const float *d_w, const uint64_t *d_off, uint32_t ntab,
+                       const uint32_t *d_order, wrs_row *d_rows, void *d_ws, uint64_t ws_bytes,
+                       wrs_table_summary *d_info, void *stream, int force,
+                       wrs_batch_tuning *best, wrs_batch_tuning *all, uint32_t *nall) {
+    if (!best || ntab == 0) return WRS_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint64_t total = 0;
+    cudaError_t e = cudaMemcpyAsync(&total, d_off + ntab, sizeof total, cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) return cuda_status(e);
+    const auto key = std::make_pair(ntab, total);
+    if (!force) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *best = it->second;
+            if (nall) *nall = 0;
+            return WRS_OK;
+        }
+    }
+    static const uint32_t kThreads[] = {256, 512};
+    static const uint32_t kChunks[] = {512, 1024, 2048, 4096};
+    std::vector<wrs_batch_tuning> cand;
+    for (uint32_t t : kThreads)
+        for (uint32_t c : kChunks) {
+            wrs_batch_tuning x;
+            wrs_batch_tuning_default(&x);
+            x.threads = t;
+            x.chunk = c;
+            cand.push_back(x);
+        }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    e = cudaEventCreate(&e0);
+    if (!e) e = cudaEventCreate(&e1);
+    // warm-up (first launches of each tiling configure its kernel)
+    int rc = WRS_OK;
+    for (auto &x : cand) {
+        if (rc || e) break;
+        rc = wrs_build_batched_rows_tuned(d_w, d_off, ntab, d_order, d_rows, d_ws, ws_bytes, d_info,
+                                          &x, stream);
+    }
+    for (auto &x : cand) {
+        float bestms = 0.f;
+        for (int rep = 0; rep < 2 && !rc && !e; ++rep) {
+            e = cudaEventRecord(e0, st);
+            if (!e)
+                rc = wrs_build_batched_rows_tuned(d_w, d_off, ntab, d_order, d_rows, d_ws, ws_bytes,
+                                                  d_info, &x, stream);
+            if (!e && !rc) e = cudaEventRecord(e1, st);
+            if (!e && !rc) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (!e && !rc) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 0 || ms < bestms) bestms = ms;
+        }
+        x.ms = bestms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (e) return cuda_status(e);
+    size_t bi = 0;
+    for (size_t k = 1; k < cand.size(); ++k)
+        if (cand[k].ms < cand[bi].ms) bi = k;
+    // leave the buffers holding the chosen tiling's build (the same table)
+    *best = cand[bi];
+    if (all && nall) {
+        const uint32_t m = (uint32_t)std::min<size_t>(*nall, cand.size());
+        for (uint32_t k = 0; k < m; ++k) all[k] = cand[k];
+    }
+    if (nall) *nall = (uint32_t)cand.size();
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = *best;
+    }
+    return WRS_OK;
 }
 
 int wrs_sample_batched_rows(const wrs_row *d_rows, const uint64_t *d_off, uint32_t ntab,

@@ -19,32 +19,36 @@
 
 namespace wrs {
 
-constexpr int kBT = 256;         // threads of a batched CTA
+// Tiling of a batched CTA (picked per batch by wrs_batch_autotune):
+//   BT  threads of a CTA (256 or 512),
+//   CH  buckets packed per chunk of the sweep (512, 1024, 2048 or 4096).
+// The table does not depend on either: chunk ends are the splits of the
+// sweep's one comparison rule.
 constexpr int kBTile = 4096;     // partition tile
-constexpr int kBItems = kBTile / kBT;
-constexpr int kBChunk = 1024;    // buckets packed per chunk
-constexpr int kBSlots = 2 * kBChunk + 2;            // lights + heavies + next heavy
-constexpr int kBPSlots = kBSlots + kBSlots / 8 + 2; // padded prefix slots
-// Largest table of a batch: a thread's exact-sum bin stays below 2^64.
+// Largest table of a batch: with at least 256 threads a thread's exact-sum
+// bin (at most 2^16 values below 2^47) stays below 2^64.
 constexpr uint64_t kBatchMaxItems = 1ull << 24;
 
+template <int BT, int CH>
 struct BatchShared {
+    static constexpr int kSlots = 2 * CH + 2;             // lights + heavies + next heavy
+    static constexpr int kPSlots = kSlots + kSlots / 8 + 2; // padded prefix slots
     union {
-        uint64_t bins[kBands][kBT];
+        uint64_t bins[kBands][BT];
         struct {
             float wv[kBTile + kBTile / 32];
             Entry e[kBTile + kBTile / 16];
         } part;
         struct {
-            u128 P[kBPSlots];
-            uint32_t item[kBSlots];
-            float w[kBSlots + kBSlots / 32 + 1];
+            u128 P[kPSlots];
+            uint32_t item[kSlots];
+            float w[kSlots + kSlots / 32 + 1];
         } pack;
     } u;
     u128 band[kBands];
-    u128 wred[kBT / 32];
-    uint64_t qred[kBT / 32];
-    uint32_t cred[kBT / 32];
+    u128 wred[BT / 32];
+    uint64_t qred[BT / 32];
+    uint32_t cred[BT / 32];
     // per-table parameters
     double W, avg;
     uint64_t Q, Qn, nl;
@@ -60,13 +64,16 @@ struct BatchShared {
 
 __device__ __forceinline__ int pp8b(int e) { return e + (e >> 3); }
 
-__global__ void __launch_bounds__(kBT, 2)
+template <int BT, int CH>
+__global__ void __launch_bounds__(BT, 512 / BT)
 k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
                 const uint32_t *__restrict__ order, uint32_t ntab, uint32_t *__restrict__ counter,
                 Entry *__restrict__ lh, uint2 *__restrict__ rows, uint2 *const *__restrict__ row_ptrs,
                 wrs_table_summary *__restrict__ info) {
+    static_assert(BT == 256 || BT == 512, "exact-sum bins need >= 256 threads");
+    constexpr int kItems = kBTile / BT;   // items of a thread in a partition tile
     extern __shared__ __align__(16) unsigned char bsm_raw[];
-    BatchShared &sm = *reinterpret_cast<BatchShared *>(bsm_raw);
+    BatchShared<BT, CH> &sm = *reinterpret_cast<BatchShared<BT, CH> *>(bsm_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (;;) {
         if (tid == 0) {
@@ -91,7 +98,7 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
         // ---- a1: exact total of this table
         for (int b = 0; b < kBands; ++b) sm.u.bins[b][tid] = 0;
         uint32_t bad = 0;
-        for (uint64_t a = tid; a < n; a += kBT) {
+        for (uint64_t a = tid; a < n; a += BT) {
             uint32_t band;
             uint64_t val;
             band_of(__ldg(wt + a), band, val, bad);
@@ -100,9 +107,9 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
         bad = __reduce_or_sync(0xffffffffu, bad);
         if (lane == 0) sm.cred[warp] = bad;
         __syncthreads();
-        for (int b = warp; b < kBands; b += kBT / 32) {
+        for (int b = warp; b < kBands; b += BT / 32) {
             u128 s = 0;
-            for (int k = 0; k < kBT / 32; ++k) s += sm.u.bins[b][lane + 32 * k];
+            for (int k = 0; k < BT / 32; ++k) s += sm.u.bins[b][lane + 32 * k];
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) {
                 uint64_t lo = __shfl_xor_sync(0xffffffffu, (uint64_t)s, d);
@@ -114,7 +121,7 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
         __syncthreads();
         if (tid == 0) {
             uint32_t st = 0;
-            for (int k = 0; k < kBT / 32; ++k) st |= sm.cred[k];
+            for (int k = 0; k < BT / 32; ++k) st |= sm.cred[k];
             double W = 0.0;
             int top = -1;
             if (!st && !exact_total(sm.band, W, top)) st |= ERR_ZEROSUM;
@@ -148,7 +155,7 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
         {
             uint64_t qs = 0;
             uint32_t c = 0;
-            for (uint64_t a = tid; a < n; a += kBT) {
+            for (uint64_t a = tid; a < n; a += BT) {
                 float x = __ldg(wt + a);
                 qs += fixed_q(x, qsc);
                 c += x <= lmax;
@@ -165,7 +172,7 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
             __syncthreads();
             if (tid == 0) {
                 uint64_t Q = 0, nl = 0;
-                for (int k = 0; k < kBT / 32; ++k) {
+                for (int k = 0; k < BT / 32; ++k) {
                     Q += sm.qred[k];
                     nl += sm.cred[k];
                 }
@@ -182,12 +189,12 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
         // ---- a2: stable partition of the table into its lh region
         {
             uint64_t run_l = 0;
-            const int e0 = warp * 512 + lane * kBItems;
+            const int e0 = warp * (32 * kItems) + lane * kItems;
             for (uint64_t tb = 0; tb < n; tb += kBTile) {
                 const uint64_t lim = n - tb;
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    int e = warp * 512 + r * 128 + lane * 4;
+                for (int r = 0; r < kItems / 4; ++r) {
+                    int e = warp * (32 * kItems) + r * 128 + lane * 4;
 #pragma unroll
                     for (int c = 0; c < 4; ++c)
                         sm.u.part.wv[pad32(e + c)] =
@@ -196,7 +203,7 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
                 __syncwarp();
                 uint32_t lmask = 0, vmask = 0;
 #pragma unroll
-                for (int k = 0; k < kBItems; ++k) {
+                for (int k = 0; k < kItems; ++k) {
                     float x = sm.u.part.wv[pad32(e0 + k)];
                     bool valid = (uint64_t)(e0 + k) < lim;
                     vmask |= (uint32_t)valid << k;
@@ -212,7 +219,7 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
                 if (lane == 31) sm.cred[warp] = icnt;
                 __syncthreads();
                 uint32_t wl = 0, tl = 0;
-                for (int k = 0; k < kBT / 32; ++k) {
+                for (int k = 0; k < BT / 32; ++k) {
                     wl += (k < warp) ? sm.cred[k] : 0u;
                     tl += sm.cred[k];
                 }
@@ -221,7 +228,7 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
                 const uint32_t tnh = tv - tl;
                 uint32_t lrank = wl + icnt - cnt, hrank = (uint32_t)e0 - lrank;
 #pragma unroll
-                for (int k = 0; k < kBItems; ++k) {
+                for (int k = 0; k < kItems; ++k) {
                     if (!((vmask >> k) & 1u)) break;
                     Entry en{(uint32_t)(tb + e0 + k), sm.u.part.wv[pad32(e0 + k)]};
                     if ((lmask >> k) & 1u) sm.u.part.e[pad16(lrank++)] = en;
@@ -230,8 +237,8 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
                 __syncthreads();
                 uint2 *lh2 = reinterpret_cast<uint2 *>(lh + base);
                 const uint2 *e2 = reinterpret_cast<const uint2 *>(sm.u.part.e);
-                for (uint32_t a = tid; a < tl; a += kBT) lh2[run_l + a] = e2[pad16(a)];
-                for (uint32_t b = tid; b < tnh; b += kBT)
+                for (uint32_t a = tid; a < tl; a += BT) lh2[run_l + a] = e2[pad16(a)];
+                for (uint32_t b = tid; b < tnh; b += BT)
                     lh2[n - 1 - (run_h + b)] = e2[pad16(kBTile - 1 - b)];
                 run_l += tl;
                 __syncthreads();
@@ -250,11 +257,11 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
             const uint64_t i = sm.i, j = sm.j;
             if (i + j >= n) break;
             const u128 D0 = sm.D, E0 = sm.E;
-            const uint32_t L = (uint32_t)min((uint64_t)kBChunk, nl - i);
-            const uint32_t H = (uint32_t)min((uint64_t)kBChunk, nh - j);
+            const uint32_t L = (uint32_t)min((uint64_t)CH, nl - i);
+            const uint32_t H = (uint32_t)min((uint64_t)CH, nh - j);
             const uint32_t extra = (j + H < nh) ? 1u : 0u;
-            const uint32_t K = (uint32_t)min((uint64_t)kBChunk, n - i - j);
-            for (uint32_t e = tid; e < L + H + extra; e += kBT) {
+            const uint32_t K = (uint32_t)min((uint64_t)CH, n - i - j);
+            for (uint32_t e = tid; e < L + H + extra; e += BT) {
                 Entry en = (e < L) ? lht[i + e] : lht[n - 1 - (j + (e - L))];
                 sm.u.pack.item[e] = en.item;
                 sm.u.pack.w[pad32(e)] = en.w;
@@ -262,7 +269,7 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
             __syncthreads();
             // blocked values: d' (lights) then e' (heavies); exclusive scan
             const uint32_t LH = L + H;
-            const uint32_t per = (LH + kBT - 1) / kBT;
+            const uint32_t per = (LH + BT - 1) / BT;
             const uint32_t b0 = tid * per;
             u128 run = 0;
             for (uint32_t k = 0; k < per; ++k) {
@@ -306,7 +313,7 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
                 }
                 return lo;
             };
-            const uint32_t per_out = (K + kBT - 1) / kBT;
+            const uint32_t per_out = (K + BT - 1) / BT;
             const uint32_t d0 = tid * per_out;
             if (d0 < K) {
                 uint32_t x = split_at(d0), y = d0 - x;
@@ -445,30 +452,58 @@ cudaError_t launch_sample_requests(const SampleReq *d_req, const uint32_t *d_chu
 
 extern int num_sms();
 
+template <int BT, int CH>
+static cudaError_t launch_bb(const float *d_w, const uint64_t *d_off, uint32_t ntab,
+                             const uint32_t *d_order, uint32_t *d_counter, Entry *d_lh,
+                             wrs_row *d_rows, wrs_row *const *d_row_ptrs, wrs_table_summary *d_info,
+                             uint32_t ctas_per_sm, cudaStream_t st) {
+    const int smem = (int)sizeof(BatchShared<BT, CH>);
+    static bool configured = false;
+    static int per_sm_max = 0;
+    cudaError_t e;
+    if (!configured) {
+        e = cudaFuncSetAttribute(k_batched_build<BT, CH>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_max, k_batched_build<BT, CH>, BT,
+                                                          smem);
+        if (e) return e;
+        if (per_sm_max < 1) per_sm_max = 1;
+        configured = true;
+    }
+    e = cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), st);
+    if (e) return e;
+    int per_sm = per_sm_max;
+    if (ctas_per_sm && (int)ctas_per_sm < per_sm) per_sm = (int)ctas_per_sm;
+    unsigned blocks = (unsigned)num_sms() * (unsigned)per_sm;
+    if (blocks > ntab) blocks = ntab ? ntab : 1;
+    k_batched_build<BT, CH><<<blocks, BT, smem, st>>>(
+        d_w, d_off, d_order, ntab, d_counter, d_lh, reinterpret_cast<uint2 *>(d_rows),
+        reinterpret_cast<uint2 *const *>(d_row_ptrs), d_info);
+    return cudaGetLastError();
+}
+
+bool batch_tuning_valid(const wrs_batch_tuning &t) {
+    return (t.threads == 256 || t.threads == 512) &&
+           (t.chunk == 512 || t.chunk == 1024 || t.chunk == 2048 || t.chunk == 4096) &&
+           t.ctas_per_sm <= 64;
+}
+
 cudaError_t launch_build_batched(const float *d_w, const uint64_t *d_off, uint32_t ntab,
                                  const uint32_t *d_order, uint32_t *d_counter, Entry *d_lh,
                                  wrs_row *d_rows, wrs_row *const *d_row_ptrs,
-                                 wrs_table_summary *d_info, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), st);
-    if (e) return e;
-    const int smem = (int)sizeof(BatchShared);
-    static bool configured = false;
-    if (!configured) {
-        e = cudaFuncSetAttribute(k_batched_build, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem);
-        if (e) return e;
-        configured = true;
-    }
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batched_build, kBT, smem);
-    if (e) return e;
-    unsigned blocks = (unsigned)num_sms() * (unsigned)(per_sm > 0 ? per_sm : 1);
-    if (blocks > ntab) blocks = ntab ? ntab : 1;
-    k_batched_build<<<blocks, kBT, smem, st>>>(d_w, d_off, d_order, ntab, d_counter, d_lh,
-                                               reinterpret_cast<uint2 *>(d_rows),
-                                               reinterpret_cast<uint2 *const *>(d_row_ptrs),
-                                               d_info);
-    return cudaGetLastError();
+                                 wrs_table_summary *d_info, const wrs_batch_tuning *tune,
+                                 cudaStream_t st) {
+    const uint32_t T = tune ? tune->threads : 256, C = tune ? tune->chunk : 1024;
+    const uint32_t cps = tune ? tune->ctas_per_sm : 0;
+#define WRS_BB(bt, ch)                                                                          \
+    if (T == bt && C == ch)                                                                     \
+        return launch_bb<bt, ch>(d_w, d_off, ntab, d_order, d_counter, d_lh, d_rows, d_row_ptrs, \
+                                 d_info, cps, st);
+    WRS_BB(256, 512) WRS_BB(256, 1024) WRS_BB(256, 2048) WRS_BB(256, 4096)
+    WRS_BB(512, 512) WRS_BB(512, 1024) WRS_BB(512, 2048) WRS_BB(512, 4096)
+#undef WRS_BB
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_sample_batched(const wrs_row *d_rows, const uint64_t *d_off, uint32_t ntab,

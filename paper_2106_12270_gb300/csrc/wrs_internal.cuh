@@ -130,6 +130,14 @@ static inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a
 
 Layout make_layout(uint64_t n, uint32_t section_size);
 
+// Batched build (wrs_batched.cu); tune == nullptr is the default tiling.
+bool batch_tuning_valid(const wrs_batch_tuning &t);
+cudaError_t launch_build_batched(const float *d_w, const uint64_t *d_off, uint32_t ntab,
+                                 const uint32_t *d_order, uint32_t *d_counter, Entry *d_lh,
+                                 wrs_row *d_rows, wrs_row *const *d_row_ptrs,
+                                 wrs_table_summary *d_info, const wrs_batch_tuning *tune,
+                                 cudaStream_t st);
+
 // ---------------------------------------------------------------------------
 // Small device helpers
 // ---------------------------------------------------------------------------

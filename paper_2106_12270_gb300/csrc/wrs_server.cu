@@ -34,9 +34,7 @@
 
 namespace wrs {
 
-cudaError_t launch_build_batched(const float *, const uint64_t *, uint32_t, const uint32_t *,
-                                 uint32_t *, Entry *, wrs_row *, wrs_row *const *,
-                                 wrs_table_summary *, cudaStream_t);
+
 cudaError_t launch_sample_requests(const SampleReq *, const uint32_t *, uint32_t, uint32_t,
                                    cudaStream_t);
 cudaError_t launch_total(const float *, uint64_t, unsigned char *, const Layout &, cudaStream_t);
@@ -438,7 +436,7 @@ bool wrs_server::launch_step() {
         if (!e) e = cudaMemcpyAsync(d_rowp, h_rowp, 8 * nb, cudaMemcpyHostToDevice, s_build);
         if (!e)
             e = launch_build_batched(d_w, d_off, nb, nullptr, d_counter, d_lh, nullptr, d_rowp,
-                                     d_summ, s_build);
+                                     d_summ, nullptr, s_build);
         if (!e)
             e = cudaMemcpyAsync(st->summ, d_summ, sizeof(wrs_table_summary) * nb,
                                 cudaMemcpyDeviceToHost, s_build);

@@ -112,3 +112,78 @@ def test_batched_bad_tables_do_not_spoil_others():
     prob, alias = table_rows(rows, off, 0)
     W = oracle.exact_sum(w[:100])
     assert oracle.mass_error(prob.astype(np.float64), alias, w[:100], W) <= 1e-5
+
+
+TILINGS = [(t, c) for t in (256, 512) for c in (512, 1024, 2048, 4096)]
+
+
+@pytest.mark.parametrize("threads,chunk", TILINGS)
+def test_every_tiling_builds_the_same_tables(batch, threads, chunk):
+    """The tiling only changes the time: rows and summaries are bit-identical
+    to the default tiling's."""
+    w, off, rows, summ, off_t = batch
+    wt = torch.from_numpy(np.ascontiguousarray(w, np.float32)).cuda()
+    rows2 = torch.zeros_like(rows)
+    bb = wrs.BatchBuilder(int(off[-1]), off.size - 1)
+    bb.tuning = wrs.BatchTuning(threads, chunk, 0, 0.0)
+    bb.build(wt, off_t, rows2, None)
+    torch.cuda.synchronize()
+    assert torch.equal(rows, rows2)
+    assert np.array_equal(summ.view(np.uint8), bb.summaries().view(np.uint8))
+
+
+def test_invalid_tiling_rejected(batch):
+    w, off, rows, summ, off_t = batch
+    wt = torch.from_numpy(np.ascontiguousarray(w, np.float32)).cuda()
+    bb = wrs.BatchBuilder(int(off[-1]), off.size - 1)
+    for bad in ((128, 1024), (256, 8192), (300, 1024)):
+        bb.tuning = wrs.BatchTuning(bad[0], bad[1], 0, 0.0)
+        with pytest.raises(wrs.WrsError):
+            bb.build(wt, off_t, torch.zeros_like(rows), None)
+
+
+def test_autotune_picks_a_candidate_and_caches_it(batch):
+    w, off, rows, summ, off_t = batch
+    wt = torch.from_numpy(np.ascontiguousarray(w, np.float32)).cuda()
+    rows2 = torch.zeros_like(rows)
+    bb = wrs.BatchBuilder(int(off[-1]), off.size - 1)
+    best, cand = bb.autotune(wt, off_t, rows2, None, force=True)
+    assert len(cand) == len(TILINGS)
+    assert {(c["threads"], c["chunk"]) for c in cand} == set(TILINGS)
+    assert all(c["ms"] > 0 for c in cand)
+    assert best["ms"] == min(c["ms"] for c in cand)
+    assert torch.equal(rows, rows2)            # the buffers hold a valid build
+    again, cand2 = bb.autotune(wt, off_t, rows2, None)   # cached: no timing
+    assert cand2 == [] and (again["threads"], again["chunk"]) == (best["threads"], best["chunk"])
+
+
+def test_batched_build_and_sample_replay_as_cuda_graph(batch):
+    """One captured graph (build + sample) replays to the eager results."""
+    w, off, rows, summ, off_t = batch
+    ntab = off.size - 1
+    wt = torch.from_numpy(np.ascontiguousarray(w, np.float32)).cuda()
+    cnt_off = torch.arange(0, 501 * (ntab + 1), 501, dtype=torch.int64, device="cuda")
+    bb = wrs.BatchBuilder(int(off[-1]), ntab)
+    rows_g = torch.zeros_like(rows)
+    out_g = torch.empty(int(cnt_off[-1]), dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):   # warm-up outside the capture (kernel attributes)
+        bb.build(wt, off_t, rows_g, None, stream=s)
+        wrs.sample_batched_rows(rows_g, off_t, ntab, cnt_off, 5, out_g, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        st = torch.cuda.current_stream()
+        bb.build(wt, off_t, rows_g, None, stream=st)
+        wrs.sample_batched_rows(rows_g, off_t, ntab, cnt_off, 5, out_g, stream=st)
+    rows_g.zero_()
+    out_g.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(rows_g, rows)
+    out_e = torch.empty_like(out_g)
+    wrs.sample_batched_rows(rows, off_t, ntab, cnt_off, 5, out_e)
+    torch.cuda.synchronize()
+    assert torch.equal(out_g, out_e)
