@@ -3,9 +3,10 @@
 // The PSA method (Sec. 2.2, Sec. 4 of "Weighted Random Sampling on GPUs")
 // in four kernels, with integer fixed-point prefix sums:
 //
-//   k_sum / k_total      a1: W = sum w_i, exact (per-exponent-band integer
-//                        sums), rounded once to FP64; avg = W/N; the scale S
-//                        of the fixed point q_i = round(w_i 2^S).
+//   k_sum                a1: W = sum w_i, exact (per-exponent-band integer
+//                        sums, assembled by the last CTA), rounded once to
+//                        FP64; avg = W/N; the scale S of the fixed point
+//                        q_i = round(w_i 2^S).
 //   k_count / k_scatter  a2+a3: light iff w_i <= W/N; stable partition into
 //   / k_segscan          one array (lights from the front, heavies from the
 //                        back, Sec. 4.2 "weight in l and h").  Persistent
@@ -40,6 +41,8 @@
 // the stored probabilities.
 #include <stdio.h>
 
+#include <algorithm>
+
 #include "wrs_device.cuh"
 
 
@@ -56,7 +59,7 @@ Layout make_layout(uint64_t n, uint32_t S) {
     L.ntiles = (n + kTile - 1) / kTile;
     L.sections = (n + S - 1) / S;
     L.params = take(sizeof(BuildParams));
-    L.sum_bins = take((uint64_t)kSumMaxBlocks * kBands * sizeof(u128));
+    L.sum_bins = take((uint64_t)kSumMaxBlocks * kSumBands * sizeof(u128));
     L.seg_cnt = take((uint64_t)kMaxSegs * 4);
     L.seg_q = take((uint64_t)kMaxSegs * 8);
     L.seg_loff = take((uint64_t)(kMaxSegs + 1) * 8);
@@ -74,22 +77,32 @@ Layout make_layout(uint64_t n, uint32_t S) {
 // a1: exact total weight
 // ===========================================================================
 
-// Each FP32 weight m * 2^(e'-150) (e' = max(biased exponent, 1)) goes into
-// band e'/24 as m << (e' mod 24) < 2^47.  A thread sees at most 2^15 items,
-// so its per-band sum stays below 2^62; blocks reduce to 128-bit sums.
+// Each FP32 weight m * 2^(e'-150) (e' = max(biased exponent, 1), m the
+// 24-bit significand with its leading bit) goes into band e'/16 as
+// m << (e' mod 16) < 2^39.  A thread sees at most 2^25 items, so its
+// per-band sum stays below 2^64; blocks reduce to 128-bit sums.  NaN/Inf and
+// negative weights are found from two running maxima of the bit patterns.
+// The last block to finish assembles W exactly (units of 2^-150), rounds it
+// to FP64 (ties to even) and derives avg, the light threshold and the
+// fixed-point scale.
 __global__ void __launch_bounds__(kSumThreads)
 k_sum(const float *__restrict__ w, uint64_t n, u128 *__restrict__ bins_out,
-      BuildParams *__restrict__ P, int aligned) {
-    __shared__ uint64_t bins[kBands][kSumThreads];
+      BuildParams *__restrict__ P, int aligned, uint32_t sections) {
+    __shared__ uint64_t bins[kSumBands][kSumThreads];
+    __shared__ u128 band[kSumBands];
+    __shared__ uint32_t s_last;
     const int tid = threadIdx.x;
 #pragma unroll
-    for (int b = 0; b < kBands; ++b) bins[b][tid] = 0;
-    uint32_t bad = 0;
+    for (int b = 0; b < kSumBands; ++b) bins[b][tid] = 0;
+    uint32_t umax = 0, amax = 0;
     auto add = [&](float x) {
-        uint32_t band;
-        uint64_t val;
-        band_of(x, band, val, bad);
-        bins[band][tid] += val;
+        const uint32_t u = __float_as_uint(x);
+        const uint32_t a = u & 0x7fffffffu;
+        umax = max(umax, u);
+        amax = max(amax, a);
+        const uint32_t ee = max(a >> 23, 1u);
+        const uint32_t m = a - ((ee - 1u) << 23);
+        bins[ee >> 4][tid] += (uint64_t)m << (ee & 15u);
     };
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + tid;
@@ -106,7 +119,7 @@ k_sum(const float *__restrict__ w, uint64_t n, u128 *__restrict__ bins_out,
     for (uint64_t i = tail + g; i < n; i += T) add(__ldg(w + i));
     __syncthreads();
     const int warp = tid >> 5, lane = tid & 31;
-    for (int b = warp; b < kBands; b += kSumThreads / 32) {
+    for (int b = warp; b < kSumBands; b += kSumThreads / 32) {
         u128 s = 0;
 #pragma unroll
         for (int k = 0; k < kSumThreads / 32; ++k) s += bins[b][lane + 32 * k];
@@ -116,38 +129,44 @@ k_sum(const float *__restrict__ w, uint64_t n, u128 *__restrict__ bins_out,
             uint64_t hi = __shfl_down_sync(0xffffffffu, (uint64_t)(s >> 64), d);
             s += ((u128)hi << 64) | lo;
         }
-        if (lane == 0) bins_out[(uint64_t)blockIdx.x * kBands + b] = s;
+        if (lane == 0) bins_out[(uint64_t)blockIdx.x * kSumBands + b] = s;
     }
+    // non-finite: |bits| >= the Inf pattern; negative: a set sign bit on a
+    // nonzero pattern (-0 is allowed)
+    uint32_t bad = (amax >= 0x7f800000u ? ERR_NONFINITE : 0u) |
+                   (umax > 0x80000000u ? ERR_NEGATIVE : 0u);
     bad = __reduce_or_sync(0xffffffffu, bad);
     if (lane == 0 && bad) atomicOr(&P->status, bad);
-}
 
-// kBands warps: warp b reduces band b over the blocks; thread 0 then
-// assembles W exactly (units of 2^-150), rounds it to FP64 (ties to even)
-// and derives avg, the light threshold and the fixed-point scale.
-__global__ void __launch_bounds__(32 * kBands)
-k_total(const u128 *__restrict__ bins_in, int nblocks, uint64_t n, uint32_t sections,
-        BuildParams *__restrict__ P) {
-    __shared__ u128 band[kBands];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    {
+    // last block: reduce the bands over all blocks and assemble W
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&P->sum_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int b = warp; b < kSumBands; b += kSumThreads / 32) {
         u128 s = 0;
-        for (int b = lane; b < nblocks; b += 32) s += bins_in[(uint64_t)b * kBands + warp];
+        for (uint32_t k = lane; k < gridDim.x; k += 32) {
+            const ulonglong2 v =
+                __ldcg(reinterpret_cast<const ulonglong2 *>(bins_out + (uint64_t)k * kSumBands + b));
+            s += ((u128)v.y << 64) | v.x;
+        }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) {
             uint64_t lo = __shfl_down_sync(0xffffffffu, (uint64_t)s, d);
             uint64_t hi = __shfl_down_sync(0xffffffffu, (uint64_t)(s >> 64), d);
             s += ((u128)hi << 64) | lo;
         }
-        if (lane == 0) band[warp] = s;
+        if (lane == 0) band[b] = s;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
+    if (tid != 0) return;
     P->n = n;
     P->sections = sections;
     double W;
     int top;
-    if (!exact_total(band, W, top)) {
+    if (!exact_total<kSumBands, 16>(band, W, top)) {
         P->W = 0.0;
         P->avg = 0.0;
         atomicOr(&P->status, ERR_ZEROSUM);
@@ -199,7 +218,7 @@ k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__
     if (aligned) {
         const float4 *w4 = reinterpret_cast<const float4 *>(w);
         const uint64_t b4 = b / 4;
-#pragma unroll 4
+#pragma unroll 8
         for (uint64_t i = a / 4 + lane; i < b4; i += 32) {
             float4 v = __ldg(w4 + i);
             cnt += (v.x <= lmax) + (v.y <= lmax) + (v.z <= lmax) + (v.w <= lmax);
@@ -661,18 +680,31 @@ k_split(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
             if (pred_c(C, k, m)) b = m;
             else a = m + 1;
         }
+        // the checkpoint index for the fine search (< 2^26), parked in the
+        // record the fine search then writes in full
+        splits[t].pad[0] = (uint32_t)a;
     }
-    s_c[tid] = a;
-    __syncthreads();
-    // fine phase: each warp handles its 32 splits one after another
-    const int warp = tid >> 5, lane = tid & 31;
-    for (int q = 0; q < 32; ++q) {
-        int st = warp * 32 + q;
-        uint64_t tt = t0 + st;
-        if (tt >= sections) break;
-        split_fine(C, Pm, tt * S, s_c[st], splits + tt, lane);
-    }
+    (void)s_c;
     (void)s_go;
+}
+
+// Fine phase of the interior splits: one warp per split (many in flight, so
+// the dependent loads of the warp search overlap across the GPU).
+__global__ void __launch_bounds__(kSplitThreads)
+k_split_fine(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
+             const CkRec *__restrict__ ckl, const CkRec *__restrict__ ckh,
+             const SegVal *__restrict__ seg_pre, SplitRec *__restrict__ splits, uint64_t n,
+             uint64_t S, uint32_t sections) {
+    if (P->status) return;
+    const uint64_t t = 1 + (uint64_t)blockIdx.x * (kSplitThreads / 32) + (threadIdx.x >> 5);
+    if (t >= sections) return;
+    const BuildParams Pm = *P;
+    SplitCtx C;
+    C.ckl = ckl; C.ckh = ckh; C.seg_pre = seg_pre; C.lh = lh; C.n = n; C.nl = Pm.nl;
+    C.nh = Pm.nh; C.Q = Pm.Q;
+    const uint64_t c = splits[t].pad[0];
+    __syncwarp();
+    split_fine(C, Pm, t * S, c, splits + t, threadIdx.x & 31);
 }
 
 // Splits 0 and s (the whole table's ends).
@@ -943,13 +975,13 @@ cudaError_t launch_total(const float *d_w, uint64_t n, unsigned char *ws, const 
     BuildParams *P = reinterpret_cast<BuildParams *>(ws + L.params);
     cudaError_t err = cudaMemsetAsync(P, 0, sizeof(BuildParams), st);
     if (err) return err;
+    // one wave of CTAs (six fit on an SM), at least 4096 items each
+    const uint64_t cap = std::min<uint64_t>((uint64_t)num_sms() * 6, kSumMaxBlocks);
     uint64_t want = (n + 4095) / 4096;
-    int blocks = (int)(want < (uint64_t)kSumMaxBlocks ? (want ? want : 1) : kSumMaxBlocks);
+    int blocks = (int)(want < cap ? (want ? want : 1) : cap);
     int aligned = ((uintptr_t)d_w % 16) == 0;
     k_sum<<<blocks, kSumThreads, 0, st>>>(d_w, n, reinterpret_cast<u128 *>(ws + L.sum_bins), P,
-                                           aligned);
-    k_total<<<1, 32 * kBands, 0, st>>>(reinterpret_cast<const u128 *>(ws + L.sum_bins), blocks, n,
-                              (uint32_t)L.sections, P);
+                                           aligned, (uint32_t)L.sections);
     return cudaGetLastError();
 }
 
@@ -1003,6 +1035,8 @@ cudaError_t launch_split(uint64_t n, unsigned char *ws, const Layout &L, uint32_
             k_split<false><<<blocks, kSplitThreads, 0, st>>>(P, lh, ckl, ckh, pre, sp, n, S, s);
         else
             k_split<true><<<blocks, kSplitThreads, 0, st>>>(P, lh, ckl, ckh, pre, sp, n, S, s);
+        const unsigned fblocks = (unsigned)((s - 1 + kSplitThreads / 32 - 1) / (kSplitThreads / 32));
+        k_split_fine<<<fblocks, kSplitThreads, 0, st>>>(P, lh, ckl, ckh, pre, sp, n, S, s);
     }
     return cudaGetLastError();
 }

@@ -52,16 +52,18 @@ __device__ inline int big_any_below(const uint32_t *big, int pos) {
     return 0;
 }
 
-// W from the per-band sums (band b counts in units of 2^(24b-150)): the
+// W from the per-band sums (band b of kWidth binades counts in units of
+// 2^(kWidth b - 150); below 2^128 each, kNB * kWidth + 128 <= 384): the
 // exact total assembled in a 384-bit integer and rounded once to FP64, ties
 // to even.  Returns false when the total is zero; `top` is the index of the
 // total's highest set bit (units of 2^-150).
+template <int kNB = kBands, int kWidth = 24>
 __device__ inline bool exact_total(const u128 *band, double &W, int &top) {
     uint32_t big[12];
     for (int k = 0; k < 12; ++k) big[k] = 0;
-    for (int b = 0; b < kBands; ++b) {
+    for (int b = 0; b < kNB; ++b) {
         u128 v = band[b];
-        int shift = 24 * b;
+        int shift = kWidth * b;
         uint64_t carry = 0;
         for (int k = 0; k < 12; ++k) {
             int o = 32 * k - shift;  // bit of v that lands at bit 0 of limb k

@@ -55,7 +55,7 @@ struct __align__(16) BuildParams {
     float invQ;        // 1 / Qf: a heavy row keeps 1 - delta * invQ
     uint32_t sections; // s
     uint32_t nseg;     // partition segments
-    uint32_t pad0;
+    uint32_t sum_done; // blocks of the total-weight kernel that are done
 };
 
 // Workspace layout (all offsets 256-byte aligned).
@@ -116,6 +116,7 @@ struct __align__(16) SampleReq {
 // Sizes shared by host and device code.
 constexpr int kBands = 11;            // exponent bands of width 24
 constexpr int kSumThreads = 256;
+constexpr int kSumBands = 16;   // total weight: bands of 16 binades
 constexpr int kSumMaxBlocks = 1216;   // 8 x 152 SMs
 constexpr int kPartThreads = 256;
 constexpr int kPartItems = 16;
