@@ -326,7 +326,7 @@ struct WarpStage {
 // the running sum at the one slot per lane where a checkpoint can fall.  The
 // next chunk's weights are loaded while the current one is processed.
 template <bool kAligned>
-__global__ void __launch_bounds__(kPartThreads, 4)
+__global__ void __launch_bounds__(kPartThreads, 3)
 k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__ P,
           const uint64_t *__restrict__ seg_loff, Entry *__restrict__ lh, CkRec *__restrict__ ckl,
           CkRec *__restrict__ ckh, SegVal *__restrict__ seg_sum, uint64_t C, uint32_t NS) {
@@ -899,16 +899,17 @@ __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
                 const uint32_t pos = heavy ? L + y : x;
                 const uint32_t nxt = heavy ? y + 1 : y;
                 const bool has = nxt < hleft;
-                const uint32_t alias = sE[pk16(has ? L + nxt : pos)].x;
-                float prob;
-                if (heavy) {
-                    prob = b > a ? 1.0f
-                                 : fminf(fmaxf(1.0f - __ll2float_rn(a - b) * invQk, 0.0f), 1.0f);
-                } else {
-                    prob = fminf(__uint_as_float(sE[pk16(x)].y) * inv_avg, 1.0f);
+                const uint2 ep = sE[pk16(pos)];   // the closed item and its weight
+                uint32_t alias = ep.x;
+                float prob = 1.0f;
+                if (has) {
+                    alias = sE[pk16(L + nxt)].x;
+                    prob = heavy ? (b > a ? 1.0f
+                                          : fminf(fmaxf(1.0f - __ll2float_rn(a - b) * invQk, 0.0f),
+                                                  1.0f))
+                                 : fminf(__uint_as_float(ep.y) * inv_avg, 1.0f);
                 }
-                if (!has) prob = 1.0f;
-                rows[sE[pk16(pos)].x] = make_uint2(__float_as_uint(prob), alias);
+                rows[ep.x] = make_uint2(__float_as_uint(prob), alias);
                 const int64_t v = sK[pk16(heavy ? L + y + 2 : x + 1)];
                 if (heavy) { ++y; b = v; }
                 else { ++x; a = v; }
