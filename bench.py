@@ -36,7 +36,16 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 BUILD_BYTES_PER_ITEM = 32      # read w twice, write + read lh, write rows
 SAMPLE_BYTES_PER_DRAW = 36     # one 32-byte row sector + a 4-byte output
-KERNELS_PER_BUILD = 10         # sum, total, count, qsum, scatter, segscan, split ends, split, pack, info
+KERNELS_PER_BUILD = 10         # sum, count, qsum, scatter, segscan, split ends, split, split fine, pack, info
+# DRAM bytes the hardware moved per unit (dram__bytes_read.sum +
+# dram__bytes_write.sum) in ncu captures of these kernels: the build at
+# N = 2^25 items (sum 4.0, count 4.0, scatter 10.65, split 1.0, pack 15.7) and
+# the naive sampler drawing 2^26 samples from a 2^25-row table (87.3 B of row
+# sectors read + 4 B written per draw); both workloads exceed L2 and the
+# traffic grows with the units, so a launch's traffic is these times its
+# units.  To be re-measured whenever one of these kernels changes.
+BUILD_TRAFFIC_PER_ITEM = 35.4
+SAMPLE_TRAFFIC_PER_DRAW = 91.3
 KERNELS_PER_SAMPLE = 1
 # batched build/sample are timed separately (extra keys), not in gpu_launches
 
@@ -367,11 +376,16 @@ def run_gpu(args):
     build_gbs = BUILD_BYTES_PER_ITEM * n / (build_ms / 1e3) / 1e9
     sample_gbs = (SAMPLE_BYTES_PER_DRAW * count / (sample_ms / 1e3) / 1e9) if count else 0.0
     build_roof = {"bound": "hbm", "achieved": build_gbs, "peak": hbm, "unit": "GB/s",
-                  "frac": build_gbs / hbm, "traffic": None, "kernel": "build (9 kernels)",
+                  "frac": build_gbs / hbm, "traffic": BUILD_TRAFFIC_PER_ITEM * n,
+                  "traffic_unit": "bytes per build (ncu, scaled from N=2^25)",
+                  "kernel": "build (10 kernels)",
                   "peak_kind": peak_kind}
     probe_gbs = (SAMPLE_BYTES_PER_DRAW * count / (probe_ms / 1e3) / 1e9) if probe else float("nan")
     sample_roof = {"bound": "hbm", "achieved": sample_gbs, "peak": hbm, "unit": "GB/s",
-                   "frac": sample_gbs / hbm, "traffic": None, "kernel": "k_sample_naive",
+                   "frac": sample_gbs / hbm,
+                   "traffic": SAMPLE_TRAFFIC_PER_DRAW * count if count else None,
+                   "traffic_unit": "bytes per launch (ncu, scaled from 2^26 draws)",
+                   "kernel": "k_sample_naive",
                    "peak_kind": peak_kind,
                    "random_gather_probe": {"achieved": probe_gbs, "unit": "GB/s",
                                            "frac_of_probe": (sample_gbs / probe_gbs) if probe else None,
