@@ -145,10 +145,8 @@ class ClockSampler:
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_2106_12270_gb300 import replicas
+    return replicas.env()
 
 
 # ---------------------------------------------------------------------------
@@ -215,7 +213,7 @@ def run_gpu(args):
     import torch
 
     import paper_2106_12270_gb300 as wrs
-    from paper_2106_12270_gb300 import _build, inputs
+    from paper_2106_12270_gb300 import _build, inputs, replicas
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -228,8 +226,9 @@ def run_gpu(args):
 
     n, count = args.n, args.samples
     cfg = wrs.config(args.section)
-    seed = (args.seed if args.seed is not None else
-            {"zipf": 3, "uniform": 1, "exponential": 4, "gamma": 7}[args.dist]) + rank
+    seed = replicas.rank_seed(args.seed if args.seed is not None else
+                              {"zipf": 3, "uniform": 1, "exponential": 4, "gamma": 7}[args.dist],
+                              rank)
     w_host = inputs.by_name(args.dist, n, seed)
     w = torch.from_numpy(w_host).cuda()
     builder = wrs.Builder(n, cfg)
@@ -277,10 +276,8 @@ def run_gpu(args):
     total_ms = t_start.elapsed_time(t_end)
     build_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
     sample_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
-    if dist:
-        t = torch.tensor([total_ms, build_ms, sample_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, build_ms, sample_ms = t.tolist()
+    total_ms, build_ms, sample_ms = replicas.max_over_ranks([total_ms, build_ms, sample_ms],
+                                                            dist, "cuda")
     ms_per_step = total_ms / args.steps
 
     # end to end through the C ABI with host buffers: pinned weights in,
@@ -307,11 +304,8 @@ def run_gpu(args):
         b.record(stream)
         torch.cuda.synchronize()
         e2e_ms = a.elapsed_time(b) / args.steps
-        if dist:
-            t = torch.tensor([e2e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = t.item()
-        e2e = {"value": world * n / (e2e_ms / 1e3), "unit": "items/s",
+        e2e_ms = replicas.max_over_ranks([e2e_ms], dist, "cuda")[0]
+        e2e = {"value": replicas.job_rate(n, world, e2e_ms), "unit": "items/s",
                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n,
                "ms_per_step": e2e_ms}
 
@@ -401,7 +395,7 @@ def run_gpu(args):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": world * n / (build_ms / 1e3), "unit": "items/s",
+            "metric": METRIC, "value": replicas.job_rate(n, world, build_ms), "unit": "items/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u128 fixed point (build), u32 (sampling)",
