@@ -218,8 +218,20 @@ k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__
     if (aligned) {
         const float4 *w4 = reinterpret_cast<const float4 *>(w);
         const uint64_t b4 = b / 4;
-#pragma unroll 8
-        for (uint64_t i = a / 4 + lane; i < b4; i += 32) {
+        uint64_t i = a / 4 + lane;
+        // groups of eight 16-byte loads per lane, all in flight before use
+        for (; i + 7 * 32 < b4; i += 8 * 32) {
+            float4 v[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) v[r] = __ldg(w4 + i + 32 * r);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                cnt += (v[r].x <= lmax) + (v[r].y <= lmax) + (v[r].z <= lmax) + (v[r].w <= lmax);
+                qs += fixed_q_bits(v[r].x, qshift) + fixed_q_bits(v[r].y, qshift) +
+                      fixed_q_bits(v[r].z, qshift) + fixed_q_bits(v[r].w, qshift);
+            }
+        }
+        for (; i < b4; i += 32) {
             float4 v = __ldg(w4 + i);
             cnt += (v.x <= lmax) + (v.y <= lmax) + (v.z <= lmax) + (v.w <= lmax);
             qs += fixed_q_bits(v.x, qshift) + fixed_q_bits(v.y, qshift) +
