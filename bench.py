@@ -74,6 +74,12 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--batch-tables", type=int, default=100_000)
+    ap.add_argument("--sampler-heatmap", action="store_true",
+                    help="also time every sampling mode over a grid of table sizes and draw "
+                         "counts (Sec. 6, sampler comparison)")
+    ap.add_argument("--ablation", action="store_true",
+                    help="also time the split and pack steps for both split methods and "
+                         "every section size on this table (Sec. 6, split/pack variants)")
     return ap.parse_args()
 
 
@@ -365,6 +371,8 @@ def run_gpu(args):
 
     batched = None if args.no_batched else run_batched(args, world, rank)
     serving_res = None if args.no_serving else run_serving(args, rank)
+    heatmap = run_sampler_heatmap(args) if args.sampler_heatmap else None
+    ablation = run_ablation(args, w, n) if args.ablation else None
 
     hbm, peak_kind = peaks()
     build_gbs = BUILD_BYTES_PER_ITEM * n / (build_ms / 1e3) / 1e9
@@ -410,6 +418,8 @@ def run_gpu(args):
             "sectioned_sampling": sec,
             "batched": batched,
             "serving": serving_res,
+            **({"sampler_heatmap": heatmap} if heatmap is not None else {}),
+            **({"ablation": ablation} if ablation is not None else {}),
             "roofline": dominant, "build_roofline": build_roof, "sample_roofline": sample_roof,
             "cpu_baseline": cpu, "e2e": e2e, "accuracy": accuracy, "clocks": clk,
             "gpu_launches": args.steps * (KERNELS_PER_BUILD + KERNELS_PER_SAMPLE),
@@ -521,6 +531,85 @@ def run_batched(args, world, rank):
                                       for c in cand]},
             "graph_step_ms": graph_ms,
             "graph_items_per_s": total / (graph_ms / 1e3)}
+
+
+def _time_ms(fn, reps=3):
+    """Mean device time of fn() over reps runs after one warm-up (CUDA events)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_sampler_heatmap(args):
+    """Every sampling mode over table sizes x draw counts (the paper compares
+    its samplers over both axes, Sec. 6): uniform weights, a fresh table per
+    size.  Reports ms per cell and the fastest mode."""
+    import torch
+
+    import paper_2106_12270_gb300 as wrs
+    from paper_2106_12270_gb300 import inputs
+
+    sizes = [1 << k for k in (16, 20, 24, 27)]
+    counts = [1 << k for k in (16, 20, 24, 28)]
+    modes = [("naive", wrs.SAMPLE_NAIVE, 0), ("cached", wrs.SAMPLE_CACHED, 8192),
+             ("limited", wrs.SAMPLE_LIMITED, 8192), ("smem", wrs.SAMPLE_SMEM, 16384)]
+    out = torch.empty(max(counts), dtype=torch.int32, device="cuda")
+    cells = []
+    for n in sizes:
+        w = torch.from_numpy(inputs.uniform(n, 1)).cuda()
+        b = wrs.Builder(n)
+        rows = torch.empty(n, dtype=torch.int64, device="cuda")
+        b.build(w, rows)
+        torch.cuda.synchronize()
+        for c in counts:
+            cell = {"n": n, "count": c}
+            for name, mode, sec_rows in modes:
+                if mode == wrs.SAMPLE_NAIVE:
+                    ms = _time_ms(lambda: wrs.sample_rows(rows, n, 0, c, 2, out[:c]))
+                else:
+                    nsec = wrs.sample_sections(n, sec_rows)
+                    cnt = torch.empty(nsec, dtype=torch.int64, device="cuda")
+                    off = torch.empty(nsec, dtype=torch.int64, device="cuda")
+                    ms = _time_ms(lambda: wrs.sample_sectioned_rows(rows, n, c, 2, mode, sec_rows,
+                                                                    cnt, off, out[:c]))
+                cell[name] = ms
+            cell["best"] = min((k for k, _, _ in modes), key=lambda k: cell[k])
+            cell["auto"] = wrs.sample_auto_choice(n, c)
+            cells.append(cell)
+        del w, rows, b
+        torch.cuda.empty_cache()
+    return {"weights": "uniform [0,1) (seed 1)", "unit": "ms", "cells": cells}
+
+
+def run_ablation(args, w, n):
+    """Split and pack steps for both split methods (Sec. 4.1: partial p-ary
+    vs binary search) and every section size (Sec. 4.2) on the bench table."""
+    import torch
+
+    import paper_2106_12270_gb300 as wrs
+
+    res = []
+    rows = torch.empty(n, dtype=torch.int64, device="cuda")
+    for method, mname in ((wrs.SPLIT_PARY, "pary"), (wrs.SPLIT_BINARY, "binary")):
+        for sec in (256, 512, 1024, 2048, 4096, 8192):
+            cfg = wrs.config(sec, method)
+            ws = torch.empty(wrs.build_workspace_bytes(n, cfg), dtype=torch.uint8, device="cuda")
+            wrs.step_total(w, ws, cfg)
+            wrs.step_partition(w, ws, cfg)
+            split_ms = _time_ms(lambda: wrs.step_split(n, ws, cfg))
+            pack_ms = _time_ms(lambda: wrs.step_pack(n, rows, ws, cfg))
+            res.append({"split": mname, "section": sec, "split_ms": split_ms, "pack_ms": pack_ms})
+            del ws
+            torch.cuda.empty_cache()
+    return {"n": n, "dist": args.dist, "steps": res}
 
 
 def run_serving(args, rank):

@@ -229,7 +229,8 @@ enum wrs_sample_mode {
     WRS_SAMPLE_NAIVE = 0,
     WRS_SAMPLE_CACHED = 1,
     WRS_SAMPLE_LIMITED = 2,
-    WRS_SAMPLE_SMEM = 3
+    WRS_SAMPLE_SMEM = 3,
+    WRS_SAMPLE_AUTO = 4   /* wrs_sample_auto: pick one of the above */
 };
 
 /* Number of sections for n rows with at most section_rows rows each:
@@ -251,6 +252,28 @@ int wrs_sample_sectioned_rows(const wrs_row *d_rows, uint64_t n, uint64_t count,
                               uint64_t seed, uint32_t mode, uint32_t section_rows,
                               uint64_t *d_counts, uint64_t *d_offsets, uint32_t *d_out,
                               void *stream);
+
+/* Sampling method selection (the paper compares its samplers over table
+ * size and sample count, Sec. 6): the mode and section size wrs_sample_auto
+ * uses for n rows and count samples.  The rule comes from the measured
+ * heat map of all modes on GB300 (bench --sampler-heatmap): cached
+ * sectioned sampling (8192 rows per section) for tables of at least 2^23
+ * rows and at least 2^23 draws, naive sampling otherwise. */
+int wrs_sample_auto_choice(uint64_t n, uint64_t count, uint32_t *mode, uint32_t *section_rows);
+
+/* Device workspace of wrs_sample_auto: the per-section counts and offsets of
+ * the chosen sectioned mode (0 bytes when it picks naive sampling). */
+int wrs_sample_auto_workspace_bytes(uint64_t n, uint64_t count, uint64_t *bytes);
+
+/* Draws `count` samples into d_out with the mode wrs_sample_auto_choice
+ * picks: naive (samples 0..count-1 of stream (seed, 0, WRS_TAG_NAIVE), as
+ * wrs_sample_rows) or sectioned (as wrs_sample_sectioned_rows, grouped by
+ * section; counts and offsets in d_ws).  *mode_used (may be NULL) receives
+ * the mode.  Every mode draws from the same distribution; the output depends
+ * on (n, count, seed) only. */
+int wrs_sample_auto(const wrs_row *d_rows, uint64_t n, uint64_t count, uint64_t seed,
+                    uint32_t *d_out, void *d_ws, uint64_t ws_bytes, uint32_t *mode_used,
+                    void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Batches of independent tables (one launch for many tables)              */

@@ -106,6 +106,10 @@ def lib():
                 "wrs_sample_rows": (I, [P, U64, U64, U64, U64, U32, U32, P, P]),
                 "wrs_diag_random_gather": (I, [P, U64, U64, U64, I, P, P]),
                 "wrs_sample_sections": (I, [U64, U32, ctypes.POINTER(U64)]),
+                "wrs_sample_auto_choice": (I, [U64, U64, ctypes.POINTER(U32),
+                                               ctypes.POINTER(U32)]),
+                "wrs_sample_auto_workspace_bytes": (I, [U64, U64, ctypes.POINTER(U64)]),
+                "wrs_sample_auto": (I, [P, U64, U64, U64, P, P, U64, ctypes.POINTER(U32), P]),
                 "wrs_build_batched_workspace_bytes": (I, [U64, U32, ctypes.POINTER(U64)]),
                 "wrs_batch_order": (I, [P, U32, P]),
                 "wrs_build_batched_rows": (I, [P, P, U32, P, P, P, U64, P, P]),
@@ -244,6 +248,32 @@ def sample_sectioned_rows(rows, n: int, count: int, seed: int, mode: int, sectio
     _check(lib().wrs_sample_sectioned_rows(_ptr(rows), n, count, seed & (2**64 - 1), mode,
                                            section_rows, _ptr(counts), _ptr(offsets), _ptr(out),
                                            _stream(stream)), "wrs_sample_sectioned_rows")
+
+
+MODE_NAMES = {0: "naive", 1: "cached", 2: "limited", 3: "smem"}
+
+
+def sample_auto_choice(n: int, count: int) -> str:
+    """The sampling mode wrs_sample_auto picks for n rows and count draws."""
+    mode, rows = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().wrs_sample_auto_choice(n, count, ctypes.byref(mode), ctypes.byref(rows)),
+           "wrs_sample_auto_choice")
+    return MODE_NAMES[mode.value]
+
+
+def sample_auto(rows, n: int, count: int, seed: int, out, stream=None) -> str:
+    """Draw count samples with the automatically chosen mode (wrs_sample_auto);
+    returns the mode's name.  The workspace is a torch tensor on the device."""
+    import torch
+    nb = ctypes.c_uint64()
+    _check(lib().wrs_sample_auto_workspace_bytes(n, count, ctypes.byref(nb)),
+           "wrs_sample_auto_workspace_bytes")
+    ws = torch.empty(max(nb.value, 256), dtype=torch.uint8, device=rows.device)
+    used = ctypes.c_uint32()
+    _check(lib().wrs_sample_auto(_ptr(rows), n, count, seed & (2**64 - 1), _ptr(out), _ptr(ws),
+                                 ws.numel(), ctypes.byref(used), _stream(stream)),
+           "wrs_sample_auto")
+    return MODE_NAMES[used.value]
 
 
 SUMMARY_DTYPE = np.dtype([("status", "<i4"), ("n", "<u4"), ("W", "<f8"), ("nl", "<u8"),

@@ -218,6 +218,53 @@ int wrs_sample_sectioned_rows(const wrs_row *d_rows, uint64_t n, uint64_t count,
                                                d_offsets, d_out, (cudaStream_t)stream));
 }
 
+int wrs_sample_auto_choice(uint64_t n, uint64_t count, uint32_t *mode, uint32_t *section_rows) {
+    if (!mode || !section_rows || n == 0) return WRS_EINVAL;
+    // measured on GB300 (sampler heat map over 2^16..2^27 rows and 2^16..2^28
+    // draws): naive sampling wins while the table fits in L2; above about
+    // half of L2 (2^23 rows = 64 MB) a naive draw costs 9-21 ps, a cached
+    // sectioned draw 3.4 ps plus 0.05-0.15 ms for the count tree, so the
+    // sectioned mode pays from about 2^23 draws on
+    const bool sectioned = n >= (1ull << 23) && count >= (1ull << 23);
+    *mode = sectioned ? WRS_SAMPLE_CACHED : WRS_SAMPLE_NAIVE;
+    *section_rows = sectioned ? 8192u : 0u;
+    return WRS_OK;
+}
+
+int wrs_sample_auto_workspace_bytes(uint64_t n, uint64_t count, uint64_t *bytes) {
+    if (!bytes) return WRS_EINVAL;
+    uint32_t mode, rows;
+    int rc = wrs_sample_auto_choice(n, count, &mode, &rows);
+    if (rc) return rc;
+    uint64_t nsec = 0;
+    if (mode != WRS_SAMPLE_NAIVE) {
+        rc = wrs_sample_sections(n, rows, &nsec);
+        if (rc) return rc;
+    }
+    *bytes = 2 * align_up(8 * nsec, 256);
+    return WRS_OK;
+}
+
+int wrs_sample_auto(const wrs_row *d_rows, uint64_t n, uint64_t count, uint64_t seed,
+                    uint32_t *d_out, void *d_ws, uint64_t ws_bytes, uint32_t *mode_used,
+                    void *stream) {
+    uint32_t mode, rows;
+    int rc = wrs_sample_auto_choice(n, count, &mode, &rows);
+    if (rc) return rc;
+    if (mode_used) *mode_used = mode;
+    if (mode == WRS_SAMPLE_NAIVE)
+        return wrs_sample_rows(d_rows, n, 0, count, seed, 0, WRS_TAG_NAIVE, d_out, stream);
+    uint64_t nsec = 0;
+    rc = wrs_sample_sections(n, rows, &nsec);
+    if (rc) return rc;
+    const uint64_t half = align_up(8 * nsec, 256);
+    if (!d_ws || ((uintptr_t)d_ws & 255u) || ws_bytes < 2 * half) return WRS_EINVAL;
+    unsigned char *ws = (unsigned char *)d_ws;
+    return wrs_sample_sectioned_rows(d_rows, n, count, seed, mode, rows,
+                                     reinterpret_cast<uint64_t *>(ws),
+                                     reinterpret_cast<uint64_t *>(ws + half), d_out, stream);
+}
+
 int wrs_build_batched_workspace_bytes(uint64_t total, uint32_t ntab, uint64_t *bytes) {
     if (!bytes) return WRS_EINVAL;
     (void)ntab;

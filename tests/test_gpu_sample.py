@@ -82,3 +82,31 @@ def test_naive_small_tables():
         want = oracle.sample_naive(b.prob, b.alias, 0, 10001, 3)
         assert np.array_equal(got, want)
         assert got.max() < n
+
+
+def test_auto_choice_rule():
+    assert wrs.sample_auto_choice(1000, 10**9) == "naive"          # table in L2
+    assert wrs.sample_auto_choice(1 << 27, 1000) == "naive"        # few draws
+    assert wrs.sample_auto_choice(1 << 27, 1 << 28) == "cached"    # many draws, large table
+    assert wrs.sample_auto_choice(1 << 27, 1 << 24) == "cached"
+    assert wrs.sample_auto_choice(1 << 24, 1 << 20) == "naive"
+
+
+@pytest.mark.parametrize("n,count", [(100_003, 1_000_001), (1 << 23, 9_000_001)])
+def test_auto_draws_exactly_what_the_chosen_mode_draws(n, count):
+    w = inputs.by_name("zipf", n, 11)
+    b = Built(w)
+    out = torch.empty(count, dtype=torch.int32, device="cuda")
+    mode = wrs.sample_auto(b.rows_t, n, count, 42, out)
+    torch.cuda.synchronize()
+    assert mode == wrs.sample_auto_choice(n, count)
+    want = torch.empty_like(out)
+    if mode == "naive":
+        wrs.sample_rows(b.rows_t, n, 0, count, 42, want)
+    else:
+        nsec = wrs.sample_sections(n, 8192)
+        cnt = torch.empty(nsec, dtype=torch.int64, device="cuda")
+        off = torch.empty(nsec, dtype=torch.int64, device="cuda")
+        wrs.sample_sectioned_rows(b.rows_t, n, count, 42, wrs.SAMPLE_CACHED, 8192, cnt, off, want)
+    torch.cuda.synchronize()
+    assert torch.equal(out, want)
