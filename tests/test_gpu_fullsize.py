@@ -1,0 +1,96 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the
+bench times (section size 1024, partial p-ary splits, naive sampling with
+Philox seed 2): properties that hold at any size, and sampled outputs the
+oracle computes one by one.
+
+* N = 1e8 shuffled power law (seed 3): exact W and light/heavy counts, list
+  entries at sampled ranks, every item's mass, the rows against the oracle's
+  PSA sweep, and sampled draws of the 1e9-draw stream against the oracle's
+  sampler on the exported table.
+* N = 2^30 Exp(1) (seed 4): exact W and counts, every item's mass.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2106_12270_gb300 as wrs
+from paper_2106_12270_gb300 import inputs
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def build(w_host):
+    n = w_host.size
+    w = torch.from_numpy(w_host).cuda()
+    cfg = wrs.config(1024, wrs.SPLIT_PARY)
+    b = wrs.Builder(n, cfg)
+    rows = torch.empty(n, dtype=torch.int64, device="cuda")
+    b.build(w, rows)
+    torch.cuda.synchronize()
+    info = wrs.parse_info(b.info)
+    return w, b, rows, info
+
+
+def device_mass_error(rows, w, W):
+    """max_i |mass_i - N w_i/W| / max(1, N w_i/W) in FP64 on the device."""
+    n = w.numel()
+    raw = rows.view(torch.int32).view(n, 2)
+    prob = raw[:, 0].view(torch.float32).double()
+    alias = raw[:, 1].long()
+    mass = prob.clone()
+    mass.index_add_(0, alias, 1.0 - prob)
+    expect = w.double() * (n / W)
+    return float(((mass - expect).abs() / expect.clamp(min=1.0)).max())
+
+
+def test_full_size_1e8_power_law_build_and_samples():
+    n = 100_000_000
+    w_host = inputs.zipf_permuted(n, 3)
+    w, b, rows, info = build(w_host)
+    assert info["status"] == wrs.OK
+    W = oracle.exact_sum(w_host)
+    assert info["W"] == W
+    light = w_host.astype(np.float64) <= W / n
+    nl = int(light.sum())
+    assert (info["nl"], info["nh"]) == (nl, n - nl)
+    # list entries at sampled ranks: the k-th light / heavy in index order
+    rng = np.random.default_rng(11)
+    lpos = np.flatnonzero(light)
+    hpos = np.flatnonzero(~light)
+    lh = wrs.build_layout(n, b.cfg)["lh"]
+    raw = b.ws[lh: lh + 8 * n].view(torch.int32).view(n, 2).cpu().numpy()
+    for k in rng.integers(0, nl, 2000):
+        assert int(raw[k, 0]) == lpos[k]
+    for k in rng.integers(0, n - nl, 2000):
+        assert int(raw[n - 1 - k, 0]) == hpos[k]
+    assert device_mass_error(rows, w, W) <= 1e-5
+    # rows against the oracle's PSA sweep with the same sections
+    prob, alias = wrs.rows_to_numpy(rows)
+    t = oracle.psa(w_host, 1024)
+    same = alias == t["alias"]
+    assert (~same).sum() <= n // 10000
+    assert np.max(np.abs(prob[same] - t["prob"][same])) < 1e-6
+    # sampled draws of the bench's 1e9-draw stream (seed 2)
+    count = 1_000_000_000
+    out = torch.empty(count, dtype=torch.int32, device="cuda")
+    wrs.sample_rows(rows, n, 0, count, 2, out)
+    torch.cuda.synchronize()
+    for q in rng.integers(0, count - 64, 200):
+        want = oracle.sample_naive(prob, alias, int(q), 64, 2, 0, wrs.TAG_NAIVE)
+        got = out[int(q): int(q) + 64].cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, want), q
+
+
+def test_full_size_2pow30_exponential_build():
+    n = 1 << 30
+    w_host = inputs.exponential(n, 4)
+    w, b, rows, info = build(w_host)
+    assert info["status"] == wrs.OK
+    W = oracle.exact_sum(w_host)
+    assert info["W"] == W
+    nl = int(torch.count_nonzero(w.double() <= W / n))
+    assert (info["nl"], info["nh"]) == (nl, n - nl)
+    assert device_mass_error(rows, w, W) <= 1e-5
