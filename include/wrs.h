@@ -47,7 +47,7 @@ enum wrs_status {
     WRS_EZEROSUM = 2,    /* all weights are zero: no distribution (Sec. 1) */
     WRS_ENONFINITE = 3,  /* a weight is NaN or infinite */
     WRS_ENOMEM = 4,      /* device allocation failed or budget exceeded */
-    WRS_ETIMEOUT = 5,    /* a bounded device wait gave up */
+    WRS_ETIMEOUT = 5,    /* reserved: no kernel waits on another, none times out */
     WRS_ECUDA = 6,       /* a CUDA runtime call failed */
     WRS_EBUSY = 7,       /* request loop: no room right now */
     WRS_ENOTFOUND = 8    /* request loop: unknown ticket */

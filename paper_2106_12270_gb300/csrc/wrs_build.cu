@@ -56,7 +56,6 @@ Layout make_layout(uint64_t n, uint32_t S) {
         off = align_up(off + (bytes ? bytes : 1), 256);
         return o;
     };
-    L.ntiles = (n + kTile - 1) / kTile;
     L.sections = (n + S - 1) / S;
     L.params = take(sizeof(BuildParams));
     L.sum_bins = take((uint64_t)kSumMaxBlocks * kSumBands * sizeof(u128));
@@ -183,7 +182,7 @@ k_sum(const float *__restrict__ w, uint64_t n, u128 *__restrict__ bins_out,
 }
 
 // ===========================================================================
-// a2 + a3: classify, stable partition, prefix sums (decoupled look-back)
+// a2 + a3: classify, stable partition, prefix sums (per-warp sub-segments)
 // ===========================================================================
 
 
@@ -307,8 +306,6 @@ k_qsum(BuildParams *__restrict__ P, const uint32_t *__restrict__ seg_cnt,
     if (threadIdx.x == 0) {
         P->Q = Q;
         P->Qn = Q / n;
-        P->NQn = (u128)P->Qn * n;
-        P->NQn1 = P->NQn + n;
         P->Qf = __ull2float_rn(Q);
         P->invQ = __frcp_rn(P->Qf);
         P->nseg = NS;
@@ -641,9 +638,7 @@ k_split(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
         const CkRec *__restrict__ ckl, const CkRec *__restrict__ ckh,
         const SegVal *__restrict__ seg_pre, SplitRec *__restrict__ splits, uint64_t n,
         uint64_t S, uint32_t sections) {
-    __shared__ uint64_t s_c[kSplitThreads];
     __shared__ unsigned long long s_a, s_b;
-    __shared__ int s_go;
     if (P->status) return;
     const BuildParams Pm = *P;
     SplitCtx C;
@@ -696,8 +691,6 @@ k_split(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
         // record the fine search then writes in full
         splits[t].pad[0] = (uint32_t)a;
     }
-    (void)s_c;
-    (void)s_go;
 }
 
 // Fine phase of the interior splits: one warp per split (many in flight, so
@@ -952,8 +945,7 @@ __global__ void k_info(const BuildParams *__restrict__ P, wrs_build_info *__rest
     wrs_build_info r;
     r.status = (st & ERR_NONFINITE) ? WRS_ENONFINITE
              : (st & (ERR_NEGATIVE | ERR_INTERNAL)) ? WRS_EINVAL
-             : (st & ERR_ZEROSUM) ? WRS_EZEROSUM
-             : (st & ERR_TIMEOUT) ? WRS_ETIMEOUT : WRS_OK;
+             : (st & ERR_ZEROSUM) ? WRS_EZEROSUM : WRS_OK;
     r.scale = P->scale;
     r.W = P->W;
     r.avg = P->avg;

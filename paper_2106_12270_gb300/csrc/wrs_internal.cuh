@@ -19,13 +19,8 @@ enum : uint32_t {
     ERR_NEGATIVE = 1u,   // a weight with the sign bit set (other than -0)
     ERR_NONFINITE = 2u,  // NaN or Inf
     ERR_ZEROSUM = 4u,    // W == 0
-    ERR_TIMEOUT = 8u,    // a bounded wait gave up
     ERR_INTERNAL = 16u   // an invariant failed (reported as EINVAL)
 };
-
-// Upper bound on polls of one bounded wait (each poll sleeps up to ~256 ns,
-// so a wait gives up after roughly a quarter of a second).
-constexpr uint32_t kSpinLimit = 1u << 20;
 
 // ---------------------------------------------------------------------------
 // Build parameters, computed on the device by the total-weight and q-sum
@@ -38,8 +33,6 @@ constexpr uint32_t kSpinLimit = 1u << 20;
 struct __align__(16) BuildParams {
     u128 Dtot;         // D'(nl): total scaled light deficit
     u128 Etot;         // E'(nh): total scaled heavy excess
-    u128 NQn;          // N * Qn
-    u128 NQn1;         // N * (Qn + 1)
     double W;          // exact total weight rounded to FP64
     double avg;        // W / N
     uint64_t Q;        // sum of all q_i: one bucket in fixed point (< 2^63)
@@ -72,7 +65,6 @@ struct Layout {
     uint64_t ckh;        // (n/32 + 2) CkRec
     uint64_t splits;     // (s+1) SplitRec
     uint64_t total;
-    uint64_t ntiles;
     uint64_t sections;
 };
 
@@ -120,8 +112,6 @@ constexpr int kSumBands = 16;   // total weight: bands of 16 binades
 constexpr int kSumMaxBlocks = 1216;   // 8 x 152 SMs
 constexpr int kPartThreads = 256;
 constexpr int kPartItems = 16;
-constexpr int kTile = kPartThreads * kPartItems;   // 4096 items per tile
-constexpr int kPackThreads = 256;
 constexpr int kSegPerSM = 4;          // partition CTAs per SM (8 warps, one sub-segment each)
 constexpr int kMaxSegs = 8192;        // sub-segments (a multiple of 1024)
 constexpr int kChunk = 512;           // items a partition warp handles at a time
@@ -262,16 +252,6 @@ __device__ __forceinline__ uint32_t walker_pick(uint32_t row, uint32_t coin,
                                                 uint2 r) {
     uint64_t tau = __float2ull_ru(__uint_as_float(r.x) * 4294967296.0f);
     return (uint64_t)coin < tau ? row : r.y;
-}
-
-// Bounded-spin helpers for device-scope flags.
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 }  // namespace wrs
