@@ -64,8 +64,9 @@ struct BatchShared {
 
 __device__ __forceinline__ int pp8b(int e) { return e + (e >> 3); }
 
+// At most 64 registers: four 256-thread CTAs (or two of 512) per SM.
 template <int BT, int CH>
-__global__ void __launch_bounds__(BT, 512 / BT)
+__global__ void __launch_bounds__(BT, 1024 / BT)
 k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
                 const uint32_t *__restrict__ order, uint32_t ntab, uint32_t *__restrict__ counter,
                 Entry *__restrict__ lh, uint2 *__restrict__ rows, uint2 *const *__restrict__ row_ptrs,

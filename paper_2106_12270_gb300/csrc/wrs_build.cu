@@ -695,7 +695,7 @@ k_split(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
 
 // Fine phase of the interior splits: one warp per split (many in flight, so
 // the dependent loads of the warp search overlap across the GPU).
-__global__ void __launch_bounds__(kSplitThreads)
+__global__ void __launch_bounds__(kSplitThreads, 8)
 k_split_fine(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
              const CkRec *__restrict__ ckl, const CkRec *__restrict__ ckh,
              const SegVal *__restrict__ seg_pre, SplitRec *__restrict__ splits, uint64_t n,
