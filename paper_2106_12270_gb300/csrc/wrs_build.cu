@@ -790,22 +790,20 @@ __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
         return;   // inconsistent splits: write nothing
     }
 
-    // phase 1: coalesced load of the section's lights, heavies and the next
-    // heavy item (the alias of the last rows), all loads in flight at once
+    // phase 1: asynchronous copies of the section's lights, heavies and the
+    // next heavy item straight into shared memory
     {
         const uint2 *lh2 = reinterpret_cast<const uint2 *>(lh);
-        uint2 v[kPer + 1];
 #pragma unroll
         for (int r = 0; r <= kPer; ++r) {
             const uint32_t e = tid + r * T;
-            if (e < K + extra)
-                v[r] = __ldcs(lh2 + (e < L ? (uint64_t)i0 + e : n - 1 - ((uint64_t)j0 + (e - L))));
+            if (e < K + extra) {
+                const uint2 *src = lh2 + (e < L ? (uint64_t)i0 + e : n - 1 - ((uint64_t)j0 + (e - L)));
+                const uint32_t d = (uint32_t)__cvta_generic_to_shared(sE + pk16(e));
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+            }
         }
-#pragma unroll
-        for (int r = 0; r <= kPer; ++r) {
-            const uint32_t e = tid + r * T;
-            if (e < K + extra) sE[pk16(e)] = v[r];
-        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
     }
     __syncthreads();
 
