@@ -286,34 +286,49 @@ def run_gpu(args):
                                                             dist, "cuda")
     ms_per_step = total_ms / args.steps
 
-    # end to end through the C ABI with host buffers: pinned weights in,
-    # table rows out, copies inside the timed region
+    # end to end through the C ABI with host buffers (wrs_build_rows_host):
+    # pinned weights in, table rows and summary out, copies inside the timed
+    # region.  Two workspaces on two streams: one step's copy out overlaps
+    # the next step's copy in and build (as a pipeline of requests would).
     e2e = None
     if not args.no_e2e:
+        nbuf = 2
         w_pin = torch.from_numpy(w_host).pin_memory()
-        rows_pin = torch.empty(n, dtype=torch.int64).pin_memory()
-        w_dev = torch.empty_like(w)
+        rows_pin = [torch.empty(n, dtype=torch.int64).pin_memory() for _ in range(nbuf)]
+        info_pin = [torch.zeros(wrs.INFO_BYTES, dtype=torch.uint8).pin_memory()
+                    for _ in range(nbuf)]
+        hws = [torch.empty(wrs.build_host_workspace_bytes(n, cfg), dtype=torch.uint8,
+                           device="cuda") for _ in range(nbuf)]
+        streams = [torch.cuda.Stream() for _ in range(nbuf)]
 
-        def e2e_step():
-            w_dev.copy_(w_pin, non_blocking=True)
-            wrs.build_rows(w_dev, rows, builder.ws, builder.info, cfg)
-            rows_pin.copy_(rows, non_blocking=True)
+        def e2e_steps(k0, k1):
+            for k in range(k0, k1):
+                b = k % nbuf
+                wrs.build_rows_host(w_pin, rows_pin[b], hws[b], info_pin[b], cfg, streams[b])
 
-        for _ in range(max(1, args.warmup)):
-            e2e_step()
+        e2e_steps(0, max(2, args.warmup))
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
+        for st in streams:
+            st.wait_event(a)
+        e2e_steps(0, args.steps)
+        for st in streams:
+            stream.wait_stream(st)
         b.record(stream)
         torch.cuda.synchronize()
         e2e_ms = a.elapsed_time(b) / args.steps
+        bad = [wrs.parse_info(x)["status"] for x in info_pin if wrs.parse_info(x)["status"]]
+        if bad:
+            raise RuntimeError(f"host build failed: {bad}")
+        if not torch.equal(rows_pin[(args.steps - 1) % nbuf], rows.cpu()):
+            raise RuntimeError("host build differs from the device build")
         e2e_ms = replicas.max_over_ranks([e2e_ms], dist, "cuda")[0]
         e2e = {"value": replicas.job_rate(n, world, e2e_ms), "unit": "items/s",
-               "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n,
-               "ms_per_step": e2e_ms}
+               "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n + wrs.INFO_BYTES,
+               "ms_per_step": e2e_ms, "api": "wrs_build_rows_host",
+               "pipelining": f"{nbuf} workspaces on {nbuf} streams"}
 
     # accuracy of the timed table: the reconstructed mass of every item
     # against N w_i / W in FP64 (plain numpy on the host; the stated bound is

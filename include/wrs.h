@@ -152,6 +152,19 @@ int wrs_build_rows(const float *d_w, uint64_t n, wrs_row *d_rows,
                    void *d_ws, uint64_t ws_bytes, const wrs_config *cfg,
                    wrs_build_info *d_info, void *stream);
 
+/* Full build from host memory: h_w (n FP32 weights, host) -> h_rows (n rows,
+ * host), with the copies on `stream`: weights in, the build of
+ * wrs_build_rows, rows and the summary (h_info, host) out.  With pinned host
+ * buffers the call only enqueues; the caller syncs the stream before reading
+ * h_rows.  Two workspaces on two streams let one call's copy out overlap the
+ * next call's copy in and build.  d_ws: >= wrs_build_host_workspace_bytes(n)
+ * bytes, 256-byte aligned, device (the build workspace plus a device copy of
+ * the weights and the rows). */
+int wrs_build_host_workspace_bytes(uint64_t n, const wrs_config *cfg, uint64_t *bytes);
+int wrs_build_rows_host(const float *h_w, uint64_t n, wrs_row *h_rows, void *d_ws,
+                        uint64_t ws_bytes, const wrs_config *cfg, wrs_build_info *h_info,
+                        void *stream);
+
 /* The same build without allocating anything (the paper has no counterpart;
  * it serves callers that cannot allocate device memory when they build: a
  * service whose device memory is all reserved at start-up, or code inside a

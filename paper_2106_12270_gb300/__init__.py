@@ -98,6 +98,8 @@ def lib():
                 "wrs_build_layout": (I, [U64, CP, ctypes.POINTER(Layout)]),
                 "wrs_build_rows": (I, [P, U64, P, P, U64, CP, P, P]),
                 "wrs_build_rows_noalloc": (I, [P, U64, P, CP, P, P]),
+                "wrs_build_host_workspace_bytes": (I, [U64, CP, ctypes.POINTER(U64)]),
+                "wrs_build_rows_host": (I, [P, U64, P, P, U64, CP, P, P]),
                 "wrs_step_total": (I, [P, U64, P, U64, CP, P]),
                 "wrs_step_partition": (I, [P, U64, P, U64, CP, P]),
                 "wrs_step_split": (I, [U64, P, U64, CP, P]),
@@ -199,6 +201,23 @@ def build_rows_noalloc(w, rows, info, cfg: Config | None = None, stream=None):
     library; n <= 3.5 million; calls on one device must not overlap)."""
     _check(lib().wrs_build_rows_noalloc(_ptr(w), w.numel(), _ptr(rows), _cfg(cfg), _ptr(info),
                                         _stream(stream)), "wrs_build_rows_noalloc")
+
+
+def build_host_workspace_bytes(n: int, cfg: Config | None = None) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().wrs_build_host_workspace_bytes(n, _cfg(cfg), ctypes.byref(out)),
+           "wrs_build_host_workspace_bytes")
+    return out.value
+
+
+def build_rows_host(w_host, rows_host, ws, info_host, cfg: Config | None = None, stream=None):
+    """Enqueue a build from host memory (wrs_build_rows_host): w_host (float32
+    [n], host, pinned for an asynchronous call) -> rows_host (int64 [n], host);
+    info_host: uint8 [INFO_BYTES] host tensor for the summary."""
+    n = w_host.numel()
+    _check(lib().wrs_build_rows_host(_ptr(w_host), n, _ptr(rows_host), _ptr(ws),
+                                     ws.numel() * ws.element_size(), _cfg(cfg), _ptr(info_host),
+                                     _stream(stream)), "wrs_build_rows_host")
 
 
 def step_total(w, ws, cfg=None, stream=None):

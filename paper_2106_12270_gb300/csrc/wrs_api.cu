@@ -186,6 +186,48 @@ int wrs_build_rows(const float *d_w, uint64_t n, wrs_row *d_rows, void *d_ws, ui
     return cuda_status(e);
 }
 
+// Host-buffer build: [build workspace][weights][rows][summary], each region
+// 256-byte aligned.
+static uint64_t host_ws_regions(uint64_t build_total, uint64_t n, uint64_t *w_off, uint64_t *r_off,
+                                uint64_t *i_off) {
+    *w_off = align_up(build_total, 256);
+    *r_off = *w_off + align_up(4 * n, 256);
+    *i_off = *r_off + align_up(8 * n, 256);
+    return *i_off + align_up(sizeof(wrs_build_info), 256);
+}
+
+int wrs_build_host_workspace_bytes(uint64_t n, const wrs_config *cfg, uint64_t *bytes) {
+    uint64_t b = 0;
+    int rc = wrs_build_workspace_bytes(n, cfg, &b);
+    if (rc) return rc;
+    uint64_t wo, ro, io;
+    *bytes = host_ws_regions(b, n, &wo, &ro, &io);
+    return WRS_OK;
+}
+
+int wrs_build_rows_host(const float *h_w, uint64_t n, wrs_row *h_rows, void *d_ws,
+                        uint64_t ws_bytes, const wrs_config *cfg, wrs_build_info *h_info,
+                        void *stream) {
+    uint64_t b = 0;
+    int rc = wrs_build_workspace_bytes(n, cfg, &b);
+    if (rc) return rc;
+    if (!h_w || !h_rows || !h_info || !d_ws || ((uintptr_t)d_ws & 255u)) return WRS_EINVAL;
+    uint64_t wo, ro, io;
+    if (ws_bytes < host_ws_regions(b, n, &wo, &ro, &io)) return WRS_EINVAL;
+    unsigned char *ws = (unsigned char *)d_ws;
+    float *d_w = reinterpret_cast<float *>(ws + wo);
+    wrs_row *d_rows = reinterpret_cast<wrs_row *>(ws + ro);
+    wrs_build_info *d_info = reinterpret_cast<wrs_build_info *>(ws + io);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(d_w, h_w, 4 * n, cudaMemcpyHostToDevice, st);
+    if (e) return cuda_status(e);
+    rc = wrs_build_rows(d_w, n, d_rows, d_ws, b, cfg, d_info, stream);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(h_rows, d_rows, 8 * n, cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaMemcpyAsync(h_info, d_info, sizeof(wrs_build_info), cudaMemcpyDeviceToHost, st);
+    return cuda_status(e);
+}
+
 int wrs_sample_rows(const wrs_row *d_rows, uint64_t n, uint64_t first, uint64_t count,
                     uint64_t seed, uint32_t stream_lo, uint32_t stream_hi, uint32_t *d_out,
                     void *stream) {

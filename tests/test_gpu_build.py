@@ -288,3 +288,25 @@ def test_total_weight_wide_range_random():
         assert b.info["W"] == oracle.exact_sum(w), trial
         l, h = oracle.classify(w, b.info["W"] / n)
         assert (b.info["nl"], b.info["nh"]) == (len(l), len(h))
+
+
+@pytest.mark.parametrize("n", [1, 4097, 1_000_003])
+def test_host_buffer_build_equals_device_build(n):
+    """wrs_build_rows_host: weights and rows in (pinned) host memory, the
+    copies on the stream; the same table as the device build."""
+    w = inputs.by_name("zipf", n, 77)
+    b = Built(w)
+    cfg = wrs.config()
+    ws = torch.empty(wrs.build_host_workspace_bytes(n, cfg), dtype=torch.uint8, device="cuda")
+    w_pin = torch.from_numpy(w).pin_memory()
+    rows_pin = torch.zeros(n, dtype=torch.int64).pin_memory()
+    info_pin = torch.zeros(wrs.INFO_BYTES, dtype=torch.uint8).pin_memory()
+    s = torch.cuda.Stream()
+    wrs.build_rows_host(w_pin, rows_pin, ws, info_pin, cfg, s)
+    s.synchronize()
+    info = wrs.parse_info(info_pin)
+    assert info["status"] == wrs.OK and info["W"] == b.info["W"]
+    assert torch.equal(rows_pin, b.rows_t.cpu())
+    # too small a workspace is refused before anything is enqueued
+    with pytest.raises(wrs.WrsError):
+        wrs.build_rows_host(w_pin, rows_pin, ws[: ws.numel() // 2], info_pin, cfg, s)
