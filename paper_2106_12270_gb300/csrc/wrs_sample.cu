@@ -179,9 +179,8 @@ k_sample_sec(const uint2 *__restrict__ rows, uint64_t n, uint64_t nsec,
         __syncthreads();
     }
     const uint64_t calls = (c + 1) >> 1;
-    for (uint64_t cc = threadIdx.x; cc < calls; cc += blockDim.x) {
-        uint4 x = philox4x32_10(
-            make_uint4((uint32_t)cc, (uint32_t)(cc >> 32), (uint32_t)s, WRS_TAG_SECTION), k0, k1);
+    // two independent Philox calls per thread and step (interleaved chains)
+    auto one = [&](uint64_t cc, uint4 x) {
         uint64_t ra, rb;
         uint32_t ca, cb;
         walker_split(((uint64_t)x.x << 32) | x.y, R, ra, ca);
@@ -197,7 +196,22 @@ k_sample_sec(const uint2 *__restrict__ rows, uint64_t n, uint64_t nsec,
         } else {
             out[q] = sa;
         }
+    };
+    const uint64_t B = blockDim.x;
+    uint64_t cc = threadIdx.x;
+    for (; cc + B < calls; cc += 2 * B) {
+        const uint64_t c2 = cc + B;
+        const uint4 x1 = philox4x32_10(
+            make_uint4((uint32_t)cc, (uint32_t)(cc >> 32), (uint32_t)s, WRS_TAG_SECTION), k0, k1);
+        const uint4 x2 = philox4x32_10(
+            make_uint4((uint32_t)c2, (uint32_t)(c2 >> 32), (uint32_t)s, WRS_TAG_SECTION), k0, k1);
+        one(cc, x1);
+        one(c2, x2);
     }
+    if (cc < calls)
+        one(cc, philox4x32_10(
+                    make_uint4((uint32_t)cc, (uint32_t)(cc >> 32), (uint32_t)s, WRS_TAG_SECTION),
+                    k0, k1));
 }
 
 // Shared memory a LIMITED-mode CTA requests (and does not use) so that only
