@@ -396,9 +396,7 @@ k_batched_sample(const uint2 *__restrict__ rows, const uint64_t *__restrict__ of
         const uint64_t o = cnt_off[t], c = cnt_off[t + 1] - o;
         if (n == 0) continue;
         const uint64_t calls = (c + 1) >> 1;
-        for (uint64_t cc = threadIdx.x; cc < calls; cc += blockDim.x) {
-            uint4 x = philox4x32_10(make_uint4((uint32_t)cc, (uint32_t)(cc >> 32), t, WRS_TAG_BATCH),
-                                    k0, k1);
+        auto one = [&](uint64_t cc, uint4 x) {
             uint64_t ra, rb;
             uint32_t ca, cb;
             walker_split(((uint64_t)x.x << 32) | x.y, n, ra, ca);
@@ -407,7 +405,22 @@ k_batched_sample(const uint2 *__restrict__ rows, const uint64_t *__restrict__ of
             uint64_t q = o + 2 * cc;
             out[q] = walker_pick((uint32_t)ra, ca, va);
             if (2 * cc + 1 < c) out[q + 1] = walker_pick((uint32_t)rb, cb, vb);
+        };
+        // two independent Philox calls per thread and step (interleaved chains)
+        const uint64_t B = blockDim.x;
+        uint64_t cc = threadIdx.x;
+        for (; cc + B < calls; cc += 2 * B) {
+            const uint64_t c2 = cc + B;
+            const uint4 x1 = philox4x32_10(
+                make_uint4((uint32_t)cc, (uint32_t)(cc >> 32), t, WRS_TAG_BATCH), k0, k1);
+            const uint4 x2 = philox4x32_10(
+                make_uint4((uint32_t)c2, (uint32_t)(c2 >> 32), t, WRS_TAG_BATCH), k0, k1);
+            one(cc, x1);
+            one(c2, x2);
         }
+        if (cc < calls)
+            one(cc, philox4x32_10(make_uint4((uint32_t)cc, (uint32_t)(cc >> 32), t, WRS_TAG_BATCH),
+                                  k0, k1));
     }
 }
 
