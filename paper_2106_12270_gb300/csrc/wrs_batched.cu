@@ -444,9 +444,7 @@ k_sample_requests(const SampleReq *__restrict__ req, const uint32_t *__restrict_
     const uint64_t q0 = (uint64_t)(blk - chunk_off[lo]) * kReqChunk;
     const uint64_t q1 = min(q0 + kReqChunk, R.count);
     const uint2 *rows = reinterpret_cast<const uint2 *>(R.rows);
-    for (uint64_t cc = (q0 >> 1) + threadIdx.x; 2 * cc < q1; cc += blockDim.x) {
-        uint4 x = philox4x32_10(make_uint4((uint32_t)cc, (uint32_t)(cc >> 32), R.slo, R.shi), R.k0,
-                                R.k1);
+    auto one = [&](uint64_t cc, uint4 x) {
         uint64_t ra, rb;
         uint32_t ca, cb;
         walker_split(((uint64_t)x.x << 32) | x.y, R.n, ra, ca);
@@ -454,7 +452,20 @@ k_sample_requests(const SampleReq *__restrict__ req, const uint32_t *__restrict_
         uint64_t q = 2 * cc;
         R.out[q] = walker_pick((uint32_t)ra, ca, __ldg(rows + ra));
         if (q + 1 < q1) R.out[q + 1] = walker_pick((uint32_t)rb, cb, __ldg(rows + rb));
+    };
+    auto draw = [&](uint64_t cc) {
+        return philox4x32_10(make_uint4((uint32_t)cc, (uint32_t)(cc >> 32), R.slo, R.shi), R.k0,
+                             R.k1);
+    };
+    // two independent Philox calls per thread and step (interleaved chains)
+    const uint64_t B = blockDim.x;
+    uint64_t cc = (q0 >> 1) + threadIdx.x;
+    for (; 2 * (cc + B) < q1; cc += 2 * B) {
+        const uint4 x1 = draw(cc), x2 = draw(cc + B);
+        one(cc, x1);
+        one(cc + B, x2);
     }
+    if (2 * cc < q1) one(cc, draw(cc));
 }
 
 cudaError_t launch_sample_requests(const SampleReq *d_req, const uint32_t *d_chunk_off,
