@@ -42,6 +42,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "wrs_device.cuh"
 
@@ -882,7 +883,8 @@ __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
         uint32_t lo = d0 > H ? d0 - H : 0, hi = d0 < L ? d0 : L;
         while (lo < hi) {
             const uint32_t m = (lo + hi) >> 1;
-            const bool p = (d0 - m == 0) || (m == L) || (Bv(d0 - m - 1) <= Av(m));
+            // m < hi <= min(d0, L): both neighbours exist
+            const bool p = Bv(d0 - m - 1) <= Av(m);
             if (p) hi = m;
             else lo = m + 1;
         }
@@ -895,29 +897,36 @@ __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
         // heavy after the section); without one the item keeps its bucket.
         // A heavy keeps 1 - (A - B) 2^15 / Q of its bucket.
         const uint32_t hleft = (uint32_t)min(nh - (uint64_t)j0, (uint64_t)K + 1);
+        // hcur: item of heavy y, the one that fills the next light bucket
+        uint32_t hcur = y < hleft ? sE[pk16(L + y)].x : 0u;
+        auto merge = [&](auto kFull) {
 #pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            if (d0 + k < K) {
-                const bool heavy = (y < H) && (x == L || b <= a);
-                const uint32_t pos = heavy ? L + y : x;
-                const uint32_t nxt = heavy ? y + 1 : y;
-                const bool has = nxt < hleft;
-                const uint2 ep = sE[pk16(pos)];   // the closed item and its weight
-                uint32_t alias = ep.x;
-                float prob = 1.0f;
-                if (has) {
-                    alias = sE[pk16(L + nxt)].x;
-                    prob = heavy ? (b > a ? 1.0f
-                                          : fminf(fmaxf(1.0f - __ll2float_rn(a - b) * invQk, 0.0f),
-                                                  1.0f))
-                                 : fminf(__uint_as_float(ep.y) * inv_avg, 1.0f);
+            for (int k = 0; k < kPer; ++k) {
+                if (d0 + k < K) {
+                    const bool heavy = (y < H) && (x == L || b <= a);
+                    // one entry load per step: the closed light (item and
+                    // weight), or the heavy after the closed one (its item)
+                    const uint2 ld = sE[pk16(heavy ? L + y + 1 : x)];
+                    const uint32_t item = heavy ? hcur : ld.x;
+                    const bool has = decltype(kFull)::value || (heavy ? y + 1 : y) < hleft;
+                    uint32_t alias = item;
+                    float prob = 1.0f;
+                    if (has) {
+                        alias = heavy ? ld.x : hcur;
+                        prob = heavy ? fminf(fmaxf(1.0f - __ll2float_rn(a - b) * invQk, 0.0f), 1.0f)
+                                     : fminf(__uint_as_float(ld.y) * inv_avg, 1.0f);
+                    }
+                    rows[item] = make_uint2(__float_as_uint(prob), alias);
+                    const int64_t v = sK[pk16(heavy ? L + y + 2 : x + 1)];
+                    if (heavy) { ++y; b = v; hcur = ld.x; }
+                    else { ++x; a = v; }
                 }
-                rows[ep.x] = make_uint2(__float_as_uint(prob), alias);
-                const int64_t v = sK[pk16(heavy ? L + y + 2 : x + 1)];
-                if (heavy) { ++y; b = v; }
-                else { ++x; a = v; }
             }
-        }
+        };
+        // every closed item has a next heavy unless the heavy list ends
+        // within K + 1 entries of the section's first heavy
+        if (hleft > K) merge(std::true_type());
+        else merge(std::false_type());
     }
 }
 
