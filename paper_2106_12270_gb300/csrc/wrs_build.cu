@@ -305,11 +305,28 @@ k_qsum(BuildParams *__restrict__ P, const uint32_t *__restrict__ seg_cnt,
         ce += c[k];
     }
     if (threadIdx.x == 0) {
+        const uint64_t Qn = Q / n;
         P->Q = Q;
-        P->Qn = Q / n;
+        P->Qn = Qn;
         P->Qf = __ull2float_rn(Q);
         P->invQ = __frcp_rn(P->Qf);
         P->nseg = NS;
+        // Clamps: a light (w <= lmax) changes only if q > Qn, i.e. w >= wq
+        // with wq the least weight of q >= Qn + 1, about (Qn + 1/2) 2^-S;
+        // a heavy only if w < wq.  Both lie between lmax and wq; the
+        // interval below covers that range with a relative margin of 2^-16
+        // (far above the FP64 and FP32 rounding of its ends).
+        const double wq = ldexp((double)Qn + 0.5, -P->scale);
+        const double lm = (double)P->light_max;
+        const double lo = fmin(wq, lm) * (1.0 - 0x1p-16);
+        const double hi = fmax(wq, lm) * (1.0 + 0x1p-16);
+        float mid = (float)(0.5 * (lo + hi)), half = (float)(0.5 * (hi - lo) * (1.0 + 0x1p-10));
+        if (!(lm > 0.0) || !(half > 0.0f) || !(half < INFINITY)) {
+            mid = 0.0f;
+            half = INFINITY;   // no usable interval: every chunk takes the exact clamps
+        }
+        P->tmid = mid;
+        P->thalf = half;
     }
     (void)qe;
 }
@@ -349,6 +366,7 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
     const QScale qsc = qscale(P->qshift);
     const uint64_t Qn = P->Qn;
     const float lmax = P->light_max;
+    const float tmid = P->tmid, thalf = P->thalf;
     uint64_t a, b;
     sub_range(s, NS, C, n, a, b);
     uint64_t run_l = seg_loff[s];       // global rank of the next light
@@ -430,15 +448,36 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
         const int kb = (int)tl - s0;
         const uint64_t Qn1 = Qn + 1;
         uint64_t acc = 0, snap_l = 0, snap_h = 0, snap_b = 0;
+        // A full chunk with no weight near the light threshold needs no
+        // clamp (its lights have q <= Qn, its heavies q > Qn): sum q as is.
+        // Otherwise (a partial chunk, or a weight in the threshold
+        // interval) the pass applies the clamps.
+        bool exact = tv < (uint32_t)kChunk;
+        if (!exact) {
+            float dmin = INFINITY;
 #pragma unroll
-        for (int k = 0; k < kPartItems; ++k) {
-            const uint32_t slot = (uint32_t)(s0 + k);
-            if (k == kl) snap_l = acc;
-            if (k == kb) snap_b = acc;
-            const uint64_t q = fixed_q(sm.e[pad16(slot)].w, qsc);
-            const uint64_t v = slot < tl ? min(q, Qn) : (slot >= hstart ? max(q, Qn1) : 0ull);
-            acc += v;
-            if (k == kh) snap_h = acc;    // inclusive of the heavy ckpt slot
+            for (int k = 0; k < kPartItems; ++k) {
+                if (k == kl) snap_l = acc;
+                if (k == kb) snap_b = acc;
+                const float x = sm.e[pad16(s0 + k)].w;
+                dmin = fminf(dmin, fabsf(x - tmid));
+                acc += fixed_q(x, qsc);
+                if (k == kh) snap_h = acc;    // inclusive of the heavy ckpt slot
+            }
+            exact = __any_sync(0xffffffffu, dmin <= thalf);
+        }
+        if (exact) {
+            acc = snap_l = snap_h = snap_b = 0;
+#pragma unroll
+            for (int k = 0; k < kPartItems; ++k) {
+                const uint32_t slot = (uint32_t)(s0 + k);
+                if (k == kl) snap_l = acc;
+                if (k == kb) snap_b = acc;
+                const uint64_t q = fixed_q(sm.e[pad16(slot)].w, qsc);
+                const uint64_t v = slot < tl ? min(q, Qn) : (slot >= hstart ? max(q, Qn1) : 0ull);
+                acc += v;
+                if (k == kh) snap_h = acc;    // inclusive of the heavy ckpt slot
+            }
         }
         uint64_t inc = acc;
 #pragma unroll

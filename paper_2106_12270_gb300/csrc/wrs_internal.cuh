@@ -49,6 +49,9 @@ struct __align__(16) BuildParams {
     uint32_t sections; // s
     uint32_t nseg;     // partition segments
     uint32_t sum_done; // blocks of the total-weight kernel that are done
+    // Every weight whose light/heavy clamp of q is not the identity lies in
+    // [tmid - thalf, tmid + thalf] (a superset, see k_qsum).
+    float tmid, thalf;
 };
 
 // Workspace layout (all offsets 256-byte aligned).

@@ -128,6 +128,47 @@ def test_fixed_point_exact(kind):
         assert ck == want, which
 
 
+def _near_threshold(kind: str, n: int) -> np.ndarray:
+    r = np.random.default_rng(23)
+    if kind == "near":       # every weight within 2^-17 of 1
+        return (1.0 + r.integers(-64, 64, n) * 2.0**-23).astype(np.float32)
+    if kind == "equal":
+        return np.full(n, 0.37, np.float32)
+    w = r.exponential(1.0, n).astype(np.float32)   # Exp(1) with 1% at the float mean
+    w[r.random(n) < 0.01] = np.float32(w.astype(np.float64).mean())
+    return w
+
+
+@pytest.mark.parametrize("kind", ["near", "equal", "exp_at_mean"])
+def test_fixed_point_exact_near_threshold(kind):
+    """Weights at or next to the light threshold: the partition's per-chunk
+    test sends these chunks through the clamped pass; its checkpoints must
+    still be the exact clamped sums."""
+    n = 20011
+    w = _near_threshold(kind, n)
+    b = Built(w)
+    S = b.info["scale"]
+    q = fixed_point_q(w, S)
+    Q = sum(q)
+    assert b.info["Q"] == Q
+    Qn = Q // n
+    l, h = oracle.classify(w, oracle.exact_sum(w) / n)
+    assert (b.info["nl"], b.info["nh"]) == (len(l), len(h))
+    li, _, hi, _ = b.lists()
+    for which, lst, clamp in (("ckl", li, lambda v: min(v, Qn)),
+                              ("ckh", hi, lambda v: max(v, Qn + 1))):
+        ck = b.checkpoints(which)
+        acc, want = 0, []
+        for a, idx in enumerate(lst):
+            if a % 32 == 0:
+                want.append(acc)
+            acc += clamp(q[int(idx)])
+        if len(lst) % 32 == 0:
+            want.append(acc)
+        assert ck == want, which
+    check_table(b)
+
+
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("section", [256, 1024, 4096])
 @pytest.mark.parametrize("method", [wrs.SPLIT_PARY, wrs.SPLIT_BINARY])
