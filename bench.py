@@ -498,6 +498,7 @@ def run_batched(args, world, rank):
         sms.append(ev[1].elapsed_time(ev[2]))
     summ = bb.summaries()
     ok = int((summ["status"] == wrs.OK).sum())
+    mass_err = _batched_mass_error(rows, w, off, ntab)
     build_ms = statistics.mean(bms)
     sample_ms = statistics.mean(sms)
 
@@ -545,7 +546,31 @@ def run_batched(args, world, rank):
                        "candidates": [{k: c[k] for k in ("threads", "chunk", "ms")}
                                       for c in cand]},
             "graph_step_ms": graph_ms,
-            "graph_items_per_s": total / (graph_ms / 1e3)}
+            "graph_items_per_s": total / (graph_ms / 1e3),
+            "max_mass_error": mass_err, "mass_error_bound": 1e-5}
+
+
+def _batched_mass_error(rows, w, off, ntab):
+    """max over every item of every table of |mass_i - N_t w_i/W_t| /
+    max(1, N_t w_i/W_t), in FP64 on the device (torch ops: a measurement of
+    the built tables, not part of the build)."""
+    import torch
+    dev = rows.device
+    sizes = off[1:] - off[:-1]
+    tid = torch.repeat_interleave(torch.arange(ntab, device=dev), sizes)
+    raw = rows.view(torch.int32).view(-1, 2)
+    prob = raw[:, 0].contiguous().view(torch.float32).double()
+    alias = raw[:, 1].long() + off[:-1][tid]
+    mass = prob.clone()
+    mass.index_add_(0, alias, 1.0 - prob)
+    del alias
+    wd = w.double()
+    Wt = torch.zeros(ntab, dtype=torch.float64, device=dev).index_add_(0, tid, wd)
+    Wi = Wt[tid]
+    expect = wd * sizes[tid].double() / Wi.clamp(min=1e-300)
+    err = (mass - expect).abs() / expect.clamp(min=1.0)
+    err = torch.where(Wi > 0, err, torch.zeros_like(err))
+    return float(err.max())
 
 
 def _time_ms(fn, reps=3):

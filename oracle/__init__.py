@@ -16,6 +16,8 @@ function cites the part of the paper (arXiv 2106.12270) it follows:
 * ``split_pary``      PSA splits by partial p-ary search (Sec. 4.1, Alg. 1).
 * ``pary_search``     Algorithm 1 on a sorted list (Sec. 4.1).
 * ``psa``             PSA split + sweep-pack (Sec. 2.2, Sec. 4.2).
+* ``psa_prec``        the same PSA with its prefix arithmetic rounded to FP64,
+                      paired FP32 or plain FP32 (precision study).
 * ``mass``            reconstructed mass per item (Sec. 2.2).
 * ``philox``          Philox-4x32-10 (Salmon et al., SC'11).
 * ``sample_naive``    Walker sampling, integer form (Sec. 2.2, Sec. 5).
@@ -76,6 +78,7 @@ def _load():
                 "orc_split_pary": [P, U64, P, U64, D, P, U64, U32, P, P, P],
                 "orc_pary_search": [P, U64, P, U64, U32, P],
                 "orc_psa": [P, U64, U64, P, P, P, P, P, P, P, U32],
+                "orc_psa_prec": [P, U64, U64, ctypes.c_int, P, P],
                 "orc_mass": [P, P, U64, P],
                 "orc_sample_naive": [P, P, U64, U64, U64, U64, U32, U32, P],
                 "orc_sample_sectioned": [P, P, U64, U64, P, U64, U32, P],
@@ -205,6 +208,22 @@ def psa(w, section: int, pary_p: int = 0):
                            pary_p), "psa")
     return dict(prob=prob[:n], alias=alias[:n], nl=int(nl[0]), nh=int(nh[0]),
                 split_i=si, split_j=sj, spill=sp)
+
+
+PREC_FP64, PREC_FP32_PAIR, PREC_FP32 = 0, 1, 2
+
+
+def psa_prec(w, section: int, prec: int):
+    """PSA (binary split search) with the prefix sums, split comparisons and
+    sweep residual rounded to FP64 (prec 0), a pair of FP32 values (1, what
+    compensated FP32 keeps) or plain FP32 (2).  Returns (prob f64, alias)."""
+    w = _f32(w)
+    n = w.size
+    prob = np.zeros(max(n, 1), np.float64)
+    alias = np.zeros(max(n, 1), np.uint32)
+    _check(_load().orc_psa_prec(_ptr(w), n, section, prec, _ptr(prob),
+                                _ptr(alias)), "psa_prec")
+    return prob[:n], alias[:n]
 
 
 def mass(prob, alias) -> np.ndarray:

@@ -27,6 +27,8 @@
  *   orc_pary_search       Algorithm 1 on a plain sorted list (Sec. 4.1).
  *   orc_psa               PSA: split + sweep-pack of each section (Sec. 2.2,
  *                         Sec. 4.2).
+ *   orc_psa_prec          the same PSA with its prefix arithmetic rounded to
+ *                         FP64, paired FP32 or FP32 (precision study).
  *   orc_mass              reconstructed mass of each item from a table
  *                         (Sec. 2.2: every row is one bucket of W/N).
  *   orc_philox4x32_10     Philox-4x32-10 counter-based generator (Salmon,
@@ -540,6 +542,116 @@ int orc_psa(const float *w, uint64_t n, uint64_t S, double *prob,
     rc = ORC_OK;
 out:
     free(l); free(h); free(sl); free(sh); free(k); free(si); free(sj); free(sp);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* PSA in a chosen working precision (precision study).                      */
+/*                                                                           */
+/* The paper keeps the prefix sums, the split comparisons and the sweep's     */
+/* residual in FP64 (Sec. 2.2, Sec. 6).  This copy of the PSA above (binary   */
+/* split search) rounds every one of those quantities to a working precision */
+/* after each operation:                                                      */
+/*   prec 0: FP64 (no extra rounding; equal to orc_psa bit for bit),          */
+/*   prec 1: a pair of FP32 values hi + lo (about 48 significant bits: what  */
+/*           compensated FP32 summation keeps),                               */
+/*   prec 2: plain FP32.                                                      */
+/* The total W, the average and the light/heavy classification are exact as  */
+/* in orc_psa, so only the prefix arithmetic differs.                         */
+/* ------------------------------------------------------------------------ */
+
+static double wp(int prec, double x)
+{
+    if (prec == 1) {
+        float hi = (float)x;
+        float lo = (float)(x - (double)hi);
+        return (double)hi + (double)lo;
+    }
+    if (prec == 2)
+        return (double)(float)x;
+    return x;
+}
+
+int orc_psa_prec(const float *w, uint64_t n, uint64_t S, int prec,
+                 double *prob, uint32_t *alias)
+{
+    double W, avg0;
+    int rc = total_and_avg(w, n, &W, &avg0);
+    if (rc)
+        return rc;
+    if (S == 0 || prec < 0 || prec > 2)
+        return ORC_EINVAL;
+    const double avg = wp(prec, avg0);
+    uint32_t *l = malloc(n * sizeof *l), *h = malloc(n * sizeof *h);
+    double *sl = malloc((n + 1) * sizeof *sl), *sh = malloc((n + 1) * sizeof *sh);
+    uint64_t nsec = (n + S - 1) / S;
+    uint64_t *si = malloc((nsec + 1) * sizeof *si), *sj = malloc((nsec + 1) * sizeof *sj);
+    double *sp = malloc((nsec + 1) * sizeof *sp);
+    if (!l || !h || !sl || !sh || !si || !sj || !sp) {
+        rc = ORC_ENOMEM;
+        goto out;
+    }
+    uint64_t nl, nh;
+    orc_classify(w, n, avg0, l, h, &nl, &nh);
+    sl[0] = sh[0] = 0.0;
+    for (uint64_t a = 0; a < nl; ++a)
+        sl[a + 1] = wp(prec, sl[a] + (double)w[l[a]]);
+    for (uint64_t b = 0; b < nh; ++b)
+        sh[b + 1] = wp(prec, sh[b] + (double)w[h[b]]);
+    /* splits: the smallest i with f(i) = sl(i) + sh(k-i) - k avg <= 0 in the
+     * valid range, each term rounded to the working precision */
+    for (uint64_t t = 0; t <= nsec; ++t) {
+        uint64_t kk = t * S < n ? t * S : n;
+        uint64_t a = kk > nh ? kk - nh : 0, b = kk < nl ? kk : nl;
+        double kavg = wp(prec, (double)kk * avg);
+        while (a < b) {
+            uint64_t m = a + (b - a) / 2;
+            if (wp(prec, wp(prec, sl[m] + sh[kk - m]) - kavg) <= 0.0)
+                b = m;
+            else
+                a = m + 1;
+        }
+        si[t] = a;
+        sj[t] = kk - a;
+        sp[t] = kk - a < nh ? wp(prec, wp(prec, sl[a] + sh[kk - a + 1]) - kavg) : 0.0;
+    }
+    for (uint64_t t = 0; t < nsec; ++t) {
+        uint64_t i = si[t], j = sj[t];
+        uint64_t i_end = si[t + 1], j_end = sj[t + 1];
+        double r = sp[t];
+        while (i < i_end || j < j_end) {
+            int light_left = i < i_end;
+            int heavy_left = j < j_end;
+            if (heavy_left && (r <= avg || !light_left)) {
+                uint32_t g = h[j];
+                double keep = wp(prec, r / avg);
+                prob[g] = keep < 0.0 ? 0.0 : (keep > 1.0 ? 1.0 : keep);
+                if (j + 1 < nh) {
+                    alias[g] = h[j + 1];
+                    r = wp(prec, wp(prec, r + (double)w[h[j + 1]]) - avg);
+                } else {
+                    prob[g] = 1.0;
+                    alias[g] = g;
+                    r = 0.0;
+                }
+                ++j;
+            } else {
+                uint32_t lo = l[i];
+                if (j < nh) {
+                    prob[lo] = wp(prec, (double)w[lo] / avg);
+                    alias[lo] = h[j];
+                    r = wp(prec, r - wp(prec, avg - (double)w[lo]));
+                } else {
+                    prob[lo] = 1.0;
+                    alias[lo] = lo;
+                }
+                ++i;
+            }
+        }
+    }
+    rc = ORC_OK;
+out:
+    free(l); free(h); free(sl); free(sh); free(si); free(sj); free(sp);
     return rc;
 }
 

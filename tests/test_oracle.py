@@ -380,3 +380,27 @@ def test_sectioned_sampler_stays_in_sections_and_fits():
         assert np.all(rows_ok | alias_ok)
     # counts proportional to section sizes make the whole stream exact in law
     assert _gof(out, w.size, w.astype(np.float64) / w.astype(np.float64).sum()) > 1e-3
+
+
+# --------------------------------------------------------------------------
+# Precision study: the PSA's prefix arithmetic in FP64, paired FP32
+# (compensated summation) and plain FP32
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", ["uniform", "zipf", "exponential"])
+def test_precision_study_prefix_arithmetic(kind):
+    """FP64 working precision reproduces orc_psa bit for bit; FP64 and paired
+    FP32 (about 48 bits) meet the 1e-5 mass bound for an FP32-stored table;
+    plain FP32 prefix sums miss it by orders of magnitude at 2e6 items."""
+    n = 2_000_000
+    w = inputs.by_name(kind, n, 11)
+    W = oracle.exact_sum(w)
+    ref = oracle.psa(w, 1024)
+    errs = []
+    for prec in (oracle.PREC_FP64, oracle.PREC_FP32_PAIR, oracle.PREC_FP32):
+        prob, alias = oracle.psa_prec(w, 1024, prec)
+        if prec == oracle.PREC_FP64:
+            assert np.array_equal(prob, ref["prob"]) and np.array_equal(alias, ref["alias"])
+        p32 = prob.astype(np.float32).astype(np.float64)
+        errs.append(oracle.mass_error(p32, alias, w, W))
+    assert errs[0] <= 1e-6 and errs[1] <= 1e-5 and errs[2] > 1e-3, errs
