@@ -352,7 +352,7 @@ def run_gpu(args):
     sec = {}
     for mode, name, rows_per in () if args.build_only else ((wrs.SAMPLE_CACHED, "cached", 8192),
                                  (wrs.SAMPLE_LIMITED, "limited", 8192),
-                                 (wrs.SAMPLE_SMEM, "smem", 16384)):
+                                 (wrs.SAMPLE_SMEM, "smem", 4096)):
         nsec = wrs.sample_sections(n, rows_per)
         cnt_t = torch.empty(nsec, dtype=torch.int64, device="cuda")
         off_t = torch.empty(nsec, dtype=torch.int64, device="cuda")
@@ -368,6 +368,26 @@ def run_gpu(args):
         ms = a.elapsed_time(b) / args.steps
         sec[name] = {"ms": ms, "samples_per_s": world * count / (ms / 1e3),
                      "section_rows": rows_per}
+
+    # Philox-rate probe: the sectioned samplers' generator calls and 4-byte
+    # stores alone (same draw count); their arithmetic roofline
+    if sec:
+        wrs.diag_philox(count, 7, out)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            wrs.diag_philox(count, 7, out)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ph_ms = a.elapsed_time(b) / args.steps
+        for v in sec.values():
+            v["frac_of_philox_probe"] = ph_ms / v["ms"]
+        sec["philox_probe"] = {"ms": ph_ms, "samples_per_s": world * count / (ph_ms / 1e3),
+                               "bound": "alu",
+                               "what": "the same Philox-4x32-10 calls and 4-byte stores, "
+                                       "no rows (wrs_diag_philox)"}
 
     # random-gather probe: the naive sampler's access pattern alone (same
     # table size, same number of draws), best of the three load paths
@@ -600,7 +620,8 @@ def run_sampler_heatmap(args):
     sizes = [1 << k for k in (16, 20, 24, 27)]
     counts = [1 << k for k in (16, 20, 24, 28)]
     modes = [("naive", wrs.SAMPLE_NAIVE, 0), ("cached", wrs.SAMPLE_CACHED, 8192),
-             ("limited", wrs.SAMPLE_LIMITED, 8192), ("smem", wrs.SAMPLE_SMEM, 16384)]
+             ("limited", wrs.SAMPLE_LIMITED, 8192), ("smem", wrs.SAMPLE_SMEM, 4096),
+             ("smem16k", wrs.SAMPLE_SMEM, 16384)]
     out = torch.empty(max(counts), dtype=torch.int32, device="cuda")
     cells = []
     for n in sizes:

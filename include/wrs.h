@@ -220,7 +220,8 @@ enum wrs_stream_tag {
     WRS_TAG_NAIVE = 0,     /* plain sampling: stream_hi of wrs_sample_rows */
     WRS_TAG_SECTION = 1,   /* sectioned sampling: (section, WRS_TAG_SECTION) */
     WRS_TAG_COUNTS = 2,    /* sectioned counts tree nodes */
-    WRS_TAG_BATCH = 3      /* batched sampling: (table, WRS_TAG_BATCH) */
+    WRS_TAG_BATCH = 3,     /* batched sampling: (table, WRS_TAG_BATCH) */
+    WRS_TAG_DIAG = 4       /* the Philox-rate probe (wrs_diag_philox) */
 };
 
 /* a6: naive sampling (Sec. 5 "baseline"): samples first .. first+count-1 of
@@ -269,9 +270,13 @@ int wrs_sample_sectioned_rows(const wrs_row *d_rows, uint64_t n, uint64_t count,
 /* Sampling method selection (the paper compares its samplers over table
  * size and sample count, Sec. 6): the mode and section size wrs_sample_auto
  * uses for n rows and count samples.  The rule comes from the measured
- * heat map of all modes on GB300 (bench --sampler-heatmap): cached
- * sectioned sampling (8192 rows per section) for tables of at least 2^23
- * rows and at least 2^23 draws, naive sampling otherwise. */
+ * heat map of all modes on GB300 (bench --sampler-heatmap):
+ *   - shared-memory sectioned sampling, 4096 rows per section, for tables of
+ *     at least 2^23 rows with at least 2^23 draws and 8 draws per row, and
+ *     for tables of at least 2^20 rows with at least 128 draws per row;
+ *   - cached sectioned sampling, 8192 rows per section, for the other tables
+ *     of at least 2^23 rows with at least 2^23 draws;
+ *   - naive sampling otherwise. */
 int wrs_sample_auto_choice(uint64_t n, uint64_t count, uint32_t *mode, uint32_t *section_rows);
 
 /* Device workspace of wrs_sample_auto: the per-section counts and offsets of
@@ -433,6 +438,17 @@ int wrs_server_destroy(wrs_server *s);
  * 2 = streaming (ld.global.cs).  Contents of d_out are meaningless. */
 int wrs_diag_random_gather(const wrs_row *d_rows, uint64_t nrows, uint64_t count,
                            uint64_t seed, int flavor, uint32_t *d_out, void *stream);
+
+/* Philox-rate probe (measures the hardware; no counterpart in the paper):
+ * ceil(count/2) Philox-4x32-10 calls, call c on counter
+ * (c_lo, c_hi, 0, WRS_TAG_DIAG) under key (seed_lo, seed_hi), writing
+ * d_out[2c] = x0 ^ x1 and d_out[2c+1] = x2 ^ x3 (d_out holds count
+ * uint32; an 8-byte aligned device pointer).  The same calls and output bytes
+ * as a sectioned sampler without the rows: the bench uses its rate as the
+ * arithmetic roofline of the cached sectioned sampler.  Errors: WRS_EINVAL
+ * for a null or not 8-byte aligned d_out with count > 0, WRS_ECUDA for a
+ * failed launch. */
+int wrs_diag_philox(uint64_t count, uint64_t seed, uint32_t *d_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -29,7 +29,7 @@ __all__ = [
 OK, EINVAL, EZEROSUM, ENONFINITE, ENOMEM, ETIMEOUT, ECUDA, EBUSY, ENOTFOUND = range(9)
 SPLIT_PARY, SPLIT_BINARY = 0, 1
 SAMPLE_NAIVE, SAMPLE_CACHED, SAMPLE_LIMITED, SAMPLE_SMEM = 0, 1, 2, 3
-TAG_NAIVE, TAG_SECTION, TAG_COUNTS, TAG_BATCH = 0, 1, 2, 3
+TAG_NAIVE, TAG_SECTION, TAG_COUNTS, TAG_BATCH, TAG_DIAG = 0, 1, 2, 3, 4
 ROW_BYTES = 8
 
 _lock = threading.Lock()
@@ -107,6 +107,7 @@ def lib():
                 "wrs_step_info": (I, [U64, P, U64, CP, P, P]),
                 "wrs_sample_rows": (I, [P, U64, U64, U64, U64, U32, U32, P, P]),
                 "wrs_diag_random_gather": (I, [P, U64, U64, U64, I, P, P]),
+                "wrs_diag_philox": (I, [U64, U64, P, P]),
                 "wrs_sample_sections": (I, [U64, U32, ctypes.POINTER(U64)]),
                 "wrs_sample_auto_choice": (I, [U64, U64, ctypes.POINTER(U32),
                                                ctypes.POINTER(U32)]),
@@ -272,12 +273,18 @@ def sample_sectioned_rows(rows, n: int, count: int, seed: int, mode: int, sectio
 MODE_NAMES = {0: "naive", 1: "cached", 2: "limited", 3: "smem"}
 
 
-def sample_auto_choice(n: int, count: int) -> str:
-    """The sampling mode wrs_sample_auto picks for n rows and count draws."""
+def sample_auto_plan(n: int, count: int):
+    """(mode code, rows per section) that wrs_sample_auto uses for n rows and
+    count draws (rows per section is 0 for naive sampling)."""
     mode, rows = ctypes.c_uint32(), ctypes.c_uint32()
     _check(lib().wrs_sample_auto_choice(n, count, ctypes.byref(mode), ctypes.byref(rows)),
            "wrs_sample_auto_choice")
-    return MODE_NAMES[mode.value]
+    return mode.value, rows.value
+
+
+def sample_auto_choice(n: int, count: int) -> str:
+    """The sampling mode wrs_sample_auto picks for n rows and count draws."""
+    return MODE_NAMES[sample_auto_plan(n, count)[0]]
 
 
 def sample_auto(rows, n: int, count: int, seed: int, out, stream=None) -> str:
@@ -438,6 +445,11 @@ def diag_random_gather(rows, nrows: int, count: int, seed: int, flavor: int, out
     """Enqueue the random-gather probe (measurement support, not the method)."""
     _check(lib().wrs_diag_random_gather(_ptr(rows), nrows, count, seed, flavor, _ptr(out),
                                         _stream(stream)), "wrs_diag_random_gather")
+
+
+def diag_philox(count: int, seed: int, out, stream=None):
+    """Enqueue the Philox-rate probe (measurement support, not the method)."""
+    _check(lib().wrs_diag_philox(count, seed, _ptr(out), _stream(stream)), "wrs_diag_philox")
 
 
 def parse_info(info_tensor) -> dict:

@@ -28,6 +28,7 @@ cudaError_t launch_sample_batched(const wrs_row *, const uint64_t *, uint32_t, c
                                   uint64_t, uint32_t *, cudaStream_t);
 cudaError_t launch_random_gather(const void *, uint64_t, uint64_t, uint64_t, int, uint32_t *,
                                  cudaStream_t);
+cudaError_t launch_philox_rate(uint64_t, uint64_t, uint32_t *, cudaStream_t);
 
 thread_local int g_last_cuda = 0;
 
@@ -263,13 +264,25 @@ int wrs_sample_sectioned_rows(const wrs_row *d_rows, uint64_t n, uint64_t count,
 int wrs_sample_auto_choice(uint64_t n, uint64_t count, uint32_t *mode, uint32_t *section_rows) {
     if (!mode || !section_rows || n == 0) return WRS_EINVAL;
     // measured on GB300 (sampler heat map over 2^16..2^27 rows and 2^16..2^28
-    // draws): naive sampling wins while the table fits in L2; above about
-    // half of L2 (2^23 rows = 64 MB) a naive draw costs 9-21 ps, a cached
-    // sectioned draw 3.4 ps plus 0.05-0.15 ms for the count tree, so the
-    // sectioned mode pays from about 2^23 draws on
-    const bool sectioned = n >= (1ull << 23) && count >= (1ull << 23);
-    *mode = sectioned ? WRS_SAMPLE_CACHED : WRS_SAMPLE_NAIVE;
-    *section_rows = sectioned ? 8192u : 0u;
+    // draws): naive sampling wins while the table fits in L2 and the draws
+    // per row are few.  From about half of L2 (2^23 rows = 64 MB) and 2^23
+    // draws a sectioned mode pays: the shared-memory mode (4096-row
+    // sections, each row's threshold converted once) from about 8 draws per
+    // row, the cached mode (8192-row sections, rows read through L1) below.
+    // Tables of 2^20+ rows with 128+ draws per row also take the
+    // shared-memory mode; smaller tables have too few sections to fill the GPU.
+    const bool big = n >= (1ull << 23) && count >= (1ull << 23);
+    const bool dense = n >= (1ull << 20) && count / n >= 128;
+    if ((big && count / n >= 8) || dense) {
+        *mode = WRS_SAMPLE_SMEM;
+        *section_rows = 4096u;
+    } else if (big) {
+        *mode = WRS_SAMPLE_CACHED;
+        *section_rows = 8192u;
+    } else {
+        *mode = WRS_SAMPLE_NAIVE;
+        *section_rows = 0u;
+    }
     return WRS_OK;
 }
 
@@ -464,6 +477,11 @@ int wrs_diag_random_gather(const wrs_row *d_rows, uint64_t nrows, uint64_t count
     if (flavor < 0 || flavor > 2) return WRS_EINVAL;
     return cuda_status(
         launch_random_gather(d_rows, nrows, count, seed, flavor, d_out, (cudaStream_t)stream));
+}
+
+int wrs_diag_philox(uint64_t count, uint64_t seed, uint32_t *d_out, void *stream) {
+    if (count && (!d_out || ((uintptr_t)d_out & 7u))) return WRS_EINVAL;
+    return cuda_status(launch_philox_rate(count, seed, d_out, (cudaStream_t)stream));
 }
 
 }  // extern "C"

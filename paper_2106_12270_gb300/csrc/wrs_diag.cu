@@ -1,4 +1,4 @@
-// wrs_diag.cu - a measurement kernel for the sampler's roofline.
+// wrs_diag.cu - measurement kernels for the samplers' rooflines.
 //
 // The naive sampler (Sec. 5 "baseline") is bound by random 8-byte row
 // gathers from HBM.  This kernel performs the same access pattern without
@@ -7,6 +7,11 @@
 // against the random-gather rate this GPU actually sustains, not only
 // against the streaming copy bandwidth.  The row index comes from a cheap
 // integer hash, not Philox, so that the kernel is bound by memory alone.
+//
+// The sectioned samplers read their rows from L2 and are bound by Philox
+// arithmetic instead.  The second kernel makes the same Philox-4x32-10 calls
+// (two per thread and step, two 32-bit outputs per call) and writes the same
+// 4 bytes per sample, without the rows.
 #include "wrs_internal.cuh"
 
 namespace wrs {
@@ -50,7 +55,41 @@ k_random_gather(const uint2 *__restrict__ rows, uint64_t nrows, uint64_t count, 
     }
 }
 
+// Philox rate: call c (counter (c_lo, c_hi, 0, WRS_TAG_DIAG), key (k0, k1))
+// writes out[2c] = x.x ^ x.y and out[2c+1] = x.z ^ x.w.
+__global__ void __launch_bounds__(256)
+k_philox_rate(uint64_t count, uint32_t k0, uint32_t k1, uint32_t *__restrict__ out) {
+    const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t calls = (count + 1) >> 1;
+    auto put = [&](uint64_t c, uint4 x) {
+        const uint64_t q = 2 * c;
+        const uint32_t a = x.x ^ x.y, b = x.z ^ x.w;
+        if (q + 1 < count) *reinterpret_cast<uint2 *>(out + q) = make_uint2(a, b);
+        else out[q] = a;
+    };
+    uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; c + T < calls; c += 2 * T) {
+        const uint64_t c2 = c + T;
+        const uint4 x1 =
+            philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), 0u, WRS_TAG_DIAG), k0, k1);
+        const uint4 x2 =
+            philox4x32_10(make_uint4((uint32_t)c2, (uint32_t)(c2 >> 32), 0u, WRS_TAG_DIAG), k0, k1);
+        put(c, x1);
+        put(c2, x2);
+    }
+    if (c < calls)
+        put(c, philox4x32_10(make_uint4((uint32_t)c, (uint32_t)(c >> 32), 0u, WRS_TAG_DIAG), k0, k1));
+}
+
 extern int num_sms();
+
+cudaError_t launch_philox_rate(uint64_t count, uint64_t seed, uint32_t *out, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    k_philox_rate<<<(unsigned)num_sms() * 8, 256, 0, st>>>(count, (uint32_t)seed,
+                                                           (uint32_t)(seed >> 32), out);
+    return cudaGetLastError();
+}
+
 
 cudaError_t launch_random_gather(const void *rows, uint64_t nrows, uint64_t count, uint64_t seed,
                                  int flavor, uint32_t *out, cudaStream_t st) {

@@ -253,8 +253,10 @@ __device__ __forceinline__ void walker_split(uint64_t u, uint64_t rows,
 // (power-of-two scaling) and the conversion rounds up, so this is the ceiling.
 __device__ __forceinline__ uint32_t walker_pick(uint32_t row, uint32_t coin,
                                                 uint2 r) {
-    uint64_t tau = __float2ull_ru(__uint_as_float(r.x) * 4294967296.0f);
-    return (uint64_t)coin < tau ? row : r.y;
+    const float t = __uint_as_float(r.x) * 4294967296.0f;
+    // below 2^32 the ceiling fits 32 bits (the largest such float is
+    // 2^32 - 256); prob = 1 keeps the row for every coin
+    return (t >= 4294967296.0f || coin < __float2uint_ru(t)) ? row : r.y;
 }
 
 }  // namespace wrs

@@ -175,9 +175,20 @@ k_sample_sec(const uint2 *__restrict__ rows, uint64_t n, uint64_t nsec,
     const uint64_t R = r1 - r0;
     const uint64_t c = counts[s], o = offsets[s];
     if (kSmem) {
-        for (uint64_t r = threadIdx.x; r < R; r += blockDim.x) srow[r] = __ldg(rows + r0 + r);
+        // each row once: its keep threshold ceil(prob 2^32) as an integer and
+        // its alias; a row with prob 1 keeps itself as the alias, so that
+        // coin < 0xffffffff or not picks the same item
+        for (uint64_t r = threadIdx.x; r < R; r += blockDim.x) {
+            const uint2 v = __ldg(rows + r0 + r);
+            const float t = __uint_as_float(v.x) * 4294967296.0f;
+            srow[r] = t >= 4294967296.0f ? make_uint2(0xffffffffu, (uint32_t)(r0 + r))
+                                         : make_uint2(__float2uint_ru(t), v.y);
+        }
         __syncthreads();
     }
+    auto pick = [&](uint32_t row, uint32_t coin, uint2 v) {
+        return kSmem ? (coin < v.x ? row : v.y) : walker_pick(row, coin, v);
+    };
     const uint64_t calls = (c + 1) >> 1;
     // two independent Philox calls per thread and step (interleaved chains)
     auto one = [&](uint64_t cc, uint4 x) {
@@ -187,8 +198,8 @@ k_sample_sec(const uint2 *__restrict__ rows, uint64_t n, uint64_t nsec,
         walker_split(((uint64_t)x.z << 32) | x.w, R, rb, cb);
         uint2 va = kSmem ? srow[ra] : __ldg(rows + r0 + ra);
         uint2 vb = kSmem ? srow[rb] : __ldg(rows + r0 + rb);
-        uint32_t sa = walker_pick((uint32_t)(r0 + ra), ca, va);
-        uint32_t sb = walker_pick((uint32_t)(r0 + rb), cb, vb);
+        uint32_t sa = pick((uint32_t)(r0 + ra), ca, va);
+        uint32_t sb = pick((uint32_t)(r0 + rb), cb, vb);
         uint64_t q = o + 2 * cc;
         if (2 * cc + 1 < c) {
             if (vec_ok && (q & 1) == 0) *reinterpret_cast<uint2 *>(out + q) = make_uint2(sa, sb);

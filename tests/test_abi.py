@@ -60,6 +60,9 @@ def test_host_argument_checks(lib):
     assert lib.wrs_build_rows(None, 10, None, None, 0, None, None, None) == wrs.EINVAL
     assert lib.wrs_sample_rows(None, 10, 0, 5, 1, 0, 0, None, None) == wrs.EINVAL
     assert lib.wrs_sample_rows(None, 0, 0, 5, 1, 0, 0, None, None) == wrs.EINVAL
+    # the Philox probe needs an 8-byte aligned output (checked on the host)
+    assert lib.wrs_diag_philox(4, 1, ctypes.c_void_p(4), None) == wrs.EINVAL
+    assert lib.wrs_diag_philox(4, 1, None, None) == wrs.EINVAL
     assert lib.wrs_abi_version() >= 1
     assert lib.wrs_strerror(wrs.EZEROSUM) == b"all weights are zero"
 

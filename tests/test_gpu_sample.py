@@ -85,14 +85,19 @@ def test_naive_small_tables():
 
 
 def test_auto_choice_rule():
-    assert wrs.sample_auto_choice(1000, 10**9) == "naive"          # table in L2
+    assert wrs.sample_auto_choice(1000, 10**9) == "naive"          # tiny table in L2
     assert wrs.sample_auto_choice(1 << 27, 1000) == "naive"        # few draws
-    assert wrs.sample_auto_choice(1 << 27, 1 << 28) == "cached"    # many draws, large table
+    assert wrs.sample_auto_choice(1 << 27, 1 << 28) == "cached"    # 2 draws per row
     assert wrs.sample_auto_choice(1 << 27, 1 << 24) == "cached"
     assert wrs.sample_auto_choice(1 << 24, 1 << 20) == "naive"
+    assert wrs.sample_auto_choice(1 << 24, 1 << 28) == "smem"      # 16 draws per row
+    assert wrs.sample_auto_choice(10**8, 10**9) == "smem"
+    assert wrs.sample_auto_choice(1 << 20, 1 << 28) == "smem"      # 256 draws per row
+    assert wrs.sample_auto_choice(1 << 20, 1 << 24) == "naive"
 
 
-@pytest.mark.parametrize("n,count", [(100_003, 1_000_001), (1 << 23, 9_000_001)])
+@pytest.mark.parametrize("n,count", [(100_003, 1_000_001), (1 << 23, 9_000_001),
+                                     (1 << 23, 70_000_001)])
 def test_auto_draws_exactly_what_the_chosen_mode_draws(n, count):
     w = inputs.by_name("zipf", n, 11)
     b = Built(w)
@@ -101,12 +106,31 @@ def test_auto_draws_exactly_what_the_chosen_mode_draws(n, count):
     torch.cuda.synchronize()
     assert mode == wrs.sample_auto_choice(n, count)
     want = torch.empty_like(out)
+    code, rows_per = wrs.sample_auto_plan(n, count)
     if mode == "naive":
         wrs.sample_rows(b.rows_t, n, 0, count, 42, want)
     else:
-        nsec = wrs.sample_sections(n, 8192)
+        nsec = wrs.sample_sections(n, rows_per)
         cnt = torch.empty(nsec, dtype=torch.int64, device="cuda")
         off = torch.empty(nsec, dtype=torch.int64, device="cuda")
-        wrs.sample_sectioned_rows(b.rows_t, n, count, 42, wrs.SAMPLE_CACHED, 8192, cnt, off, want)
+        wrs.sample_sectioned_rows(b.rows_t, n, count, 42, code, rows_per, cnt, off, want)
     torch.cuda.synchronize()
     assert torch.equal(out, want)
+
+
+@pytest.mark.parametrize("count, seed", [(1001, 0x0123456789ABCDEF), (4096, 2), (1, 7)])
+def test_philox_probe_matches_oracle(count, seed):
+    """The Philox-rate probe makes exactly the stated calls: out[2c] and
+    out[2c+1] fold the four words of call c on counter (c, 0, 0, TAG_DIAG)."""
+    out = torch.zeros(count + 1, dtype=torch.int32, device="cuda")
+    wrs.diag_philox(count, seed, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    want = np.zeros(count + 1, np.uint32)
+    for c in range((count + 1) // 2):
+        x = oracle.philox([c & 0xFFFFFFFF, c >> 32, 0, wrs.TAG_DIAG], key)
+        want[2 * c] = x[0] ^ x[1]
+        if 2 * c + 1 < count:
+            want[2 * c + 1] = x[2] ^ x[3]
+    assert np.array_equal(got, want)   # including the untouched slot after count
