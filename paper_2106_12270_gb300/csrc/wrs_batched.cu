@@ -7,11 +7,13 @@
 // counter (largest tables first) and runs the whole PSA pipeline on it --
 // exact total, fixed-point total Q, stable partition into l and h, and a
 // sweep-pack done chunk by chunk (Sec. 4.2 "chunked loading", Algorithm 2):
-// the CTA loads the next lights and heavies of the sweep into shared memory,
-// merges C buckets cooperatively (merge path over the scaled deficit and
-// excess prefix sums), and carries the Vose state (i, j, D', E') to the next
-// chunk.  Because one CTA owns a table, the carried state replaces the split
-// search.  Rows use table-local item indices.
+// the CTA loads a window of the next lights and heavies of the sweep (up to
+// CH of each) into shared memory, forms the 64-bit sweep keys of the window
+// from the exact prefix sums, closes buckets cooperatively (merge path) until
+// the window runs out of lights or of heavies, and carries the exact Vose
+// state (i, j, D', E') to the next chunk.  Because one CTA owns a table, the
+// carried state replaces the split search.  Rows use table-local item
+// indices.
 //
 // a9, batched sampling: one CTA per table draws that table's samples with
 // Walker's rule, counters keyed by the table id.
@@ -32,7 +34,7 @@ constexpr uint64_t kBatchMaxItems = 1ull << 24;
 template <int BT, int CH>
 struct BatchShared {
     static constexpr int kSlots = 2 * CH + 2;             // lights + heavies + next heavy
-    static constexpr int kPSlots = kSlots + kSlots / 8 + 2; // padded prefix slots
+    static constexpr int kKSlots = kSlots + kSlots / 16 + 2; // padded (one slot in 16)
     union {
         uint64_t bins[kBands][BT];
         struct {
@@ -40,9 +42,8 @@ struct BatchShared {
             Entry e[kBTile + kBTile / 16];
         } part;
         struct {
-            u128 P[kPSlots];
-            uint32_t item[kSlots];
-            float w[kSlots + kSlots / 32 + 1];
+            int64_t K[kKSlots];   // keys: slot x = A(x), slot L+1+y = B(y)
+            uint2 E[kKSlots];     // entries: lights, heavies, the next heavy
         } pack;
     } u;
     u128 band[kBands];
@@ -59,10 +60,12 @@ struct BatchShared {
     // pack state carried across chunks
     uint64_t i, j;
     u128 D, E;
-    uint32_t xk;
+    u128 wredL[BT / 32];    // light part of each warp's values (P(L))
+    u128 Dn, Pe;            // D'(i + xk) and P(L + yk) of the chunk's end
+    uint32_t Kc, xk, yk;    // buckets the chunk closes; lights and heavies among them
 };
 
-__device__ __forceinline__ int pp8b(int e) { return e + (e >> 3); }
+__device__ __forceinline__ uint32_t pk16b(uint32_t e) { return e + (e >> 4); }
 
 // At most 64 registers: four 256-thread CTAs (or two of 512) per SM.
 template <int BT, int CH>
@@ -246,7 +249,11 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
             }
         }
 
-        // ---- a5: chunked sweep-pack
+        // ---- a5: chunked sweep-pack.  A chunk loads up to CH lights and CH
+        // heavies (and the heavy after them), forms the 64-bit sweep keys of
+        // that window (as the single-table pack: floors of the exact
+        // prefixes at 2^15 units, relative to the chunk's start), and closes
+        // buckets until the window runs out of lights or of heavies.
         if (tid == 0) {
             sm.i = 0; sm.j = 0; sm.D = 0; sm.E = 0;
         }
@@ -254,121 +261,207 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
         const uint32_t N = (uint32_t)n;
         const Entry *lht = lh + base;
         uint2 *rt = row_ptrs ? row_ptrs[t] : rows + base;
-        for (;;) {
+        const float inv_avg = sm.inv_avg;
+        const float invQk = sm.invQ * (float)(1u << kKeyShift);
+        constexpr uint32_t kPer = (2 * CH + BT - 1) / BT;   // window positions per thread
+        int64_t *sK = sm.u.pack.K;
+        uint2 *sE = sm.u.pack.E;
+        // every chunk closes at least one bucket (a window side that does not
+        // end its list holds CH >= 512 entries); the bound only guards that
+        for (uint64_t chunk = 0; chunk <= n; ++chunk) {
             const uint64_t i = sm.i, j = sm.j;
             if (i + j >= n) break;
             const u128 D0 = sm.D, E0 = sm.E;
             const uint32_t L = (uint32_t)min((uint64_t)CH, nl - i);
             const uint32_t H = (uint32_t)min((uint64_t)CH, nh - j);
-            const uint32_t extra = (j + H < nh) ? 1u : 0u;
-            const uint32_t K = (uint32_t)min((uint64_t)CH, n - i - j);
-            for (uint32_t e = tid; e < L + H + extra; e += BT) {
-                Entry en = (e < L) ? lht[i + e] : lht[n - 1 - (j + (e - L))];
-                sm.u.pack.item[e] = en.item;
-                sm.u.pack.w[pad32(e)] = en.w;
+            const bool lastL = i + L == nl, lastH = j + H == nh;
+            const uint32_t ne = L + H + (lastH ? 0u : 1u);
+            // entries, several loads in flight per thread
+            {
+                const uint2 *lh2 = reinterpret_cast<const uint2 *>(lht);
+                auto src = [&](uint32_t e) {
+                    return e < L ? lh2[i + e] : lh2[n - 1 - (j + (e - L))];
+                };
+                uint32_t e = tid;
+                for (; e + 3 * BT < ne; e += 4 * BT) {
+                    uint2 v[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) v[r] = src(e + r * BT);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) sE[pk16b(e + r * BT)] = v[r];
+                }
+                for (; e < ne; e += BT) sE[pk16b(e)] = src(e);
             }
             __syncthreads();
-            // blocked values: d' (lights) then e' (heavies); exclusive scan
+            // values d' = Q - N q (lights) and e' = N q - Q (heavies) of the
+            // thread's window positions [b0, b0 + kPer): their sum, and the
+            // sum of the light ones (for P(L))
             const uint32_t LH = L + H;
-            const uint32_t per = (LH + BT - 1) / BT;
-            const uint32_t b0 = tid * per;
-            u128 run = 0;
-            for (uint32_t k = 0; k < per; ++k) {
-                uint32_t e = b0 + k;
-                if (e >= LH) break;
-                float wv = sm.u.pack.w[pad32(e)];
-                u128 val = (e < L) ? (u128)(Q - (uint64_t)N * light_q(wv, qsc, Qn))
-                                   : mul_nq(N, heavy_q(wv, qsc, Qn)) - Q;
-                sm.u.pack.P[pp8b(e + 1)] = val;
-                run += val;
+            const uint32_t b0 = tid * kPer;
+            auto qclamp = [&](uint32_t e) {
+                const uint64_t q = fixed_q(__uint_as_float(sE[pk16b(e)].y), qsc);
+                return e < L ? (q > Qn ? Qn : q) : (q <= Qn ? Qn + 1 : q);
+            };
+            auto value = [&](uint32_t e, uint64_t q) {
+                return e < L ? (u128)(Q - (uint64_t)N * q) : mul_nq(N, q) - Q;
+            };
+            constexpr uint32_t kKeep = kPer <= 8 ? kPer : 1;   // q kept in registers
+            uint64_t qk[kKeep];
+            u128 run = 0, runL = 0;
+#pragma unroll
+            for (uint32_t k = 0; k < kPer; ++k) {
+                const uint32_t e = b0 + k;
+                if (e < LH) {
+                    const uint64_t q = qclamp(e);
+                    if (kPer <= 8) qk[k < kKeep ? k : 0] = q;
+                    const u128 v = value(e, q);
+                    run += v;
+                    if (e < L) runL += v;
+                }
             }
-            u128 inc = run;
+            u128 inc = run, redL = runL;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                u128 o = shfl_up_u128(inc, d);
+                const u128 o = shfl_up_u128(inc, d);
                 if (lane >= d) inc += o;
+                const uint64_t lo = __shfl_xor_sync(0xffffffffu, (uint64_t)redL, d);
+                const uint64_t hi = __shfl_xor_sync(0xffffffffu, (uint64_t)(redL >> 64), d);
+                redL += ((u128)hi << 64) | lo;
             }
             if (lane == 31) sm.wred[warp] = inc;
+            if (lane == 0) sm.wredL[warp] = redL;
             __syncthreads();
-            u128 pre = inc - run;
-            for (int k = 0; k < warp; ++k) pre += sm.wred[k];
-            if (tid == 0) sm.u.pack.P[0] = 0;
-            for (uint32_t k = 0; k < per; ++k) {
-                uint32_t e = b0 + k;
-                if (e >= LH) break;
-                pre += sm.u.pack.P[pp8b(e + 1)];
-                sm.u.pack.P[pp8b(e + 1)] = pre;
+            u128 pre0 = inc - run, PL = 0;
+            for (int k = 0; k < BT / 32; ++k) {
+                if (k < warp) pre0 += sm.wred[k];
+                PL += sm.wredL[k];
+            }
+            // keys: A(x) = floor((D0 + P(x)) / 2^15) - floor(D0 / 2^15) and
+            // B(y) = floor(E'(j+y+1) / 2^15) - floor(D0 / 2^15), capped at
+            // 2^62 (E'(j+y+1) = E0 + P(L+y+1) - P(L))
+            {
+                const u128 d0l = D0 & (u128)((1u << kKeyShift) - 1);
+                const u128 ch = E0 - D0 + d0l - PL;
+                if (tid == 0) sK[0] = 0;
+                u128 pre = pre0;
+#pragma unroll
+                for (uint32_t k = 0; k < kPer; ++k) {
+                    const uint32_t e = b0 + k;
+                    if (e < LH) {
+                        pre += value(e, kPer <= 8 ? qk[k < kKeep ? k : 0] : qclamp(e));
+                        if (e < L) {
+                            sK[pk16b(e + 1)] = (int64_t)((pre + d0l) >> kKeyShift);
+                        } else {
+                            const __int128 v = (__int128)(ch + pre) >> kKeyShift;
+                            sK[pk16b(e + 1)] = v < ((__int128)1 << 62) ? (int64_t)v
+                                                                       : ((int64_t)1 << 62);
+                        }
+                    }
+                }
             }
             __syncthreads();
-            // merge path over K buckets
-            const u128 PL = sm.u.pack.P[pp8b(L)];
-            auto Av = [&](uint32_t x) { return D0 + sm.u.pack.P[pp8b(x)]; };
-            auto Bv = [&](uint32_t y) { return E0 + (sm.u.pack.P[pp8b(L + y + 1)] - PL); };
-            auto split_at = [&](uint32_t d) {
-                uint32_t lo = d > H ? d - H : 0, hi = d < L ? d : L;
+            auto Av = [&](uint32_t x) { return sK[pk16b(x)]; };
+            auto Bv = [&](uint32_t y) { return sK[pk16b(L + y + 1)]; };
+            // how far the window reaches: light L-1 closes after the heavies
+            // with B <= A(L-1); heavy H-1 closes after the lights with
+            // A < B(H-1).  A window side that holds the rest of its list
+            // never limits the chunk.
+            if (tid == 0) {
+                const uint64_t rest = n - i - j;
+                uint64_t KL = ~0ull, KH = ~0ull;
+                uint32_t cntB = H, cntA = L;
+                if (!lastL) {
+                    const int64_t a = Av(L - 1);
+                    uint32_t lo = 0, hi = H;   // first y with B(y) > a
+                    while (lo < hi) {
+                        const uint32_t m = (lo + hi) >> 1;
+                        if (Bv(m) <= a) lo = m + 1;
+                        else hi = m;
+                    }
+                    cntB = lo;
+                    KL = (uint64_t)L + cntB;
+                }
+                if (!lastH) {
+                    const int64_t bh = Bv(H - 1);
+                    uint32_t lo = 0, hi = L;   // first x with A(x) >= B(H-1)
+                    while (lo < hi) {
+                        const uint32_t m = (lo + hi) >> 1;
+                        if (Av(m) < bh) lo = m + 1;
+                        else hi = m;
+                    }
+                    cntA = lo;
+                    KH = (uint64_t)H + cntA;
+                }
+                uint32_t Kc, xk, yk;
+                if (KL <= KH && KL <= rest) { Kc = (uint32_t)KL; xk = L; yk = cntB; }
+                else if (KH <= rest) { Kc = (uint32_t)KH; xk = cntA; yk = H; }
+                else { Kc = (uint32_t)rest; xk = L; yk = H; }
+                sm.Kc = Kc; sm.xk = xk; sm.yk = yk;
+                sm.Dn = D0;   // P(0) = 0; the owner of position xk-1 overwrites
+                sm.Pe = PL;   // P(L + 0); the owner of position L+yk-1 overwrites
+            }
+            __syncthreads();
+            const uint32_t Kc = sm.Kc, xk = sm.xk, yk = sm.yk;
+            // exact end state: P(xk) and P(L + yk) from the owners' prefixes
+            {
+                const uint32_t px = xk, pe = L + yk;
+                if (px > 0 && (px - 1) / kPer == tid) {
+                    u128 p = pre0;
+                    for (uint32_t e = b0; e < px; ++e) p += value(e, qclamp(e));
+                    sm.Dn = D0 + p;
+                }
+                if (pe > 0 && pe != L && (pe - 1) / kPer == tid) {
+                    u128 p = pre0;
+                    for (uint32_t e = b0; e < pe; ++e) p += value(e, qclamp(e));
+                    sm.Pe = p;
+                }
+            }
+            // merge path over Kc buckets
+            const uint32_t per_out = (Kc + BT - 1) / BT;
+            const uint32_t d0 = tid * per_out;
+            if (d0 < Kc) {
+                uint32_t lo = d0 > H ? d0 - H : 0, hi = d0 < L ? d0 : L;
                 while (lo < hi) {
-                    uint32_t m = (lo + hi) >> 1;
-                    bool p = (d - m == 0) || (m == L) || sweep_le(Bv(d - m - 1), Av(m));
-                    if (p) hi = m;
+                    const uint32_t m = (lo + hi) >> 1;
+                    // m < hi <= min(d0, L): both neighbours exist
+                    if (Bv(d0 - m - 1) <= Av(m)) hi = m;
                     else lo = m + 1;
                 }
-                return lo;
-            };
-            const uint32_t per_out = (K + BT - 1) / BT;
-            const uint32_t d0 = tid * per_out;
-            if (d0 < K) {
-                uint32_t x = split_at(d0), y = d0 - x;
-                u128 a = Av(x);
-                u128 b = y < H ? Bv(y) : 0;
-                const uint32_t dend = min(d0 + per_out, K);
+                uint32_t x = lo, y = d0 - lo;
+                int64_t a = Av(x);
+                int64_t b = y < H ? Bv(y) : 0;
+                // the heavy that fills the next light bucket (list offset y)
+                uint32_t hcur = j + y < nh ? sE[pk16b(L + y)].x : 0u;
+                const uint32_t dend = min(d0 + per_out, Kc);
                 for (uint32_t d = d0; d < dend; ++d) {
-                    bool heavy = (y < H) && (x == L || sweep_le(b, a));
-                    uint32_t item, alias;
-                    float prob;
+                    const bool heavy = (y < H) && (x == L || b <= a);
+                    const uint2 ld = sE[pk16b(heavy ? L + y + 1 : x)];
+                    const uint32_t item = heavy ? hcur : ld.x;
+                    const bool has = j + (heavy ? y + 1 : y) < nh;
+                    uint32_t alias = item;
+                    float prob = 1.0f;
+                    if (has) {
+                        alias = heavy ? ld.x : hcur;
+                        prob = heavy ? fminf(fmaxf(1.0f - __ll2float_rn(a - b) * invQk, 0.0f), 1.0f)
+                                     : fminf(__uint_as_float(ld.y) * inv_avg, 1.0f);
+                    }
+                    rt[item] = make_uint2(__float_as_uint(prob), alias);
                     if (heavy) {
-                        item = sm.u.pack.item[L + y];
-                        if (j + y + 1 < nh) {
-                            if (!sweep_le(b, a)) {
-                                prob = 1.0f;
-                            } else {
-                                // kept fraction 1 - (A - B) 2^15 / Q on the rounded prefixes
-                                const int64_t delta =
-                                    (int64_t)((a >> kKeyShift) - (b >> kKeyShift));
-                                prob = fminf(fmaxf(1.0f - __ll2float_rn(delta) *
-                                                              (sm.invQ * (float)(1u << kKeyShift)),
-                                                   0.0f),
-                                             1.0f);
-                            }
-                            alias = sm.u.pack.item[L + y + 1];
-                        } else {
-                            prob = 1.0f;
-                            alias = item;
-                        }
                         ++y;
-                        if (y < H) b = Bv(y);
+                        b = y < H ? Bv(y) : 0;
+                        hcur = ld.x;
                     } else {
-                        item = sm.u.pack.item[x];
-                        if (j + y < nh) {
-                            prob = fminf(sm.u.pack.w[pad32(x)] * sm.inv_avg, 1.0f);
-                            alias = sm.u.pack.item[L + y];
-                        } else {
-                            prob = 1.0f;
-                            alias = item;
-                        }
                         ++x;
                         a = Av(x);
                     }
-                    rt[item] = make_uint2(__float_as_uint(prob), alias);
                 }
             }
-            if (tid == 0) sm.xk = split_at(K);
             __syncthreads();
             if (tid == 0) {
-                uint32_t xk = sm.xk, yk = K - xk;
-                sm.D = Av(xk);
-                sm.E = yk ? Bv(yk - 1) : E0;
                 sm.i = i + xk;
                 sm.j = j + yk;
+                sm.D = sm.Dn;
+                sm.E = E0 + (sm.Pe - PL);
             }
             __syncthreads();
         }
