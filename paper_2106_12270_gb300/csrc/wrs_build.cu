@@ -614,7 +614,7 @@ __device__ __forceinline__ void crange(const SplitCtx &C, uint64_t k, uint64_t &
 // Given the smallest c with P(32c), finish the split for bucket count k with
 // one warp: the answer is in (32(c-1), 32c]; lane x tests i = 32(c-1)+1+x.
 __device__ void split_fine(const SplitCtx &C, const BuildParams &Pm, uint64_t k, uint64_t c,
-                           SplitRec *out, int lane) {
+                           u128 Dbase, u128 Ebase, SplitRec *out, int lane) {
     uint64_t lo = k > C.nh ? k - C.nh : 0;
     uint64_t hi = k < C.nl ? k : C.nl;
     const uint32_t N = (uint32_t)C.n;
@@ -623,7 +623,7 @@ __device__ void split_fine(const SplitCtx &C, const BuildParams &Pm, uint64_t k,
     if (c == 0) {
         ans = 0;
         Dv = 0;
-        Ev = ck_E(C, k >> 5);
+        Ev = Ebase;   // E'(k)
     } else {
         uint64_t lb = 32 * (c - 1);  // light base
         uint64_t hb = k - 32 * c;    // heavy base, multiple of 32
@@ -643,8 +643,7 @@ __device__ void split_fine(const SplitCtx &C, const BuildParams &Pm, uint64_t k,
             if (lane >= s) { dinc += a; einc += b; }
         }
         u128 eexc = einc - e;
-        u128 Dbase = ck_D(C, c - 1);
-        u128 Ebase = ck_E(C, hb >> 5);
+        // Dbase = D'(32(c-1)) and Ebase = E'(hb), found by the coarse phase
         u128 Dl = Dbase + dinc;                                   // D'(lb + 1 + lane)
         u128 Eh = Ebase + shfl_u128(eexc, 31 - lane);             // E'(k - (lb + 1 + lane))
         uint64_t i = lb + 1 + lane;
@@ -727,9 +726,18 @@ k_split(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
             if (pred_c(C, k, m)) b = m;
             else a = m + 1;
         }
-        // the checkpoint index for the fine search (< 2^26), parked in the
-        // record the fine search then writes in full
-        splits[t].pad[0] = (uint32_t)a;
+        // the checkpoint index for the fine search (< 2^26) and the two exact
+        // prefixes it starts from, parked in the record the fine search
+        // then writes in full
+        SplitRec &r = splits[t];
+        r.pad[0] = (uint32_t)a;
+        if (a > 0) {
+            r.D = ck_D(C, a - 1);
+            r.E = ck_E(C, (k - 32 * a) >> 5);
+        } else {
+            r.D = 0;
+            r.E = ck_E(C, k >> 5);
+        }
     }
 }
 
@@ -748,8 +756,9 @@ k_split_fine(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
     C.ckl = ckl; C.ckh = ckh; C.seg_pre = seg_pre; C.lh = lh; C.n = n; C.nl = Pm.nl;
     C.nh = Pm.nh; C.Q = Pm.Q;
     const uint64_t c = splits[t].pad[0];
+    const u128 Dbase = splits[t].D, Ebase = splits[t].E;
     __syncwarp();
-    split_fine(C, Pm, t * S, c, splits + t, threadIdx.x & 31);
+    split_fine(C, Pm, t * S, c, Dbase, Ebase, splits + t, threadIdx.x & 31);
 }
 
 // Splits 0 and s (the whole table's ends).
