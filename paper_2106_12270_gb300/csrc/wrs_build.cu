@@ -897,27 +897,31 @@ __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
     // fixed by the split), so B(y) = floor((E0 - D1 + D0 mod 2^15 +
     // P(L+y+1)) / 2^15).
     {
-        u128 pre = inc - run;
-        for (int k = 0; k < warp; ++k) pre += s_w[k];
+        // p = P(x) + (D0 mod 2^15): the light keys are p >> 15 directly
         const u128 d0l = R0.D & (u128)((1u << kKeyShift) - 1);
-        const u128 ch = R0.E - R1.D + d0l;
-        if (tid == 0) sK[pk16(0)] = 0;
+        u128 p = inc - run + d0l;
+        for (int k = 0; k < warp; ++k) p += s_w[k];
+        const u128 ch = R0.E - R1.D;
+        if (tid == 0) {
+            sK[pk16(0)] = 0;
+            sK[pk16(K + 1)] = INT64_MAX;   // after the last heavy: never closes
+        }
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             const uint32_t e = b0 + k;
             if (e < K) {
                 if (e < L) {
-                    pre += (u128)(Q - (uint64_t)N * qv[k]);
-                    sK[pk16(e + 1)] = (int64_t)((pre + d0l) >> kKeyShift);   // < 2^61
+                    p += (u128)(Q - (uint64_t)N * qv[k]);
+                    sK[pk16(e + 1)] = (int64_t)(p >> kKeyShift);   // < 2^61
                 } else {
-                    pre += mul_nq(N, qv[k]) - Q;
-                    sK[pk16(e + 1)] = sweep_key(ch, pre);
+                    p += mul_nq(N, qv[k]) - Q;
+                    sK[pk16(e + 1)] = sweep_key(ch, p);
                 }
             }
         }
         // the section's own sums must meet the split's: the thread holding
         // position K-1 has P(K) = D1 - D0 + E1 - E0
-        if (b0 < K && b0 + kPer >= K && pre != (R1.D - R0.D) + (R1.E - R0.E))
+        if (b0 < K && b0 + kPer >= K && p - d0l != (R1.D - R0.D) + (R1.E - R0.E))
             atomicOr(const_cast<uint32_t *>(&P->status), ERR_INTERNAL);
     }
     __syncthreads();
@@ -938,7 +942,7 @@ __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
         }
         uint32_t x = lo, y = d0 - lo;
         int64_t a = Av(x);
-        int64_t b = y < H ? Bv(y) : 0;
+        int64_t b = Bv(y);   // y = H reads the sentinel
         // one output per step: close heavy y (b <= a, or no light left) or
         // light x.  The next heavy in the list fills the bucket's rest: list
         // offset y+1 for a heavy, y for a light (sE slot K holds the first
@@ -951,7 +955,8 @@ __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
 #pragma unroll
             for (int k = 0; k < kPer; ++k) {
                 if (d0 + k < K) {
-                    const bool heavy = (y < H) && (x == L || b <= a);
+                    // (y = H leaves b at the sentinel, above every key)
+                    const bool heavy = x == L || b <= a;
                     // one entry load per step: the closed light (item and
                     // weight), or the heavy after the closed one (its item)
                     const uint2 ld = sE[pk16(heavy ? L + y + 1 : x)];
