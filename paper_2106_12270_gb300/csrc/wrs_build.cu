@@ -498,9 +498,21 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
         // ---- coalesced copy-out
         uint2 *lh2 = reinterpret_cast<uint2 *>(lh);
         const uint2 *e2 = reinterpret_cast<const uint2 *>(sm.e);
-        for (uint32_t q = lane; q < tl; q += 32) lh2[run_l + q] = e2[pad16(q)];
-        for (uint32_t q = lane; q < tnh; q += 32)
-            lh2[n - 1 - (run_h + q)] = e2[pad16(kChunk - 1 - q)];
+        // two entries in flight per lane
+        for (uint32_t q = lane; q < tl; q += 64) {
+            const uint2 v0 = e2[pad16(q)];
+            const bool two = q + 32 < tl;
+            const uint2 v1 = two ? e2[pad16(q + 32)] : v0;
+            lh2[run_l + q] = v0;
+            if (two) lh2[run_l + q + 32] = v1;
+        }
+        for (uint32_t q = lane; q < tnh; q += 64) {
+            const uint2 v0 = e2[pad16(kChunk - 1 - q)];
+            const bool two = q + 32 < tnh;
+            const uint2 v1 = two ? e2[pad16(kChunk - 1 - (q + 32))] : v0;
+            lh2[n - 1 - (run_h + q)] = v0;
+            if (two) lh2[n - 1 - (run_h + q + 32)] = v1;
+        }
         run_l += tl;
         run_h += tnh;
         run_sl += TL;
