@@ -237,7 +237,8 @@ int wrs_sample_rows(const wrs_row *d_rows, uint64_t n, uint64_t first,
  * draw every section's samples inside it, so that its rows stay in cache:
  * CACHED gathers rows through L1/L2, LIMITED additionally reserves shared
  * memory so only one CTA runs per SM (fewer sections evict each other),
- * SMEM copies each section's rows into shared memory first.  The three
+ * SMEM copies each section's rows into shared memory first, each row as
+ * its integer keep threshold ceil(prob 2^32) and its alias.  The three
  * sectioned modes produce identical samples; they differ only in speed. */
 enum wrs_sample_mode {
     WRS_SAMPLE_NAIVE = 0,

@@ -162,8 +162,10 @@ k_sec_counts(uint64_t n, uint64_t nsec, uint64_t count, uint32_t k0, uint32_t k1
 }
 
 // One CTA per section: draw its samples from its rows.  kSmem stages the
-// section's rows in shared memory first (coalesced 8-byte loads), otherwise
-// the rows are gathered through the caches.
+// section's rows in shared memory first (coalesced 8-byte loads; each row
+// becomes its integer keep threshold and alias, so a draw needs no
+// float-to-integer conversion), otherwise the rows are gathered through the
+// caches.
 template <bool kSmem>
 __global__ void __launch_bounds__(256)
 k_sample_sec(const uint2 *__restrict__ rows, uint64_t n, uint64_t nsec,
