@@ -187,3 +187,50 @@ def test_batched_build_and_sample_replay_as_cuda_graph(batch):
     wrs.sample_batched_rows(rows, off_t, ntab, cnt_off, 5, out_e)
     torch.cuda.synchronize()
     assert torch.equal(out_g, out_e)
+
+
+def _edge_tables():
+    """Tables around chunk sizes and with extreme light/heavy mixes: the
+    chunked sweep's windows run out of lights first, of heavies first, or
+    end exactly on a chunk."""
+    r = np.random.default_rng(31)
+    tabs = []
+    for n in (511, 512, 513, 1023, 1024, 1025, 2047, 2048, 2049, 4095, 4096, 4097, 8193):
+        tabs.append(r.random(n).astype(np.float32))                       # uniform
+        tabs.append(r.exponential(1.0, n).astype(np.float32))              # Exp(1)
+    for n in (3000, 9000):
+        w = np.ones(n, np.float32)
+        w[r.random(n) < 0.1] = 0.01        # 90% heavy: lights run out first
+        tabs.append(w)
+        w = np.ones(n, np.float32)
+        w[n // 3] = 1e6                    # one heavy that fills everything
+        tabs.append(w)
+        tabs.append(np.full(n, 0.37, np.float32))                          # all light
+        tabs.append((1.0 + r.integers(-64, 64, n) * 2.0**-23).astype(np.float32))
+        w = r.gamma(0.1, 1.0, n).astype(np.float32)
+        w[: n // 2] = 0.0                  # a long run of zero weights
+        tabs.append(w)
+    return tabs
+
+
+@pytest.mark.parametrize("threads,chunk", [(256, 1024), (256, 512), (512, 2048)])
+def test_batched_window_edges_equal_single_builds(threads, chunk):
+    tabs = _edge_tables()
+    sizes = np.array([t.size for t in tabs], np.int64)
+    off = np.zeros(sizes.size + 1, np.uint64)
+    off[1:] = np.cumsum(sizes).astype(np.uint64)
+    w = np.concatenate(tabs)
+    wt = torch.from_numpy(w).cuda()
+    off_t = torch.from_numpy(off.astype(np.int64)).cuda()
+    rows = torch.zeros(int(off[-1]), dtype=torch.int64, device="cuda")
+    bb = wrs.BatchBuilder(int(off[-1]), sizes.size)
+    bb.tuning = wrs.BatchTuning(threads, chunk, 0, 0.0)
+    bb.build(wt, off_t, rows, None)
+    torch.cuda.synchronize()
+    summ = bb.summaries()
+    for t, wtab in enumerate(tabs):
+        assert summ[t]["status"] == wrs.OK, t
+        b = Built(wtab)
+        prob, alias = table_rows(rows, off, t)
+        assert np.array_equal(prob.view(np.uint32), b.prob.view(np.uint32)), t
+        assert np.array_equal(alias, b.alias), t
