@@ -405,13 +405,21 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
         if (base + kChunk < b) load_chunk(base + kChunk);
         __syncwarp();
         // ---- classify (input order) and count
+        const bool full = lim >= (uint64_t)kChunk;   // every chunk but a sub-segment's last
         uint32_t lmask = 0, vmask = 0;
+        if (full) {
+            vmask = (1u << kPartItems) - 1u;
 #pragma unroll
-        for (int k = 0; k < kPartItems; ++k) {
-            float x = sm.wv[pad32(e0 + k)];
-            bool valid = (uint64_t)(e0 + k) < lim;
-            vmask |= (uint32_t)valid << k;
-            lmask |= (uint32_t)(valid && x <= lmax) << k;
+            for (int k = 0; k < kPartItems; ++k)
+                lmask |= (uint32_t)(sm.wv[pad32(e0 + k)] <= lmax) << k;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kPartItems; ++k) {
+                float x = sm.wv[pad32(e0 + k)];
+                bool valid = (uint64_t)(e0 + k) < lim;
+                vmask |= (uint32_t)valid << k;
+                lmask |= (uint32_t)(valid && x <= lmax) << k;
+            }
         }
         const uint32_t cnt = __popc(lmask);
         uint32_t icnt = cnt;
@@ -432,7 +440,7 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
             for (int k = 0; k < kPartItems; ++k) {
                 const bool lt = (lmask >> k) & 1u;
                 const uint32_t slot = lt ? lrank : hslot;
-                if ((vmask >> k) & 1u)
+                if (full || ((vmask >> k) & 1u))
                     sm.e[pad16(slot)] = Entry{(uint32_t)(base + e0 + k), sm.wv[pad32(e0 + k)]};
                 lrank += lt;
                 hslot -= !lt;
