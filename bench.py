@@ -39,13 +39,13 @@ SAMPLE_BYTES_PER_DRAW = 36     # one 32-byte row sector + a 4-byte output
 KERNELS_PER_BUILD = 10         # sum, count, qsum, scatter, segscan, split ends, split, split fine, pack, info
 # DRAM bytes the hardware moved per unit (dram__bytes_read.sum +
 # dram__bytes_write.sum) in ncu captures of these kernels: the build at
-# N = 2^25 items (sum 4.1, count 4.0, scatter 10.7, split 0.9, pack 15.6) and
-# the naive sampler drawing 2^26 samples from a 2^25-row table (87.3 B of row
+# N = 2^25 items (sum 4.1, count 4.0, scatter 10.6, split 0.9, pack 15.6) and
+# the naive sampler drawing 2^25 samples from a 2^25-row table (87.6 B of row
 # sectors read + 4 B written per draw); both workloads exceed L2 and the
 # traffic grows with the units, so a launch's traffic is these times its
 # units.  To be re-measured whenever one of these kernels changes.
 BUILD_TRAFFIC_PER_ITEM = 35.2
-SAMPLE_TRAFFIC_PER_DRAW = 91.3
+SAMPLE_TRAFFIC_PER_DRAW = 91.5
 KERNELS_PER_SAMPLE = 1
 # batched build/sample are timed separately (extra keys), not in gpu_launches
 
@@ -421,7 +421,7 @@ def run_gpu(args):
     sample_roof = {"bound": "hbm", "achieved": sample_gbs, "peak": hbm, "unit": "GB/s",
                    "frac": sample_gbs / hbm,
                    "traffic": SAMPLE_TRAFFIC_PER_DRAW * count if count else None,
-                   "traffic_unit": "bytes per launch (ncu, scaled from 2^26 draws)",
+                   "traffic_unit": "bytes per launch (ncu, scaled from 2^25 draws)",
                    "kernel": "k_sample_naive",
                    "peak_kind": peak_kind,
                    "random_gather_probe": {"achieved": probe_gbs, "unit": "GB/s",
