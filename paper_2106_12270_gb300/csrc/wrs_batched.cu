@@ -205,13 +205,21 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
                             (uint64_t)(e + c) < lim ? __ldg(wt + tb + e + c) : 0.f;
                 }
                 __syncwarp();
+                const bool fullt = lim >= (uint64_t)kBTile;   // every tile but the table's last
                 uint32_t lmask = 0, vmask = 0;
+                if (fullt) {
+                    vmask = (kItems == 32) ? 0xffffffffu : ((1u << kItems) - 1u);
 #pragma unroll
-                for (int k = 0; k < kItems; ++k) {
-                    float x = sm.u.part.wv[pad32(e0 + k)];
-                    bool valid = (uint64_t)(e0 + k) < lim;
-                    vmask |= (uint32_t)valid << k;
-                    lmask |= (uint32_t)(valid && x <= lmax) << k;
+                    for (int k = 0; k < kItems; ++k)
+                        lmask |= (uint32_t)(sm.u.part.wv[pad32(e0 + k)] <= lmax) << k;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < kItems; ++k) {
+                        float x = sm.u.part.wv[pad32(e0 + k)];
+                        bool valid = (uint64_t)(e0 + k) < lim;
+                        vmask |= (uint32_t)valid << k;
+                        lmask |= (uint32_t)(valid && x <= lmax) << k;
+                    }
                 }
                 const uint32_t cnt = __popc(lmask);
                 uint32_t icnt = cnt;
@@ -233,7 +241,7 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
                 uint32_t lrank = wl + icnt - cnt, hrank = (uint32_t)e0 - lrank;
 #pragma unroll
                 for (int k = 0; k < kItems; ++k) {
-                    if (!((vmask >> k) & 1u)) break;
+                    if (!fullt && !((vmask >> k) & 1u)) break;
                     Entry en{(uint32_t)(tb + e0 + k), sm.u.part.wv[pad32(e0 + k)]};
                     if ((lmask >> k) & 1u) sm.u.part.e[pad16(lrank++)] = en;
                     else sm.u.part.e[pad16(kBTile - 1 - hrank++)] = en;
