@@ -584,18 +584,21 @@ static cudaError_t launch_bb(const float *d_w, const uint64_t *d_off, uint32_t n
                              wrs_row *d_rows, wrs_row *const *d_row_ptrs, wrs_table_summary *d_info,
                              uint32_t ctas_per_sm, cudaStream_t st) {
     const int smem = (int)sizeof(BatchShared<BT, CH>);
-    static bool configured = false;
-    static int per_sm_max = 0;
-    cudaError_t e;
-    if (!configured) {
-        e = cudaFuncSetAttribute(k_batched_build<BT, CH>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e) return e;
+    cudaError_t e = ensure_dynamic_smem<k_batched_build<BT, CH>>((uint32_t)smem);
+    if (e) return e;
+    // resident CTAs per SM for this tiling, cached per device
+    static std::atomic<int> resident[kMaxDevices];
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e) return e;
+    const int slot = dev >= 0 && dev < kMaxDevices ? dev : 0;
+    int per_sm_max = resident[slot].load(std::memory_order_relaxed);
+    if (per_sm_max <= 0) {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_max, k_batched_build<BT, CH>, BT,
                                                           smem);
         if (e) return e;
         if (per_sm_max < 1) per_sm_max = 1;
-        configured = true;
+        resident[slot].store(per_sm_max, std::memory_order_relaxed);
     }
     e = cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), st);
     if (e) return e;

@@ -1044,15 +1044,20 @@ __global__ void k_info(const BuildParams *__restrict__ P, wrs_build_info *__rest
 // host launchers
 // ===========================================================================
 
-static int g_num_sms = 0;
+// SM count of the current device (cached per device; any positive value
+// gives valid grids, so a race only repeats the query).
 int num_sms() {
-    if (!g_num_sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-        if (g_num_sms <= 0) g_num_sms = 152;
+    static std::atomic<int> sms[kMaxDevices];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int slot = dev >= 0 && dev < kMaxDevices ? dev : 0;
+    int v = sms[slot].load(std::memory_order_relaxed);
+    if (v <= 0) {
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        if (v <= 0) v = 152;
+        sms[slot].store(v, std::memory_order_relaxed);
     }
-    return g_num_sms;
+    return v;
 }
 
 cudaError_t launch_total(const float *d_w, uint64_t n, unsigned char *ws, const Layout &L,
@@ -1133,13 +1138,8 @@ static cudaError_t launch_pack_t(void (*kern)(const BuildParams *, const Entry *
                                  uint32_t S, cudaStream_t st) {
     const BuildParams *P = reinterpret_cast<const BuildParams *>(ws + L.params);
     const uint32_t smem = pack_smem_bytes(S);
-    static uint32_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e =
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e) return e;
-        configured = smem;
-    }
+    cudaError_t e = kPer == 8 ? ensure_dynamic_smem<k_pack8>(smem) : ensure_dynamic_smem<k_pack16>(smem);
+    if (e) return e;
     const uint32_t threads = (S + kPer - 1) / kPer;   // S is a multiple of 256: whole warps
     kern<<<(unsigned)L.sections, threads, smem, st>>>(
         P, reinterpret_cast<const Entry *>(ws + L.lh),

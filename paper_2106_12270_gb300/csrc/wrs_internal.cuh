@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "../../include/wrs.h"
 
 namespace wrs {
@@ -121,6 +123,28 @@ constexpr int kChunk = 512;           // items a partition warp handles at a tim
 constexpr int kSplitThreads = 256;    // also p of the partial p-ary search
 
 static inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// Host: grant kernel Kern at least `bytes` of dynamic shared memory on the
+// current device.  The attribute is per device; the largest grant so far is
+// remembered per kernel and device, so the driver call happens once, and
+// concurrent callers are safe (a repeated grant is harmless).
+constexpr int kMaxDevices = 64;
+template <auto Kern>
+inline cudaError_t ensure_dynamic_smem(uint32_t bytes) {
+    static std::atomic<uint32_t> granted[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return e;
+    if (dev < 0 || dev >= kMaxDevices)
+        return cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    uint32_t cur = granted[dev].load(std::memory_order_acquire);
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e) return e;
+    while (cur < bytes && !granted[dev].compare_exchange_weak(cur, bytes, std::memory_order_acq_rel)) {
+    }
+    return cudaSuccess;
+}
 
 Layout make_layout(uint64_t n, uint32_t section_size);
 

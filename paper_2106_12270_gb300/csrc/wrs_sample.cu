@@ -245,26 +245,16 @@ cudaError_t launch_sample_sectioned(const wrs_row *d_rows, uint64_t n, uint64_t 
     if (mode == WRS_SAMPLE_SMEM) {
         uint64_t maxR = (n + nsec - 1) / nsec;
         uint32_t smem = (uint32_t)(maxR * sizeof(uint2));
-        static uint32_t configured = 0;
-        if (smem > configured) {
-            e = cudaFuncSetAttribute(k_sample_sec<true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e) return e;
-            configured = smem;
-        }
+        e = ensure_dynamic_smem<k_sample_sec<true>>(smem);
+        if (e) return e;
         k_sample_sec<true><<<(unsigned)nsec, 256, smem, st>>>(rows, n, nsec, d_counts, d_offsets,
                                                               k0, k1, d_out, vec_ok);
     } else {
         uint32_t smem = 0;
         if (mode == WRS_SAMPLE_LIMITED) {
             smem = kLimitedSmem;
-            static bool configured = false;
-            if (!configured) {
-                e = cudaFuncSetAttribute(k_sample_sec<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (e) return e;
-                configured = true;
-            }
+            e = ensure_dynamic_smem<k_sample_sec<false>>(smem);
+            if (e) return e;
         }
         k_sample_sec<false><<<(unsigned)nsec, 256, smem, st>>>(rows, n, nsec, d_counts,
                                                                d_offsets, k0, k1, d_out, vec_ok);
