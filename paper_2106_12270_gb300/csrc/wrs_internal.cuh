@@ -126,7 +126,7 @@ static inline uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a
 
 // Host: grant kernel Kern at least `bytes` of dynamic shared memory on the
 // current device.  The attribute is per device; the largest grant so far is
-// remembered per kernel and device, so the driver call happens once, and
+// remembered per kernel and device, so the CUDA call happens once, and
 // concurrent callers are safe (a repeated grant is harmless).
 constexpr int kMaxDevices = 64;
 template <auto Kern>
