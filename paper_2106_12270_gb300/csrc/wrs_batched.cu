@@ -374,39 +374,44 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
             // with B <= A(L-1); heavy H-1 closes after the lights with
             // A < B(H-1).  A window side that holds the rest of its list
             // never limits the chunk.
-            if (tid == 0) {
+            if (warp == 0) {
+                // 32-ary ballot searches over the monotone keys
+                auto count_below = [&](uint32_t len, auto below) {
+                    uint32_t lo = 0, hi = len;   // the count lies in [lo, hi]
+                    while (lo < hi) {
+                        const uint32_t step = (hi - lo + 31) / 32;
+                        const uint32_t idx = lo + lane * step;
+                        const uint32_t c =
+                            __popc(__ballot_sync(0xffffffffu, idx < hi && below(idx)));
+                        if (c == 0) { hi = lo; break; }
+                        const uint32_t nlo = lo + (c - 1) * step + 1;
+                        hi = min(lo + c * step, hi);
+                        lo = nlo;
+                    }
+                    return lo;
+                };
                 const uint64_t rest = n - i - j;
                 uint64_t KL = ~0ull, KH = ~0ull;
                 uint32_t cntB = H, cntA = L;
                 if (!lastL) {
-                    const int64_t a = Av(L - 1);
-                    uint32_t lo = 0, hi = H;   // first y with B(y) > a
-                    while (lo < hi) {
-                        const uint32_t m = (lo + hi) >> 1;
-                        if (Bv(m) <= a) lo = m + 1;
-                        else hi = m;
-                    }
-                    cntB = lo;
+                    const int64_t al = Av(L - 1);
+                    cntB = count_below(H, [&](uint32_t y) { return Bv(y) <= al; });
                     KL = (uint64_t)L + cntB;
                 }
                 if (!lastH) {
                     const int64_t bh = Bv(H - 1);
-                    uint32_t lo = 0, hi = L;   // first x with A(x) >= B(H-1)
-                    while (lo < hi) {
-                        const uint32_t m = (lo + hi) >> 1;
-                        if (Av(m) < bh) lo = m + 1;
-                        else hi = m;
-                    }
-                    cntA = lo;
+                    cntA = count_below(L, [&](uint32_t x) { return Av(x) < bh; });
                     KH = (uint64_t)H + cntA;
                 }
-                uint32_t Kc, xk, yk;
-                if (KL <= KH && KL <= rest) { Kc = (uint32_t)KL; xk = L; yk = cntB; }
-                else if (KH <= rest) { Kc = (uint32_t)KH; xk = cntA; yk = H; }
-                else { Kc = (uint32_t)rest; xk = L; yk = H; }
-                sm.Kc = Kc; sm.xk = xk; sm.yk = yk;
-                sm.Dn = D0;   // P(0) = 0; the owner of position xk-1 overwrites
-                sm.Pe = PL;   // P(L + 0); the owner of position L+yk-1 overwrites
+                if (lane == 0) {
+                    uint32_t Kc, xk, yk;
+                    if (KL <= KH && KL <= rest) { Kc = (uint32_t)KL; xk = L; yk = cntB; }
+                    else if (KH <= rest) { Kc = (uint32_t)KH; xk = cntA; yk = H; }
+                    else { Kc = (uint32_t)rest; xk = L; yk = H; }
+                    sm.Kc = Kc; sm.xk = xk; sm.yk = yk;
+                    sm.Dn = D0;   // P(0) = 0; the owner of position xk-1 overwrites
+                    sm.Pe = PL;   // P(L + 0); the owner of position L+yk-1 overwrites
+                }
             }
             __syncthreads();
             const uint32_t Kc = sm.Kc, xk = sm.xk, yk = sm.yk;
