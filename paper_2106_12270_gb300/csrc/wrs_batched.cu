@@ -418,16 +418,21 @@ k_batched_build(const float *__restrict__ w, const uint64_t *__restrict__ off,
             // exact end state: P(xk) and P(L + yk) from the owners' prefixes
             {
                 const uint32_t px = xk, pe = L + yk;
-                if (px > 0 && (px - 1) / kPer == tid) {
+                // P at a position inside this thread's range, from its
+                // exclusive prefix and its (register-held) values
+                auto prefix_to = [&](uint32_t pos) {
                     u128 p = pre0;
-                    for (uint32_t e = b0; e < px; ++e) p += value(e, qclamp(e));
-                    sm.Dn = D0 + p;
-                }
-                if (pe > 0 && pe != L && (pe - 1) / kPer == tid) {
-                    u128 p = pre0;
-                    for (uint32_t e = b0; e < pe; ++e) p += value(e, qclamp(e));
-                    sm.Pe = p;
-                }
+                    if constexpr (kPer <= 8) {
+#pragma unroll
+                        for (uint32_t k = 0; k < kPer; ++k)
+                            if (b0 + k < pos) p += value(b0 + k, qk[k < kKeep ? k : 0]);
+                    } else {
+                        for (uint32_t e = b0; e < pos; ++e) p += value(e, qclamp(e));
+                    }
+                    return p;
+                };
+                if (px > 0 && (px - 1) / kPer == tid) sm.Dn = D0 + prefix_to(px);
+                if (pe > 0 && pe != L && (pe - 1) / kPer == tid) sm.Pe = prefix_to(pe);
             }
             // merge path over Kc buckets
             const uint32_t per_out = (Kc + BT - 1) / BT;
