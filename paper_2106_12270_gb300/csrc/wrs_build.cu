@@ -351,7 +351,10 @@ struct WarpStage {
 // memory, then compute q once per entry in list order (lane = 16
 // consecutive slots) with one warp scan; checkpoint sums are snapshots of
 // the running sum at the one slot per lane where a checkpoint can fall.  The
-// next chunk's weights are loaded while the current one is processed.
+// next chunk's weights are loaded while the current one is processed.  Full
+// chunks (every chunk but a sub-segment's last) skip the per-item bounds
+// tests, and those without a weight near the light threshold skip the
+// clamps of q.
 template <bool kAligned>
 __global__ void __launch_bounds__(kPartThreads, 3)
 k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__ P,
@@ -809,9 +812,11 @@ __global__ void k_split_ends(const BuildParams *__restrict__ P, SplitRec *__rest
 //   A(x) = floor(D'(i0+x) / 2^15) - floor(D0 / 2^15)   in [0, 2^61]
 //   B(y) = floor(E'(j0+y+1) / 2^15) - floor(D0 / 2^15) > -2^48
 // (B(0) > -Q because the split took the smallest i; B is capped at 2^62,
-// above every A: a capped heavy cannot close in the section.)  The prefix
-// sums themselves are exact (128-bit); only the stored keys are rounded, the
-// same way everywhere, so the table does not depend on the section size.
+// above every A: a capped heavy cannot close in the section.  A sentinel
+// key after the section's last heavy lies above every A as well.)  The
+// prefix sums themselves are exact (128-bit); only the stored keys are
+// rounded, the same way everywhere, so the table does not depend on the
+// section size.
 constexpr int kKeyCap62 = 62;
 
 // Shared memory: sK (keys: slot x = A(x), slot L+y+1 = B(y)) and sE (the
