@@ -18,6 +18,7 @@ function cites the part of the paper (arXiv 2106.12270) it follows:
 * ``psa``             PSA split + sweep-pack (Sec. 2.2, Sec. 4.2).
 * ``psa_prec``        the same PSA with its prefix arithmetic rounded to FP64,
                       paired FP32 or plain FP32 (precision study).
+* ``psa_plus``        PSA+ (Sec. 4): greedy packing per tile, PSA on the rest.
 * ``mass``            reconstructed mass per item (Sec. 2.2).
 * ``philox``          Philox-4x32-10 (Salmon et al., SC'11).
 * ``sample_naive``    Walker sampling, integer form (Sec. 2.2, Sec. 5).
@@ -79,6 +80,7 @@ def _load():
                 "orc_pary_search": [P, U64, P, U64, U32, P],
                 "orc_psa": [P, U64, U64, P, P, P, P, P, P, P, U32],
                 "orc_psa_prec": [P, U64, U64, ctypes.c_int, P, P],
+                "orc_psa_plus": [P, U64, U64, U64, U64, P, P, P],
                 "orc_mass": [P, P, U64, P],
                 "orc_sample_naive": [P, P, U64, U64, U64, U64, U32, U32, P],
                 "orc_sample_sectioned": [P, P, U64, U64, P, U64, U32, P],
@@ -224,6 +226,21 @@ def psa_prec(w, section: int, prec: int):
     _check(_load().orc_psa_prec(_ptr(w), n, section, prec, _ptr(prob),
                                 _ptr(alias)), "psa_prec")
     return prob[:n], alias[:n]
+
+
+def psa_plus(w, section: int, tile: int, min_items: int):
+    """PSA+ (Sec. 4 "PSA+"): greedy packing inside each tile of `tile` items
+    that holds at least `min_items` lights and heavies, then PSA (binary
+    split search, sections of `section` buckets) on the unfinished items.
+    Returns (prob f64, alias u32, number of items the greedy step closed)."""
+    w = _f32(w)
+    n = w.size
+    prob = np.zeros(max(n, 1), np.float64)
+    alias = np.zeros(max(n, 1), np.uint32)
+    greedy = np.zeros(1, np.uint64)
+    _check(_load().orc_psa_plus(_ptr(w), n, section, tile, min_items, _ptr(prob),
+                                _ptr(alias), _ptr(greedy)), "psa_plus")
+    return prob[:n], alias[:n], int(greedy[0])
 
 
 def mass(prob, alias) -> np.ndarray:

@@ -29,6 +29,8 @@
  *                         Sec. 4.2).
  *   orc_psa_prec          the same PSA with its prefix arithmetic rounded to
  *                         FP64, paired FP32 or FP32 (precision study).
+ *   orc_psa_plus          PSA+ (Sec. 4 "PSA+"): greedy packing per partition
+ *                         tile, then PSA on the unfinished items.
  *   orc_mass              reconstructed mass of each item from a table
  *                         (Sec. 2.2: every row is one bucket of W/N).
  *   orc_philox4x32_10     Philox-4x32-10 counter-based generator (Salmon,
@@ -542,6 +544,179 @@ int orc_psa(const float *w, uint64_t n, uint64_t S, double *prob,
     rc = ORC_OK;
 out:
     free(l); free(h); free(sl); free(sh); free(k); free(si); free(sj); free(sp);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* PSA+ (Sec. 4 "PSA+"): greedy packing inside each partition tile, then PSA  */
+/* on the items the greedy step did not finish.                              */
+/*                                                                           */
+/* Tile t holds items [tT, min((t+1)T, n)).  If it has at least m light and  */
+/* m heavy items, its lights and heavies (index order) are swept as in PSA:   */
+/* the current heavy with r left closes its own bucket when r <= W/N and the  */
+/* tile has a next heavy; otherwise it fills the next light bucket.  The     */
+/* sweep stops when the tile has no light left to fill or no next heavy.     */
+/* The heavy current at that point keeps its remaining weight r and, like   */
+/* every other item not yet closed, goes to the rest of the build: light iff */
+/* its current weight is <= W/N.  That rest is built by the PSA above (binary */
+/* split search, sections of S buckets) on the current weights, in index    */
+/* order.  Reading of the paper: the leftover heavy's weight and its class  */
+/* are not stated; carrying r is what keeps every bucket at W/N.            */
+/* ------------------------------------------------------------------------ */
+
+/* PSA over a list of items (ids, current weights), lights and heavies given
+ * in index order; the arithmetic of orc_psa with the binary split. */
+static int psa_rest(const uint32_t *lid, const double *lw, uint64_t nl,
+                    const uint32_t *hid, const double *hw, uint64_t nh,
+                    double avg, uint64_t S, double *prob, uint32_t *alias)
+{
+    const uint64_t n = nl + nh;
+    if (n == 0)
+        return ORC_OK;
+    double *sl = malloc((nl + 1) * sizeof *sl), *sh = malloc((nh + 1) * sizeof *sh);
+    if (!sl || !sh) {
+        free(sl); free(sh);
+        return ORC_ENOMEM;
+    }
+    sl[0] = sh[0] = 0.0;
+    for (uint64_t a = 0; a < nl; ++a)
+        sl[a + 1] = sl[a] + lw[a];
+    for (uint64_t b = 0; b < nh; ++b)
+        sh[b + 1] = sh[b] + hw[b];
+    const uint64_t nsec = (n + S - 1) / S;
+    uint64_t i_prev = 0, j_prev = 0;
+    double sp_prev = nh ? sl[0] + sh[1] - 0.0 : 0.0;
+    for (uint64_t t = 1; t <= nsec; ++t) {
+        /* the split at k = min(tS, n) */
+        uint64_t kk = t * S < n ? t * S : n;
+        uint64_t a = kk > nh ? kk - nh : 0, b = kk < nl ? kk : nl;
+        while (a < b) {
+            uint64_t m = a + (b - a) / 2;
+            if (sl[m] + sh[kk - m] - (double)kk * avg <= 0.0)
+                b = m;
+            else
+                a = m + 1;
+        }
+        const uint64_t i_end = a, j_end = kk - a;
+        const double sp = j_end < nh ? sl[a] + sh[j_end + 1] - (double)kk * avg : 0.0;
+        /* sweep section t-1 from the previous split */
+        uint64_t i = i_prev, j = j_prev;
+        double r = sp_prev;
+        while (i < i_end || j < j_end) {
+            int light_left = i < i_end;
+            int heavy_left = j < j_end;
+            if (heavy_left && (r <= avg || !light_left)) {
+                uint32_t g = hid[j];
+                double keep = r / avg;
+                prob[g] = keep < 0.0 ? 0.0 : (keep > 1.0 ? 1.0 : keep);
+                if (j + 1 < nh) {
+                    alias[g] = hid[j + 1];
+                    r = r + hw[j + 1] - avg;
+                } else {
+                    prob[g] = 1.0;
+                    alias[g] = g;
+                    r = 0.0;
+                }
+                ++j;
+            } else {
+                uint32_t lo = lid[i];
+                if (j < nh) {
+                    prob[lo] = lw[i] / avg;
+                    alias[lo] = hid[j];
+                    r = r - (avg - lw[i]);
+                } else {
+                    prob[lo] = 1.0;
+                    alias[lo] = lo;
+                }
+                ++i;
+            }
+        }
+        i_prev = i_end;
+        j_prev = j_end;
+        sp_prev = sp;
+    }
+    free(sl); free(sh);
+    return ORC_OK;
+}
+
+int orc_psa_plus(const float *w, uint64_t n, uint64_t S, uint64_t T,
+                 uint64_t m, double *prob, uint32_t *alias, uint64_t *greedy)
+{
+    double W, avg;
+    int rc = total_and_avg(w, n, &W, &avg);
+    if (rc)
+        return rc;
+    if (S == 0 || T == 0)
+        return ORC_EINVAL;
+    /* the rest: ids and current weights, lights and heavies in index order */
+    uint32_t *lid = malloc(n * sizeof *lid), *hid = malloc(n * sizeof *hid);
+    double *lw = malloc(n * sizeof *lw), *hw = malloc(n * sizeof *hw);
+    uint32_t *tl = malloc(T * sizeof *tl), *th = malloc(T * sizeof *th);
+    double *cur = malloc(n * sizeof *cur);
+    unsigned char *done = calloc(n, 1);
+    if (!lid || !hid || !lw || !hw || !tl || !th || !cur || !done) {
+        rc = ORC_ENOMEM;
+        goto out;
+    }
+    uint64_t closed = 0;
+    for (uint64_t i = 0; i < n; ++i)
+        cur[i] = (double)w[i];
+    for (uint64_t t0 = 0; t0 < n; t0 += T) {
+        const uint64_t t1 = t0 + T < n ? t0 + T : n;
+        uint64_t ntl = 0, nth = 0;
+        for (uint64_t i = t0; i < t1; ++i) {
+            if ((double)w[i] <= avg)
+                tl[ntl++] = (uint32_t)i;
+            else
+                th[nth++] = (uint32_t)i;
+        }
+        if (ntl < m || nth < m || ntl == 0 || nth == 0)
+            continue;
+        uint64_t i = 0, j = 0;
+        double r = (double)w[th[0]];
+        for (;;) {
+            if (r <= avg) {
+                if (j + 1 >= nth)
+                    break;               /* no next heavy in the tile */
+                uint32_t g = th[j];
+                double keep = r / avg;
+                prob[g] = keep < 0.0 ? 0.0 : (keep > 1.0 ? 1.0 : keep);
+                alias[g] = th[j + 1];
+                done[g] = 1;
+                ++closed;
+                r = r + (double)w[th[j + 1]] - avg;
+                ++j;
+            } else {
+                if (i >= ntl)
+                    break;               /* no light left to fill */
+                uint32_t lo = tl[i];
+                prob[lo] = (double)w[lo] / avg;
+                alias[lo] = th[j];
+                done[lo] = 1;
+                ++closed;
+                r = r - (avg - (double)w[lo]);
+                ++i;
+            }
+        }
+        cur[th[j]] = r;                  /* the heavy left current */
+    }
+    uint64_t nl = 0, nh = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        if (done[i])
+            continue;
+        if (cur[i] <= avg) {
+            lid[nl] = (uint32_t)i;
+            lw[nl++] = cur[i];
+        } else {
+            hid[nh] = (uint32_t)i;
+            hw[nh++] = cur[i];
+        }
+    }
+    rc = psa_rest(lid, lw, nl, hid, hw, nh, avg, S, prob, alias);
+    if (greedy)
+        *greedy = closed;
+out:
+    free(lid); free(hid); free(lw); free(hw); free(tl); free(th); free(cur); free(done);
     return rc;
 }
 

@@ -404,3 +404,69 @@ def test_precision_study_prefix_arithmetic(kind):
         p32 = prob.astype(np.float32).astype(np.float64)
         errs.append(oracle.mass_error(p32, alias, w, W))
     assert errs[0] <= 1e-6 and errs[1] <= 1e-5 and errs[2] > 1e-3, errs
+
+
+# --------------------------------------------------------------------------
+# PSA+ (Sec. 4 "PSA+"): greedy packing per tile, then PSA on the rest
+# --------------------------------------------------------------------------
+
+def test_psa_plus_golden():
+    g = read("psa_plus_worked_1313.txt")
+    w = np.array([float(x) for x in g["weights"].split()], np.float32)
+    prob, alias, greedy = oracle.psa_plus(w, 1024, int(g["tile"]), int(g["min_items"]))
+    assert greedy == int(g["greedy"])
+    assert [Fraction(p).limit_denominator(64) for p in prob] == fractions(g["prob"])
+    assert alias.tolist() == ints(g["alias"])
+    assert [Fraction(m).limit_denominator(64) for m in oracle.mass(prob, alias)] == \
+        fractions(g["mass"])
+
+
+@pytest.mark.parametrize("kind", ["uniform", "zipf", "exponential", "gamma"])
+def test_psa_plus_without_greedy_step_is_psa(kind):
+    """With no tile eligible for greedy packing, PSA+ is PSA (binary split),
+    bit for bit."""
+    w = inputs.by_name(kind, 20011, 3)
+    ref = oracle.psa(w, 1024)
+    prob, alias, greedy = oracle.psa_plus(w, 1024, 4096, 10**9)
+    assert greedy == 0
+    assert np.array_equal(prob, ref["prob"]) and np.array_equal(alias, ref["alias"])
+
+
+def test_psa_plus_brute_force_masses():
+    """Every weight vector over {0, 1/2, 1, 2, 3}^N, N <= 4, every tile size
+    and threshold: each item's reconstructed mass is N w_i / W."""
+    vals = [0.0, 0.5, 1.0, 2.0, 3.0]
+    for N in range(1, 5):
+        for ws in itertools.product(vals, repeat=N):
+            w = np.array(ws, np.float32)
+            if w.sum() == 0:
+                continue
+            W = float(w.astype(np.float64).sum())
+            want = w.astype(np.float64) * N / W
+            for T in sorted({1, 2, 3, N}):
+                for m in (1, 2):
+                    for S in (1, 2, 1024):
+                        prob, alias, _ = oracle.psa_plus(w, S, T, m)
+                        assert np.all((prob >= 0) & (prob <= 1)) and np.all(alias < N)
+                        got = oracle.mass(prob, alias)
+                        assert np.allclose(got, want, rtol=0, atol=1e-12), (ws, T, m, S)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "zipf", "exponential", "gamma"])
+@pytest.mark.parametrize("tile, m", [(64, 1), (512, 8), (4096, 1)])
+def test_psa_plus_masses_random(kind, tile, m):
+    w = inputs.by_name(kind, 100_003, 9)
+    W = oracle.exact_sum(w)
+    prob, alias, greedy = oracle.psa_plus(w, 1024, tile, m)
+    assert 0 < greedy <= w.size
+    assert np.all((prob >= 0) & (prob <= 1)) and np.all(alias < w.size)
+    e = oracle.expected_mass(w, W)
+    assert np.max(np.abs(oracle.mass(prob, alias) - e) / np.maximum(1.0, e)) <= 1e-9
+
+
+def test_psa_plus_greedy_share_uniform():
+    """Sec. 6 (PSA+): with uniform random weights the greedy step finishes
+    around 90% of the items on GPU-sized tiles."""
+    w = inputs.uniform(1_000_000, 1)
+    _, _, greedy = oracle.psa_plus(w, 1024, 512, 1)
+    assert greedy / w.size >= 0.85
