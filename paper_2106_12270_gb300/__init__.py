@@ -24,6 +24,7 @@ __all__ = [
     "WrsError", "lib", "config", "build_workspace_bytes", "build_layout", "build_rows",
     "step_total", "step_partition", "step_split", "step_pack", "step_info", "sample_rows",
     "parse_info", "INFO_BYTES", "BatchTuning", "ROW_BYTES", "Builder", "rows_to_numpy",
+    "build_plus_workspace_bytes", "build_rows_plus",
 ]
 
 OK, EINVAL, EZEROSUM, ENONFINITE, ENOMEM, ETIMEOUT, ECUDA, EBUSY, ENOTFOUND = range(9)
@@ -108,6 +109,8 @@ def lib():
                 "wrs_sample_rows": (I, [P, U64, U64, U64, U64, U32, U32, P, P]),
                 "wrs_diag_random_gather": (I, [P, U64, U64, U64, I, P, P]),
                 "wrs_diag_philox": (I, [U64, U64, P, P]),
+                "wrs_build_plus_workspace_bytes": (I, [U64, P, ctypes.POINTER(U64)]),
+                "wrs_build_rows_plus": (I, [P, U64, P, P, U64, P, U32, P, ctypes.POINTER(U64), P]),
                 "wrs_sample_sections": (I, [U64, U32, ctypes.POINTER(U64)]),
                 "wrs_sample_auto_choice": (I, [U64, U64, ctypes.POINTER(U32),
                                                ctypes.POINTER(U32)]),
@@ -445,6 +448,28 @@ def diag_random_gather(rows, nrows: int, count: int, seed: int, flavor: int, out
     """Enqueue the random-gather probe (measurement support, not the method)."""
     _check(lib().wrs_diag_random_gather(_ptr(rows), nrows, count, seed, flavor, _ptr(out),
                                         _stream(stream)), "wrs_diag_random_gather")
+
+
+def build_plus_workspace_bytes(n: int, cfg: Config | None = None) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().wrs_build_plus_workspace_bytes(n, _cfg(cfg), ctypes.byref(out)),
+           "wrs_build_plus_workspace_bytes")
+    return out.value
+
+
+def build_rows_plus(w, rows, ws, info, cfg: Config | None = None, min_items: int = 1,
+                    stream=None) -> int:
+    """PSA+ build (Sec. 4): w (float32 [n], device) -> rows (int64 [n],
+    device); greedy packing in chunks with at least min_items light and heavy
+    items, PSA on the rest.  Returns how many items the greedy step finished;
+    synchronises the stream once."""
+    n = w.numel()
+    greedy = ctypes.c_uint64()
+    _check(lib().wrs_build_rows_plus(_ptr(w), n, _ptr(rows), _ptr(ws),
+                                     ws.numel() * ws.element_size(), _cfg(cfg), min_items,
+                                     _ptr(info), ctypes.byref(greedy),
+                                     _stream(stream)), "wrs_build_rows_plus")
+    return greedy.value
 
 
 def diag_philox(count: int, seed: int, out, stream=None):

@@ -30,6 +30,12 @@ cudaError_t launch_random_gather(const void *, uint64_t, uint64_t, uint64_t, int
                                  cudaStream_t);
 cudaError_t launch_philox_rate(uint64_t, uint64_t, uint32_t *, cudaStream_t);
 
+struct PlusLayout;
+uint64_t plus_workspace_bytes(uint64_t n, uint32_t S);
+cudaError_t launch_build_plus_ws(const float *d_w, uint64_t n, wrs_row *d_rows, unsigned char *ws,
+                                 uint32_t S, uint32_t split_method, uint32_t min_items,
+                                 wrs_build_info *d_info, uint64_t *h_rest, cudaStream_t st);
+
 thread_local int g_last_cuda = 0;
 
 int cuda_status(cudaError_t e) {
@@ -184,6 +190,34 @@ int wrs_build_rows(const float *d_w, uint64_t n, wrs_row *d_rows, void *d_ws, ui
     if (!e) e = launch_split(n, ws, L, c.section_size, c.split_method, st);
     if (!e) e = launch_pack(n, d_rows, ws, L, c.section_size, st);
     if (!e) e = launch_info(ws, L, d_info, st);
+    return cuda_status(e);
+}
+
+int wrs_build_plus_workspace_bytes(uint64_t n, const wrs_config *cfg, uint64_t *bytes) {
+    if (!bytes || n == 0 || n > kMaxN) return WRS_EINVAL;
+    wrs_config c;
+    int rc = resolve_cfg(cfg, &c);
+    if (rc) return rc;
+    *bytes = plus_workspace_bytes(n, c.section_size);
+    return WRS_OK;
+}
+
+int wrs_build_rows_plus(const float *d_w, uint64_t n, wrs_row *d_rows, void *d_ws,
+                        uint64_t ws_bytes, const wrs_config *cfg, uint32_t min_items,
+                        wrs_build_info *d_info, uint64_t *greedy_items, void *stream) {
+    if (n == 0 || n > kMaxN) return WRS_EINVAL;
+    wrs_config c;
+    int rc = resolve_cfg(cfg, &c);
+    if (rc) return rc;
+    if (!d_ws || ((uintptr_t)d_ws & 255u) || ws_bytes < plus_workspace_bytes(n, c.section_size))
+        return WRS_EINVAL;
+    if (!d_w || ((uintptr_t)d_w & 3u) || !d_rows || ((uintptr_t)d_rows & 7u) || !d_info)
+        return WRS_EINVAL;
+    uint64_t greedy = 0;
+    cudaError_t e = launch_build_plus_ws(d_w, n, d_rows, (unsigned char *)d_ws, c.section_size,
+                                         c.split_method, min_items, d_info, &greedy,
+                                         (cudaStream_t)stream);
+    if (greedy_items) *greedy_items = e ? 0 : greedy;
     return cuda_status(e);
 }
 

@@ -187,16 +187,6 @@ k_sum(const float *__restrict__ w, uint64_t n, u128 *__restrict__ bins_out,
 // ===========================================================================
 
 
-// The partition works on chunks of kChunk items; a warp owns a contiguous
-// run of chunks (a sub-segment).  Sub-segment s of NS covers chunks
-// [s*C/NS, (s+1)*C/NS) of the C chunks.
-__device__ __forceinline__ void sub_range(uint32_t s, uint32_t NS, uint64_t C, uint64_t n,
-                                          uint64_t &a, uint64_t &b) {
-    uint64_t c0 = (uint64_t)s * C / NS, c1 = (uint64_t)(s + 1) * C / NS;
-    a = c0 * kChunk;
-    b = min(c1 * kChunk, n);
-    if (a > b) a = b;
-}
 
 // Per sub-segment (one warp each, coalesced 16-byte loads): the number of
 // light items and the sum of q over all its items (unclamped).
@@ -1086,6 +1076,23 @@ uint32_t num_segments(uint64_t n) {
     if (g > (uint64_t)kMaxSegs - 1) g = kMaxSegs - 1;
     if (g > C) g = C;
     return (uint32_t)(g ? g : 1);
+}
+
+// The light counts and the q sum of every sub-segment, then Q and the light
+// offsets (the part of the partition that PSA+ shares).
+cudaError_t launch_count(const float *d_w, uint64_t n, unsigned char *ws, const Layout &L,
+                         cudaStream_t st) {
+    BuildParams *P = reinterpret_cast<BuildParams *>(ws + L.params);
+    auto *cnt = reinterpret_cast<uint32_t *>(ws + L.seg_cnt);
+    auto *segq = reinterpret_cast<uint64_t *>(ws + L.seg_q);
+    auto *loff = reinterpret_cast<uint64_t *>(ws + L.seg_loff);
+    const uint64_t C = (n + kChunk - 1) / kChunk;
+    const uint32_t NS = num_segments(n);
+    const unsigned blocks = (NS + kPartThreads / 32 - 1) / (kPartThreads / 32);
+    const int aligned = ((uintptr_t)d_w % 16) == 0;
+    k_count<<<blocks, kPartThreads, 0, st>>>(d_w, n, P, cnt, segq, C, NS, aligned);
+    k_qsum<<<1, 1024, 0, st>>>(P, cnt, segq, loff, NS, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_partition(const float *d_w, uint64_t n, unsigned char *ws, const Layout &L,

@@ -9,6 +9,17 @@ namespace wrs {
 __device__ __forceinline__ int pad32(int e) { return e + (e >> 5); }
 __device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
 
+// The partition works on chunks of kChunk items; a warp owns a contiguous
+// run of chunks (a sub-segment).  Sub-segment s of NS covers chunks
+// [s*C/NS, (s+1)*C/NS) of the C chunks.
+__device__ __forceinline__ void sub_range(uint32_t s, uint32_t NS, uint64_t C, uint64_t n,
+                                          uint64_t &a, uint64_t &b) {
+    uint64_t c0 = (uint64_t)s * C / NS, c1 = (uint64_t)(s + 1) * C / NS;
+    a = c0 * kChunk;
+    b = min(c1 * kChunk, n);
+    if (a > b) a = b;
+}
+
 // Exponent band of an FP32 weight for the exact sum: a weight m * 2^(e'-150)
 // (e' = max(biased exponent, 1)) is added to band e'/24 as m << (e' mod 24),
 // a value below 2^47.  Sets error bits for NaN/Inf and negative weights.
