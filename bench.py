@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the host-side mass check of the timed table")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-psa-plus", action="store_true",
+                    help="skip the PSA+ build (Sec. 4) timed on the same table")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--build-only", action="store_true",
                     help="time the build alone (no sampling legs, batched or serving)")
@@ -404,6 +406,8 @@ def run_gpu(args):
         probe[flavor] = a.elapsed_time(b)
     probe_ms = min(probe.values()) if probe else float("nan")
 
+    psa_plus = None if (args.no_psa_plus or args.build_only) else \
+        run_psa_plus(args, w, w_host, n, cfg, build_ms)
     batched = None if args.no_batched else run_batched(args, world, rank)
     serving_res = None if args.no_serving else run_serving(args, rank)
     heatmap = run_sampler_heatmap(args) if args.sampler_heatmap else None
@@ -452,6 +456,7 @@ def run_gpu(args):
             "samples_per_s": (world * count / (sample_ms / 1e3)) if count else None,
             "sectioned_sampling": sec,
             "batched": batched,
+            "psa_plus": psa_plus,
             "serving": serving_res,
             **({"sampler_heatmap": heatmap} if heatmap is not None else {}),
             **({"ablation": ablation} if ablation is not None else {}),
@@ -648,6 +653,51 @@ def run_sampler_heatmap(args):
         del w, rows, b
         torch.cuda.empty_cache()
     return {"weights": "uniform [0,1) (seed 1)", "unit": "ms", "cells": cells}
+
+
+def run_psa_plus(args, w, w_host, n, cfg, psa_build_ms):
+    """PSA+ (Sec. 4 "PSA+") on the bench table: greedy packing per 512-item
+    partition chunk, PSA on the rest.  Each call reads the rest's size back
+    once (a host sync), which the events around it include."""
+    import numpy as np
+    import torch
+
+    import paper_2106_12270_gb300 as wrs
+
+    rows = torch.empty(n, dtype=torch.int64, device="cuda")
+    info = torch.zeros(wrs.INFO_BYTES, dtype=torch.uint8, device="cuda")
+    ws = torch.empty(wrs.build_plus_workspace_bytes(n, cfg), dtype=torch.uint8, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        greedy = wrs.build_rows_plus(w, rows, ws, info, cfg, 1)
+    torch.cuda.synchronize()
+    st = wrs.parse_info(info)["status"]
+    if st != wrs.OK:
+        raise RuntimeError(f"PSA+ build failed: status {st}")
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        wrs.build_rows_plus(w, rows, ws, info, cfg, 1)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = float(np.mean(ts))
+    res = {"ms": ms, "items_per_s": n / (ms / 1e3), "min_items": 1, "tile": 512,
+           "greedy_items": greedy, "greedy_fraction": greedy / n,
+           "speedup_vs_psa": psa_build_ms / ms}
+    if not args.no_accuracy:
+        raw = rows.cpu().numpy().view(np.uint32).reshape(-1, 2)
+        prob = raw[:, 0].view(np.float32).astype(np.float64)
+        mass = prob + np.bincount(raw[:, 1], weights=1.0 - prob, minlength=n)
+        wd = w_host.astype(np.float64)
+        expect = wd * (n / float(np.sum(wd)))
+        res["max_mass_error"] = float((np.abs(mass - expect) / np.maximum(1.0, expect)).max())
+        del raw, prob, mass, wd, expect
+    del rows, info, ws
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_ablation(args, w, n):

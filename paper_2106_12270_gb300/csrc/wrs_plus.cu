@@ -18,9 +18,10 @@
 //                            those buckets (merge path, rows by item index),
 //                            and append the items left over, in index order,
 //                            to the warp's region of the rest arrays.  The
-//                            heavy current at the stop keeps its exact
-//                            remaining excess r = E'(y+1) - D'(x), carried as
-//                            the weight (Q + r) / (N 2^S) rounded to FP32.
+//                            heavy current at the stop keeps its remaining
+//                            excess r = E'(y+1) - D'(x) (read from the two
+//                            keys it stopped at, within 2^-46 of a bucket),
+//                            carried as the weight (Q + r) / (N 2^S) in FP32.
 //   k_rest_scan, k_rest_copy the leftover counts of the sub-segments, scanned;
 //                            the leftovers copied to one dense array.
 //   PSA on the rest          the unchanged PSA pipeline on the dense weights.
@@ -28,7 +29,8 @@
 //
 // Every sum of q fits 64 bits (they all add up to Q < 2^63), so the chunk's
 // prefixes are u64 q sums; D'(x) = x Q - N sum_l(x) and E'(y) = N sum_h(y) -
-// y Q are formed in 128 bits where needed.
+// y Q are 128-bit values, formed once per lane and then stepped by one
+// item's deficit (64 bits) or excess.
 #include "wrs_device.cuh"
 
 namespace wrs {
@@ -56,6 +58,13 @@ struct GreedyStage {
 
 __device__ __forceinline__ uint32_t pk16g(uint32_t e) { return e + (e >> 4); }
 
+// a * b as 128 bits from two 32x32 -> 64 products.
+__device__ __forceinline__ u128 mul32x64(uint32_t a, uint64_t b) {
+    const uint64_t lo = (uint64_t)a * (uint32_t)b;
+    const uint64_t hi = (uint64_t)a * (uint32_t)(b >> 32);
+    return ((u128)hi << 32) + lo;
+}
+
 template <bool kAligned>
 __global__ void __launch_bounds__(kGreedyThreads, 4)
 k_greedy(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__ P,
@@ -67,7 +76,6 @@ k_greedy(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict_
     const uint32_t s = blockIdx.x * (kGreedyThreads / 32) + (threadIdx.x >> 5);
     if (s >= NS) return;
     GreedyStage &sm = stage[threadIdx.x >> 5];
-    const QScale qsc = qscale(P->qshift);
     const uint64_t Q = P->Q, Qn = P->Qn;
     const uint32_t N = (uint32_t)n;
     const float lmax = P->light_max, inv_avg = P->inv_avg;
@@ -147,21 +155,18 @@ k_greedy(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict_
         float wres = 0.f;   // the carried weight of heavy yk (when elig)
         if (elig) {
             const uint32_t hstart = kChunk - tnh;
-            auto qlight = [&](uint32_t slot) {
-                const uint64_t q = fixed_q(sm.e[pad16(slot)].w, qsc);
-                return q > Qn ? Qn : q;
-            };
-            auto qheavy = [&](uint32_t slot) {
-                const uint64_t q = fixed_q(sm.e[pad16(slot)].w, qsc);
-                return q <= Qn ? Qn + 1 : q;
-            };
-            // lane sums of light q and heavy q over its slots, then scans
+            const int qshift = P->qshift;
+            // q of this lane's slots (integer form: the conversion to 64 bits
+            // would occupy the FP64 pipe), clamped by class; lane sums
+            uint64_t qv[kPartItems];
             uint64_t accL = 0, accH = 0;
 #pragma unroll
             for (int k = 0; k < kPartItems; ++k) {
                 const uint32_t slot = (uint32_t)(s0 + k);
-                if (slot < tl) accL += qlight(slot);
-                else if (slot >= hstart) accH += qheavy(slot);
+                const uint64_t q = fixed_q_bits(sm.e[pad16(slot)].w, qshift);
+                qv[k] = 0;
+                if (slot < tl) { qv[k] = q > Qn ? Qn : q; accL += qv[k]; }
+                else if (slot >= hstart) { qv[k] = q <= Qn ? Qn + 1 : q; accH += qv[k]; }
             }
             uint64_t incL = accL, incH = accH;
 #pragma unroll
@@ -172,27 +177,30 @@ k_greedy(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict_
             }
             const uint64_t exL = incL - accL, exH = incH - accH;
             const uint64_t THq = __shfl_sync(0xffffffffu, incH, 31);
-            // keys: A(x) = floor(D'(x) / 2^15), D'(x) = x Q - N sum_l(x), at slot x;
-            // B(y) = floor(E'(y+1) / 2^15), E'(y+1) = N sum_h(y+1) - (y+1) Q,
-            // at slot tl + 1 + y (heavy y sits at list slot kChunk - 1 - y, so
-            // its sum_h(y+1) = THq - (heavy q before that slot))
+            // keys: A(x) = floor(D'(x) / 2^15), D'(x) = x Q - N sum_l(x), at
+            // slot x; B(y) = floor(E'(y+1) / 2^15), E'(y+1) = N sum_h(y+1) -
+            // (y+1) Q, at slot tl + 1 + y.  Heavy y sits at list slot
+            // kChunk - 1 - y, so walking the slots upwards walks y down:
+            // each light adds its deficit Q - N q to D', each heavy takes its
+            // excess N q - Q off E'.  Only the lane's starting values need
+            // full products.
             {
-                uint64_t rl = exL, rh = exH;
                 if (lane == 0) sm.key[pk16g(0)] = 0;
+                u128 D = mul32x64((uint32_t)s0, Q) - mul32x64(N, exL);   // D'(s0)
+                const uint32_t s1 = (uint32_t)s0 > hstart ? (uint32_t)s0 : hstart;
+                // E'(y+1) of the lane's first heavy slot s1 (y + 1 = kChunk - s1)
+                u128 E = mul32x64(N, THq - exH) - mul32x64(kChunk - s1, Q);
 #pragma unroll
                 for (int k = 0; k < kPartItems; ++k) {
                     const uint32_t slot = (uint32_t)(s0 + k);
                     if (slot < tl) {
-                        rl += qlight(slot);
-                        const u128 D = (u128)(slot + 1) * Q - (u128)N * rl;
+                        D += Q - (uint64_t)N * qv[k];   // N q <= Q: 64 bits
                         sm.key[pk16g(slot + 1)] = (int64_t)(D >> kKeyShift);
                     } else if (slot >= hstart) {
-                        const uint32_t y = kChunk - 1 - slot;
-                        const u128 E = (u128)N * (THq - rh) - (u128)(y + 1) * Q;
                         const u128 v = E >> kKeyShift;
-                        sm.key[pk16g(tl + 1 + y)] =
+                        sm.key[pk16g(tl + 1 + (kChunk - 1 - slot))] =
                             v < ((u128)1 << 62) ? (int64_t)v : ((int64_t)1 << 62);
-                        rh += qheavy(slot);
+                        E -= mul32x64(N, qv[k]) - Q;
                     }
                 }
             }
@@ -239,53 +247,56 @@ k_greedy(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict_
                 }
                 uint32_t x = lo, y = d0 - lo;
                 int64_t av = Av(x), bv = Bv(y);
+                // hcur: item of heavy y, the one that fills the next light
+                uint32_t hcur = sm.e[pad16(kChunk - 1 - y)].item;
+#pragma unroll
                 for (int k = 0; k < kPartItems; ++k) {
-                    if (d0 + k >= Kc) break;
-                    // inside the reach a filled light exists (x < tl) unless
-                    // the heavy closes, and a closing heavy has a next heavy
-                    const bool heavy = bv <= av;
-                    uint32_t item, alias;
-                    float prob;
-                    if (heavy) {
-                        item = sm.e[pad16(kChunk - 1 - y)].item;
-                        alias = sm.e[pad16(kChunk - 2 - y)].item;
-                        prob = fminf(fmaxf(1.0f - __ll2float_rn(av - bv) * invQk, 0.0f), 1.0f);
-                        ++y;
-                        bv = Bv(y);
-                    } else {
-                        const Entry ep = sm.e[pad16(x)];
-                        item = ep.item;
-                        alias = sm.e[pad16(kChunk - 1 - y)].item;
-                        prob = fminf(ep.w * inv_avg, 1.0f);
-                        ++x;
-                        av = Av(x);
+                    if (d0 + k < Kc) {
+                        // inside the reach a closing heavy has a next heavy
+                        // and a filled light exists (x < tl)
+                        const bool heavy = bv <= av;
+                        // one entry load per step: the closed light, or the
+                        // heavy after the closed one
+                        const Entry ld = sm.e[pad16(heavy ? kChunk - 2 - y : x)];
+                        const uint32_t item = heavy ? hcur : ld.item;
+                        const uint32_t alias = heavy ? ld.item : hcur;
+                        const float prob =
+                            heavy ? fminf(fmaxf(1.0f - __ll2float_rn(av - bv) * invQk, 0.0f), 1.0f)
+                                  : fminf(ld.w * inv_avg, 1.0f);
+                        rows[item] = make_uint2(__float_as_uint(prob), alias);
+                        const int64_t v = sm.key[pk16g(heavy ? tl + 2 + y : x + 1)];
+                        if (heavy) { ++y; bv = v; hcur = ld.item; }
+                        else { ++x; av = v; }
                     }
-                    rows[item] = make_uint2(__float_as_uint(prob), alias);
                 }
             }
-            // the exact remaining excess of heavy yk: r = E'(yk+1) - D'(xk);
-            // sum_l(xk) and sum_h(yk+1) from the lanes that own those slots
-            uint64_t pl = 0, ph = 0;
-            {
-                const uint32_t ownL = xk == 0 ? 0u : (xk - 1) / kPartItems;
-                if (xk > 0 && (uint32_t)lane == ownL) {
-                    pl = exL;
-                    for (uint32_t slot = (uint32_t)s0; slot < xk; ++slot) pl += qlight(slot);
+            // the remaining excess of heavy yk, r = E'(yk+1) - D'(xk), from
+            // the two keys the sweep stopped at: within 2^15 units of the
+            // exact value (2^-46 of a bucket), far below the FP32 rounding
+            // of the carried weight.  A key at the cap (E' >= 2^77) takes
+            // the exact sums instead.
+            const int64_t bk = Bv(yk), ak = Av(xk);
+            double qrem;   // N q' of the remaining weight
+            if (bk < ((int64_t)1 << 62)) {
+                qrem = (double)Q + (double)(bk - ak) * (double)(1u << kKeyShift);
+            } else {
+                uint64_t pl = 0, ph = 0;
+#pragma unroll
+                for (int k = 0; k < kPartItems; ++k) {
+                    const uint32_t slot = (uint32_t)(s0 + k);
+                    const uint64_t q = fixed_q_bits(sm.e[pad16(slot)].w, qshift);
+                    if (slot < xk) pl += q > Qn ? Qn : q;   // lights below xk
+                    if (slot >= hstart && slot < kChunk - 1 - yk) ph += q <= Qn ? Qn + 1 : q;
                 }
-                pl = __shfl_sync(0xffffffffu, pl, (int)ownL);
-                const uint32_t sy = kChunk - 1 - yk;   // heavy yk's list slot
-                const uint32_t ownH = sy / kPartItems;
-                if ((uint32_t)lane == ownH) {
-                    ph = exH;
-                    for (uint32_t slot = (uint32_t)s0; slot < sy; ++slot)
-                        if (slot >= hstart) ph += qheavy(slot);
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) {
+                    pl += __shfl_xor_sync(0xffffffffu, pl, d);
+                    ph += __shfl_xor_sync(0xffffffffu, ph, d);
                 }
-                ph = __shfl_sync(0xffffffffu, ph, (int)ownH);
+                const __int128 Dx = (__int128)(mul32x64(xk, Q) - mul32x64(N, pl));
+                const __int128 Ey = (__int128)mul32x64(N, THq - ph) - (__int128)mul32x64(yk + 1, Q);
+                qrem = (double)Q + (double)(Ey - Dx);
             }
-            const __int128 Dx = (__int128)((u128)xk * Q) - (__int128)((u128)N * pl);
-            const __int128 Ey = (__int128)((u128)N * (THq - ph)) - (__int128)((u128)(yk + 1) * Q);
-            const __int128 r = Ey - Dx;
-            const double qrem = (double)Q + (double)r;   // N q' of the remaining weight
             wres = (float)(qrem > 0.0 ? qrem * wscale : 0.0);
         }
         // ---- the items left over, in index order, to this sub-segment's region

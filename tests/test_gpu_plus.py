@@ -164,3 +164,18 @@ def test_plus_large():
     assert mass_err(w, prob, alias) <= MASS_TOL
     _, _, g_orc = oracle.psa_plus(w, wrs.config().section_size, TILE, 1)
     assert abs(greedy - g_orc) <= greedy_tol(n), (greedy, g_orc)
+
+
+@pytest.mark.parametrize("kind,pos", [("uniform", 777), ("exponential", 1000)])
+def test_plus_dominant_heavy(kind, pos):
+    # one item holding half the weight: its excess key is past the 64-bit cap
+    # (E' >= 2^77), so the carried weight comes from the exact sums (with
+    # exponential weights other heavies of its chunk close before it)
+    n = (1 << 20) + 5
+    w = inputs.by_name(kind, n, 91)
+    w[pos] = np.float32(w.astype(np.float64).sum())
+    prob, alias, inf, greedy = build_plus(w, 1)
+    assert inf["status"] == wrs.OK
+    assert mass_err(w, prob, alias) <= MASS_TOL
+    _, _, g_orc = oracle.psa_plus(w, wrs.config().section_size, TILE, 1)
+    assert abs(greedy - g_orc) <= greedy_tol(n), (greedy, g_orc)
