@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--samples", type=int, default=1_000_000_000)
     ap.add_argument("--section", type=int, default=1024)
     ap.add_argument("--dist", default="zipf",
-                    choices=["zipf", "uniform", "exponential", "gamma"],
+                    choices=["zipf", "zipf0.5", "uniform", "exponential", "gamma"],
                     help="weights of the single table (default: shuffled power law)")
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -235,7 +235,8 @@ def run_gpu(args):
     n, count = args.n, args.samples
     cfg = wrs.config(args.section)
     seed = replicas.rank_seed(args.seed if args.seed is not None else
-                              {"zipf": 3, "uniform": 1, "exponential": 4, "gamma": 7}[args.dist],
+                              {"zipf": 3, "zipf0.5": 5, "uniform": 1, "exponential": 4,
+                               "gamma": 7}[args.dist],
                               rank)
     w_host = inputs.by_name(args.dist, n, seed)
     w = torch.from_numpy(w_host).cuda()
@@ -720,7 +721,27 @@ def run_ablation(args, w, n):
             res.append({"split": mname, "section": sec, "split_ms": split_ms, "pack_ms": pack_ms})
             del ws
             torch.cuda.empty_cache()
-    return {"n": n, "dist": args.dist, "steps": res}
+    # pack designs of Sec. 4.2 (Fig. 3) on the same split state; all write
+    # the same rows
+    cfg = wrs.config(args.section)
+    ws = torch.empty(wrs.build_workspace_bytes(n, cfg), dtype=torch.uint8, device="cuda")
+    wrs.step_total(w, ws, cfg)
+    wrs.step_partition(w, ws, cfg)
+    wrs.step_split(n, ws, cfg)
+    variants = []
+    for v, name in ((0, "one thread per section, weights gathered by index"),
+                    (1, "one thread per section, weights in the lists"),
+                    (2, "one warp per section, staged in shared memory, one lane sweeps"),
+                    (3, "merge path over the section (production pack)")):
+        if v == 3:
+            fn = lambda: wrs.step_pack(n, rows, ws, cfg)
+        else:
+            fn = lambda v=v: wrs.diag_pack_variant(w, n, rows, ws, cfg, v)
+        variants.append({"variant": v, "design": name, "pack_ms": _time_ms(fn)})
+    del ws
+    torch.cuda.empty_cache()
+    return {"n": n, "dist": args.dist, "steps": res, "section": args.section,
+            "pack_variants": variants}
 
 
 def run_serving(args, rank):

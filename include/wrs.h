@@ -458,6 +458,24 @@ int wrs_server_destroy(wrs_server *s);
 int wrs_diag_random_gather(const wrs_row *d_rows, uint64_t nrows, uint64_t count,
                            uint64_t seed, int flavor, uint32_t *d_out, void *stream);
 
+/* Pack variants of Sec. 4.2 (Fig. 3), for measurement: the sweep-pack step
+ * (wrs_step_pack) done by a sequential sweep per section instead of the
+ * merge-path pack.  Same contract as wrs_step_pack: d_ws holds a build's
+ * state after wrs_step_split with the same n and cfg; every variant writes
+ * the rows wrs_step_pack writes, bit for bit.
+ *   variant 0: one thread per section, list entries read from global
+ *              memory, each weight gathered from d_w by the item index
+ *              (d_w: the build's weights, device, 4-byte aligned);
+ *   variant 1: the same with the weight read from the list entry (d_w may
+ *              be NULL);
+ *   variant 2: one warp per section stages its entries in shared memory,
+ *              one lane sweeps them (d_w may be NULL).
+ * Errors: WRS_EINVAL for another variant or misaligned pointers, otherwise
+ * as wrs_step_pack. */
+int wrs_diag_pack_variant(const float *d_w, uint64_t n, wrs_row *d_rows, void *d_ws,
+                          uint64_t ws_bytes, const wrs_config *cfg, uint32_t variant,
+                          void *stream);
+
 /* Philox-rate probe (measures the hardware; no counterpart in the paper):
  * ceil(count/2) Philox-4x32-10 calls, call c on counter
  * (c_lo, c_hi, 0, WRS_TAG_DIAG) under key (seed_lo, seed_hi), writing

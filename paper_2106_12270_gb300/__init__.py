@@ -109,6 +109,7 @@ def lib():
                 "wrs_sample_rows": (I, [P, U64, U64, U64, U64, U32, U32, P, P]),
                 "wrs_diag_random_gather": (I, [P, U64, U64, U64, I, P, P]),
                 "wrs_diag_philox": (I, [U64, U64, P, P]),
+                "wrs_diag_pack_variant": (I, [P, U64, P, P, U64, P, U32, P]),
                 "wrs_build_plus_workspace_bytes": (I, [U64, P, ctypes.POINTER(U64)]),
                 "wrs_build_rows_plus": (I, [P, U64, P, P, U64, P, U32, P, ctypes.POINTER(U64), P]),
                 "wrs_sample_sections": (I, [U64, U32, ctypes.POINTER(U64)]),
@@ -470,6 +471,15 @@ def build_rows_plus(w, rows, ws, info, cfg: Config | None = None, min_items: int
                                      _ptr(info), ctypes.byref(greedy),
                                      _stream(stream)), "wrs_build_rows_plus")
     return greedy.value
+
+
+def diag_pack_variant(w, n: int, rows, ws, cfg: Config | None = None, variant: int = 1,
+                      stream=None):
+    """Pack step by one of the paper's sequential pack designs (Sec. 4.2,
+    Fig. 3) on a workspace after step_split; same rows as step_pack."""
+    _check(lib().wrs_diag_pack_variant(_ptr(w), n, _ptr(rows),
+                                       _ptr(ws), ws.numel() * ws.element_size(), _cfg(cfg),
+                                       variant, _stream(stream)), "wrs_diag_pack_variant")
 
 
 def diag_philox(count: int, seed: int, out, stream=None):

@@ -29,6 +29,8 @@ cudaError_t launch_sample_batched(const wrs_row *, const uint64_t *, uint32_t, c
 cudaError_t launch_random_gather(const void *, uint64_t, uint64_t, uint64_t, int, uint32_t *,
                                  cudaStream_t);
 cudaError_t launch_philox_rate(uint64_t, uint64_t, uint32_t *, cudaStream_t);
+cudaError_t launch_pack_variant(const float *, uint64_t, wrs_row *, unsigned char *, const Layout &,
+                                uint32_t, uint32_t, cudaStream_t);
 
 struct PlusLayout;
 uint64_t plus_workspace_bytes(uint64_t n, uint32_t S);
@@ -511,6 +513,19 @@ int wrs_diag_random_gather(const wrs_row *d_rows, uint64_t nrows, uint64_t count
     if (flavor < 0 || flavor > 2) return WRS_EINVAL;
     return cuda_status(
         launch_random_gather(d_rows, nrows, count, seed, flavor, d_out, (cudaStream_t)stream));
+}
+
+int wrs_diag_pack_variant(const float *d_w, uint64_t n, wrs_row *d_rows, void *d_ws,
+                          uint64_t ws_bytes, const wrs_config *cfg, uint32_t variant,
+                          void *stream) {
+    wrs_config c;
+    Layout L;
+    int rc = prep(n, d_ws, ws_bytes, cfg, &c, &L);
+    if (rc) return rc;
+    if (variant > 2 || !d_rows || ((uintptr_t)d_rows & 7u)) return WRS_EINVAL;
+    if (variant == 0 && (!d_w || ((uintptr_t)d_w & 3u))) return WRS_EINVAL;
+    return cuda_status(launch_pack_variant(d_w, n, d_rows, (unsigned char *)d_ws, L,
+                                           c.section_size, variant, (cudaStream_t)stream));
 }
 
 int wrs_diag_philox(uint64_t count, uint64_t seed, uint32_t *d_out, void *stream) {

@@ -807,7 +807,6 @@ __global__ void k_split_ends(const BuildParams *__restrict__ P, SplitRec *__rest
 // prefix sums themselves are exact (128-bit); only the stored keys are
 // rounded, the same way everywhere, so the table does not depend on the
 // section size.
-constexpr int kKeyCap62 = 62;
 
 // Shared memory: sK (keys: slot x = A(x), slot L+y+1 = B(y)) and sE (the
 // section's entries: lights, heavies, then the first heavy after the
@@ -817,12 +816,6 @@ __host__ __device__ inline uint32_t pack_per(uint32_t S) { return S <= 4096 ? 8 
 __host__ __device__ inline uint32_t pack_slots(uint32_t S) { return pk16(S + 1) + 1; }
 __host__ __device__ inline uint32_t pack_smem_bytes(uint32_t S) { return 16 * pack_slots(S); }
 
-// floor((c + p) / 2^15) for the 128-bit two's-complement sum c + p, capped
-// at 2^62 (the true value is above -2^48).
-__device__ __forceinline__ int64_t sweep_key(u128 c, u128 p) {
-    const __int128 v = (__int128)(c + p) >> kKeyShift;
-    return v < ((__int128)1 << kKeyCap62) ? (int64_t)v : ((int64_t)1 << kKeyCap62);
-}
 
 template <int kPer>
 __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,

@@ -242,6 +242,15 @@ __device__ __forceinline__ bool sweep_le(u128 E, u128 D) {
 // N * q as 128 bits (q < 2^63, N < 2^31).
 __device__ __forceinline__ u128 mul_nq(uint32_t N, uint64_t q) { return (u128)q * N; }
 
+// floor((c + p) / 2^15) for the 128-bit two's-complement sum c + p, capped
+// at 2^62 (the true value is above -2^48): a heavy's sweep key relative to
+// its section (the pack and its sequential variants).
+constexpr int kKeyCap62 = 62;
+__device__ __forceinline__ int64_t sweep_key(u128 c, u128 p) {
+    const __int128 v = (__int128)(c + p) >> kKeyShift;
+    return v < ((__int128)1 << kKeyCap62) ? (int64_t)v : ((int64_t)1 << kKeyCap62);
+}
+
 // ---------------------------------------------------------------------------
 // Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
 // 32x32->64 multiplies with fixed odd constants, mixing the high halves with

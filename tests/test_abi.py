@@ -63,6 +63,19 @@ def test_host_argument_checks(lib):
     # the Philox probe needs an 8-byte aligned output (checked on the host)
     assert lib.wrs_diag_philox(4, 1, ctypes.c_void_p(4), None) == wrs.EINVAL
     assert lib.wrs_diag_philox(4, 1, None, None) == wrs.EINVAL
+    # pack variants: a missing workspace, then an unknown variant (a fake,
+    # never dereferenced workspace address passes the workspace checks)
+    big = 1 << 40
+    assert lib.wrs_diag_pack_variant(None, 10, None, None, 0, None, 1, None) == wrs.EINVAL
+    assert lib.wrs_diag_pack_variant(None, 10, ctypes.c_void_p(256), ctypes.c_void_p(256), big,
+                                     None, 3, None) == wrs.EINVAL
+    assert lib.wrs_diag_pack_variant(None, 10, ctypes.c_void_p(256), ctypes.c_void_p(256), big,
+                                     None, 0, None) == wrs.EINVAL   # gather needs the weights
+    # PSA+: a missing or misaligned workspace
+    assert lib.wrs_build_rows_plus(None, 10, None, None, 0, None, 1, None, None, None) == wrs.EINVAL
+    assert lib.wrs_build_rows_plus(ctypes.c_void_p(256), 10, ctypes.c_void_p(256),
+                                   ctypes.c_void_p(100), big, None, 1, ctypes.c_void_p(256),
+                                   None, None) == wrs.EINVAL
     assert lib.wrs_abi_version() >= 1
     assert lib.wrs_strerror(wrs.EZEROSUM) == b"all weights are zero"
 
