@@ -179,3 +179,19 @@ def test_plus_dominant_heavy(kind, pos):
     assert mass_err(w, prob, alias) <= MASS_TOL
     _, _, g_orc = oracle.psa_plus(w, wrs.config().section_size, TILE, 1)
     assert abs(greedy - g_orc) <= greedy_tol(n), (greedy, g_orc)
+
+
+@pytest.mark.parametrize("section,method", [(256, 0), (8192, 0), (1024, 1)])
+def test_plus_config(section, method):
+    # the leftovers' PSA takes the section size and split method of cfg
+    n = 250007
+    w = inputs.by_name("exponential", n, 101)
+    cfg = wrs.config(section, method)
+    prob, alias, inf, greedy = build_plus(w, 1, cfg)
+    assert inf["status"] == wrs.OK
+    assert mass_err(w, prob, alias) <= MASS_TOL
+    _, _, g_orc = oracle.psa_plus(w, section, TILE, 1)
+    assert abs(greedy - g_orc) <= greedy_tol(n), (greedy, g_orc)
+    # the greedy step does not depend on cfg: same greedy rows as the default
+    p0, a0, _, g0 = build_plus(w, 1)
+    assert g0 == greedy
