@@ -75,6 +75,9 @@ def parse():
                     help="time the build alone (no sampling legs, batched or serving)")
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--serve-sweep", action="store_true",
+                    help="also measure the request loop's capacity and replay the stream "
+                         "at 0.3, 0.6 and 0.9 of it (--serve-requests requests each)")
     ap.add_argument("--batch-tables", type=int, default=100_000)
     ap.add_argument("--sampler-heatmap", action="store_true",
                     help="also time every sampling mode over a grid of table sizes and draw "
@@ -411,6 +414,8 @@ def run_gpu(args):
         run_psa_plus(args, w, w_host, n, cfg, build_ms)
     batched = None if args.no_batched else run_batched(args, world, rank)
     serving_res = None if args.no_serving else run_serving(args, rank)
+    if args.serve_sweep and serving_res is not None:
+        serving_res["load_sweep"] = run_serving_sweep(args, rank)
     heatmap = run_sampler_heatmap(args) if args.sampler_heatmap else None
     ablation = run_ablation(args, w, n) if args.ablation else None
 
@@ -772,6 +777,38 @@ def run_serving(args, rank):
             "samples_per_s": st["samples_drawn"] / wall if wall else None,
             "steps": st["steps"], "mean_step_requests": st["mean_step_requests"],
             "peak_bytes": st["peak_bytes"], "budget_bytes": 80 << 30}
+
+
+def run_serving_sweep(args, rank):
+    """Capacity of the request loop (the whole stream submitted at once,
+    completions per second), then the Poisson stream replayed in real time at
+    0.3, 0.6 and 0.9 of that capacity: latency against load."""
+    import paper_2106_12270_gb300 as wrs
+    from paper_2106_12270_gb300 import inputs, serving
+
+    def run(rate, realtime):
+        ops = inputs.serving_stream(args.serve_requests, 5 + rank, rate)
+        srv = wrs.Server(80 << 30, 4)
+        try:
+            _, _, _, status = serving.replay(srv, ops, realtime=realtime)
+            st = srv.stats()
+        finally:
+            srv.close()
+        wall = st["wall_s"]
+        return {"requests": len(ops), "ok": sum(1 for v in status.values() if v == wrs.OK),
+                "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"],
+                "requests_per_s": st["completed"] / wall if wall else None,
+                "mean_step_requests": st["mean_step_requests"]}
+
+    cap = run(1e9, False)   # every arrival at time ~0: the loop's own rate
+    capacity = cap["requests_per_s"]
+    points = []
+    for f in (0.3, 0.6, 0.9):
+        r = run(f * capacity, True)
+        r["load"] = f
+        r["arrival_rate_per_s"] = f * capacity
+        points.append(r)
+    return {"capacity_requests_per_s": capacity, "saturated": cap, "points": points}
 
 
 def main():
