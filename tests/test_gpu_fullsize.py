@@ -7,7 +7,8 @@ oracle computes one by one.
   entries at sampled ranks, every item's mass, the rows against the oracle's
   PSA sweep, and sampled draws of the 1e9-draw stream against the oracle's
   sampler on the exported table.
-* N = 2^30 Exp(1) (seed 4): exact W and counts, every item's mass.
+* N = 2^30 Exp(1) (seed 4): exact W and counts, every item's mass; the same
+  for a PSA+ build of those weights.
 """
 from __future__ import annotations
 
@@ -93,4 +94,19 @@ def test_full_size_2pow30_exponential_build():
     assert info["W"] == W
     nl = int(torch.count_nonzero(w.double() <= W / n))
     assert (info["nl"], info["nh"]) == (nl, n - nl)
+    assert device_mass_error(rows, w, W) <= 1e-5
+    # PSA+ on the same weights: every item's mass, and the greedy share of
+    # 512-item chunks (the oracle's PSA+ at this size would need ~35 GB of
+    # host memory; its greedy count is compared at 4e6 items and below)
+    del b
+    torch.cuda.empty_cache()
+    ws = torch.empty(wrs.build_plus_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    pinfo = torch.zeros(wrs.INFO_BYTES, dtype=torch.uint8, device="cuda")
+    greedy = wrs.build_rows_plus(w, rows, ws, pinfo)
+    pi = wrs.parse_info(pinfo)
+    assert pi["status"] == wrs.OK and pi["W"] == W
+    assert (pi["nl"], pi["nh"]) == (nl, n - nl)
+    del ws
+    torch.cuda.empty_cache()
+    assert greedy > 0.9 * n   # Exp(1): 95% in the oracle at 2e6 to 1e7 items
     assert device_mass_error(rows, w, W) <= 1e-5
