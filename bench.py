@@ -1,20 +1,26 @@
 #!/usr/bin/env python
 """Benchmark: alias-table build + sampling on GB300, one JSON line on rank 0.
 
-Workload (default): one table of N = 1e8 FP32 weights w_i = 1/rank^1.0 with
-the ranks randomly permuted (seed 3) -- the paper's shuffled power law --
-built with PSA, then 1e9 samples drawn by Walker's rule (Philox seed 2).
-A step is one build plus the samples.  Inputs (400 MB weights, 800 MB table,
-4 GB samples) are larger than L2, so no L2 flush is needed between steps.
+Workload (default): one table of N = 2^30 FP32 weights drawn from
+Exponential(1) (seed 4), built with PSA (Sec. 2.2, Sec. 4), then 1e10
+samples drawn by Walker's rule (Philox seed 2) in output chunks of at most
+4e9 draws (one 16 GB buffer reused; the chunks are consecutive ranges of
+one sample stream).  A step is one build plus the 1e10 draws.  Inputs
+(4 GiB weights, 8 GiB table, 16 GB of samples per chunk) are larger than L2,
+so no L2 flush is needed between steps.
 
 `value` is build throughput (items/s) from CUDA events around the build
 kernels of every timed step; `samples_per_s` comes from the events around
-the sampler.  Under torchrun every rank builds and samples its own table (an
-independent problem, no data-path collective): scaling is weak and `value`
-sums all ranks' items over the slowest rank's time.
+the sampler launches.  Under torchrun every rank builds and samples its own
+table (an independent problem, no data-path collective): scaling is weak and
+`value` sums all ranks' items over the slowest rank's time.
+
+Extra keys (not in the timed step): the sectioned samplers on the same table
+and draw count, the 1e8-item shuffled power law (build, 1e9 draws, mass
+error), PSA+, the batched build of 100k uneven tables and the request loop.
 
 `--impl reference` times the CPU oracle (Vose's FP64 construction) on the
-host cores for the same metric.
+host cores for the same metric, on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -36,6 +42,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 BUILD_BYTES_PER_ITEM = 32      # read w twice, write + read lh, write rows
 SAMPLE_BYTES_PER_DRAW = 36     # one 32-byte row sector + a 4-byte output
+SECTOR_BYTES = 32
 KERNELS_PER_BUILD = 10         # sum, count, qsum, scatter, segscan, split ends, split, split fine, pack, info
 # DRAM bytes the hardware moved per unit (dram__bytes_read.sum +
 # dram__bytes_write.sum) in ncu captures of these kernels: the build at
@@ -46,8 +53,7 @@ KERNELS_PER_BUILD = 10         # sum, count, qsum, scatter, segscan, split ends,
 # units.  To be re-measured whenever one of these kernels changes.
 BUILD_TRAFFIC_PER_ITEM = 35.2
 SAMPLE_TRAFFIC_PER_DRAW = 91.5
-KERNELS_PER_SAMPLE = 1
-# batched build/sample are timed separately (extra keys), not in gpu_launches
+SEEDS = {"zipf": 3, "zipf0.5": 5, "uniform": 1, "exponential": 4, "gamma": 7}
 
 
 def parse():
@@ -56,20 +62,26 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["wrs", "reference"], default="wrs")
-    ap.add_argument("--n", type=int, default=100_000_000)
-    ap.add_argument("--samples", type=int, default=1_000_000_000)
+    ap.add_argument("--n", type=int, default=1 << 30)
+    ap.add_argument("--samples", type=int, default=10_000_000_000)
+    ap.add_argument("--chunk", type=int, default=4_000_000_000,
+                    help="draws per sampling call (the output buffer holds one chunk)")
     ap.add_argument("--section", type=int, default=1024)
-    ap.add_argument("--dist", default="zipf",
+    ap.add_argument("--dist", default="exponential",
                     choices=["zipf", "zipf0.5", "uniform", "exponential", "gamma"],
-                    help="weights of the single table (default: shuffled power law)")
+                    help="weights of the single table (default: Exp(1), seed 4)")
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true",
-                    help="skip the host-side mass check of the timed table")
+                    help="skip the mass check of the timed table")
+    ap.add_argument("--no-sectioned", action="store_true",
+                    help="skip the sectioned samplers and the probes")
+    ap.add_argument("--no-power-law", action="store_true",
+                    help="skip the 1e8-item shuffled power-law table (extra key)")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-psa-plus", action="store_true",
-                    help="skip the PSA+ build (Sec. 4) timed on the same table")
+                    help="skip the PSA+ builds (Sec. 4)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--build-only", action="store_true",
                     help="time the build alone (no sampling legs, batched or serving)")
@@ -98,22 +110,32 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region
+    (read-only queries of the GPU this process runs on, named by its UUID:
+    nvidia-smi numbers GPUs physically and ignores CUDA_VISIBLE_DEVICES)."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
-        self.index = index
+    def __init__(self, device: int):
+        self.device = device
         self.proc = None
         self.lines = []
         self.thread = None
 
+    def _gpu_id(self) -> str:
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(self.device).uuid)
+            return u if u.startswith("GPU-") else "GPU-" + u
+        except Exception:
+            return str(self.device)
+
     def start(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                ["nvidia-smi", "-i", self._gpu_id(), f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
@@ -160,6 +182,10 @@ def dist_env():
     return replicas.env()
 
 
+def workload_seed(args) -> int:
+    return args.seed if args.seed is not None else SEEDS[args.dist]
+
+
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
@@ -179,6 +205,28 @@ def oracle_build_items_per_s(w, reps_budget_s: float = 20.0):
     return w.size / statistics.median(times), len(times)
 
 
+def oracle_sampler_rate(prob32, alias, draws_per_thread: int, threads: int):
+    """The oracle's naive sampler (Walker, Philox seed 2) on an exported table,
+    one contiguous range of the sample stream per host thread (the C call
+    releases the GIL, so the threads run on separate cores).  Returns
+    (samples/s, total draws)."""
+    import concurrent.futures as cf
+
+    import oracle
+    oracle.build()
+    oracle.sample_naive(prob32, alias, 0, 1024, 2)   # load the library
+
+    def part(k):
+        oracle.sample_naive(prob32, alias, k * draws_per_thread, draws_per_thread, 2)
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(part, range(threads)))
+    sec = time.perf_counter() - t0
+    total = draws_per_thread * threads
+    return total / sec, total
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -187,9 +235,10 @@ def run_reference(args):
     import oracle
     oracle.build()
     # bounded sample of the workload: the first 1e7 items of the same array
-    # recipe keep each step near one second of single-core work
+    # recipe keep each step near a tenth of a second of single-core work
+    seed = workload_seed(args)
     n = min(args.n, 10_000_000)
-    w = inputs.zipf_permuted(n, 3)
+    w = inputs.by_name(args.dist, n, seed)
     for _ in range(args.warmup):
         oracle.vose(w)
     ts = []
@@ -204,10 +253,11 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"single table, shuffled power law s=1.0 (seed 3), "
+        "config": {"workload": f"single table, {args.dist} weights (seed {seed}), "
                                f"oracle sample N={n} of N={args.n}", "n": n},
         "cpu_baseline": {"value": value, "unit": "items/s", "cores": 1, "kind": "oracle",
-                         "sample": f"Vose FP64 build of N={n} shuffled-power-law weights"},
+                         "sample": f"Vose FP64 build of the first {n} of the N={args.n} "
+                                   f"{args.dist} weights (seed {seed})"},
         "e2e": {"value": value, "unit": "items/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -218,6 +268,41 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+
+def _events(k):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+
+
+def _chunks(count: int, chunk: int):
+    """(first, size) of the sampling calls covering draws 0..count-1."""
+    out, first = [], 0
+    while first < count:
+        c = min(chunk, count - first)
+        out.append((first, c))
+        first += c
+    return out
+
+
+def device_mass_error(rows, w) -> float:
+    """max_i |mass_i - N w_i/W| / max(1, N w_i/W) of a built table, in FP64 on
+    the device with torch ops (a measurement of the result, not part of the
+    build; W here is torch's FP64 sum of the weights)."""
+    import torch
+    n = w.numel()
+    raw = rows.view(torch.int32).view(n, 2)
+    prob = raw[:, 0].contiguous().view(torch.float32).double()
+    mass = prob.clone()
+    mass.index_add_(0, raw[:, 1].long(), 1.0 - prob)
+    del prob
+    wd = w.double()
+    expect = wd * (n / float(wd.sum()))
+    del wd
+    err = float(((mass - expect).abs() / expect.clamp(min=1.0)).max())
+    del mass, expect
+    torch.cuda.empty_cache()
+    return err
+
 
 def run_gpu(args):
     import numpy as np
@@ -236,19 +321,20 @@ def run_gpu(args):
     wrs.lib()
 
     n, count = args.n, args.samples
-    cfg = wrs.config(args.section)
-    seed = replicas.rank_seed(args.seed if args.seed is not None else
-                              {"zipf": 3, "zipf0.5": 5, "uniform": 1, "exponential": 4,
-                               "gamma": 7}[args.dist],
-                              rank)
-    w_host = inputs.by_name(args.dist, n, seed)
-    w = torch.from_numpy(w_host).cuda()
-    builder = wrs.Builder(n, cfg)
-    rows = torch.empty(n, dtype=torch.int64, device="cuda")
     if args.build_only:
         count = 0
         args.no_batched = args.no_serving = args.no_e2e = args.no_accuracy = True
-    out = torch.empty(max(count, 1), dtype=torch.int32, device="cuda")
+        args.no_sectioned = args.no_power_law = True
+    cfg = wrs.config(args.section)
+    seed = replicas.rank_seed(workload_seed(args), rank)
+    t_gen = time.perf_counter()
+    w_host = inputs.by_name(args.dist, n, seed)
+    gen_s = time.perf_counter() - t_gen
+    w = torch.from_numpy(w_host).cuda()
+    builder = wrs.Builder(n, cfg)
+    rows = torch.empty(n, dtype=torch.int64, device="cuda")
+    chunks = _chunks(count, args.chunk)
+    out = torch.empty(max(min(count, args.chunk), 1), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
     def step(evs=None):
@@ -257,8 +343,8 @@ def run_gpu(args):
         wrs.build_rows(w, rows, builder.ws, builder.info, cfg)
         if evs:
             evs[1].record(stream)
-        if not args.build_only:
-            wrs.sample_rows(rows, n, 0, count, 2, out)
+        for first, c in chunks:
+            wrs.sample_rows(rows, n, first, c, 2, out[:c])
         if evs:
             evs[2].record(stream)
 
@@ -274,9 +360,8 @@ def run_gpu(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.4)  # let the sampler see the region
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
+    evs = [_events(3) for _ in range(args.steps)]
+    t_start, t_end = _events(2)
     t_start.record(stream)
     for k in range(args.steps):
         step(evs[k])
@@ -298,120 +383,24 @@ def run_gpu(args):
     # the next step's copy in and build (as a pipeline of requests would).
     e2e = None
     if not args.no_e2e:
-        nbuf = 2
-        w_pin = torch.from_numpy(w_host).pin_memory()
-        rows_pin = [torch.empty(n, dtype=torch.int64).pin_memory() for _ in range(nbuf)]
-        info_pin = [torch.zeros(wrs.INFO_BYTES, dtype=torch.uint8).pin_memory()
-                    for _ in range(nbuf)]
-        hws = [torch.empty(wrs.build_host_workspace_bytes(n, cfg), dtype=torch.uint8,
-                           device="cuda") for _ in range(nbuf)]
-        streams = [torch.cuda.Stream() for _ in range(nbuf)]
+        e2e = run_e2e(args, w_host, rows, cfg, n, world, dist)
 
-        def e2e_steps(k0, k1):
-            for k in range(k0, k1):
-                b = k % nbuf
-                wrs.build_rows_host(w_pin, rows_pin[b], hws[b], info_pin[b], cfg, streams[b])
-
-        e2e_steps(0, max(2, args.warmup))
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for st in streams:
-            st.wait_event(a)
-        e2e_steps(0, args.steps)
-        for st in streams:
-            stream.wait_stream(st)
-        b.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = a.elapsed_time(b) / args.steps
-        bad = [wrs.parse_info(x)["status"] for x in info_pin if wrs.parse_info(x)["status"]]
-        if bad:
-            raise RuntimeError(f"host build failed: {bad}")
-        if not torch.equal(rows_pin[(args.steps - 1) % nbuf], rows.cpu()):
-            raise RuntimeError("host build differs from the device build")
-        e2e_ms = replicas.max_over_ranks([e2e_ms], dist, "cuda")[0]
-        e2e = {"value": replicas.job_rate(n, world, e2e_ms), "unit": "items/s",
-               "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n + wrs.INFO_BYTES,
-               "ms_per_step": e2e_ms, "api": "wrs_build_rows_host",
-               "pipelining": f"{nbuf} workspaces on {nbuf} streams"}
-
-    # accuracy of the timed table: the reconstructed mass of every item
-    # against N w_i / W in FP64 (plain numpy on the host; the stated bound is
-    # |mass_i - N w_i/W| <= 1e-5 max(1, N w_i/W))
+    # accuracy of the timed table: every item's reconstructed mass against
+    # N w_i / W (the stated bound is |mass_i - N w_i/W| <= 1e-5 max(1, N w_i/W))
     accuracy = None
     if not args.no_accuracy:
-        import numpy as np
-        raw = rows.cpu().numpy().view(np.uint32).reshape(-1, 2)
-        prob = raw[:, 0].view(np.float32).astype(np.float64)
-        mass = prob + np.bincount(raw[:, 1], weights=1.0 - prob, minlength=n)
-        wd = w_host.astype(np.float64)
-        expect = wd * (n / float(np.sum(wd)))
-        err = np.abs(mass - expect) / np.maximum(1.0, expect)
-        accuracy = {"max_mass_error": float(err.max()), "mean_mass_error": float(err.mean()),
-                    "bound": 1e-5, "items_checked": n,
+        accuracy = {"max_mass_error": device_mass_error(rows, w), "bound": 1e-5,
+                    "items_checked": n,
                     "prefix_arithmetic": "exact 128-bit fixed-point prefix sums; sweep "
                                          "compares them at 2^-15 units (2^-46 of a bucket)"}
-        del raw, prob, mass, wd, expect, err
 
-    # sectioned sampling (Sec. 5): same draw count, samples grouped by section
-    sec = {}
-    for mode, name, rows_per in () if args.build_only else ((wrs.SAMPLE_CACHED, "cached", 8192),
-                                 (wrs.SAMPLE_LIMITED, "limited", 8192),
-                                 (wrs.SAMPLE_SMEM, "smem", 4096)):
-        nsec = wrs.sample_sections(n, rows_per)
-        cnt_t = torch.empty(nsec, dtype=torch.int64, device="cuda")
-        off_t = torch.empty(nsec, dtype=torch.int64, device="cuda")
-        wrs.sample_sectioned_rows(rows, n, count, 2, mode, rows_per, cnt_t, off_t, out)
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(args.steps):
-            wrs.sample_sectioned_rows(rows, n, count, 2, mode, rows_per, cnt_t, off_t, out)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / args.steps
-        sec[name] = {"ms": ms, "samples_per_s": world * count / (ms / 1e3),
-                     "section_rows": rows_per}
+    hbm, peak_kind = peaks()
+    sampling = None if (args.no_sectioned or not count) else \
+        run_sampling_extras(args, rows, n, count, out, world, sample_ms, hbm)
 
-    # Philox-rate probe: the sectioned samplers' generator calls and 4-byte
-    # stores alone (same draw count); their arithmetic roofline
-    if sec:
-        wrs.diag_philox(count, 7, out)
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(args.steps):
-            wrs.diag_philox(count, 7, out)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ph_ms = a.elapsed_time(b) / args.steps
-        for v in sec.values():
-            v["frac_of_philox_probe"] = ph_ms / v["ms"]
-        sec["philox_probe"] = {"ms": ph_ms, "samples_per_s": world * count / (ph_ms / 1e3),
-                               "bound": "alu",
-                               "what": "the same Philox-4x32-10 calls and 4-byte stores, "
-                                       "no rows (wrs_diag_philox)"}
-
-    # random-gather probe: the naive sampler's access pattern alone (same
-    # table size, same number of draws), best of the three load paths
-    probe = {}
-    for flavor in () if args.build_only else (0, 1, 2):
-        wrs.diag_random_gather(rows, n, count, 7, flavor, out)
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        wrs.diag_random_gather(rows, n, count, 7, flavor, out)
-        b.record(stream)
-        torch.cuda.synchronize()
-        probe[flavor] = a.elapsed_time(b)
-    probe_ms = min(probe.values()) if probe else float("nan")
-
+    power_law = None if args.no_power_law else run_power_law(args, world)
     psa_plus = None if (args.no_psa_plus or args.build_only) else \
-        run_psa_plus(args, w, w_host, n, cfg, build_ms)
+        run_psa_plus(args, w, n, cfg, build_ms)
     batched = None if args.no_batched else run_batched(args, world, rank)
     serving_res = None if args.no_serving else run_serving(args, rank)
     if args.serve_sweep and serving_res is not None:
@@ -419,24 +408,29 @@ def run_gpu(args):
     heatmap = run_sampler_heatmap(args) if args.sampler_heatmap else None
     ablation = run_ablation(args, w, n) if args.ablation else None
 
-    hbm, peak_kind = peaks()
     build_gbs = BUILD_BYTES_PER_ITEM * n / (build_ms / 1e3) / 1e9
     sample_gbs = (SAMPLE_BYTES_PER_DRAW * count / (sample_ms / 1e3) / 1e9) if count else 0.0
     build_roof = {"bound": "hbm", "achieved": build_gbs, "peak": hbm, "unit": "GB/s",
                   "frac": build_gbs / hbm, "traffic": BUILD_TRAFFIC_PER_ITEM * n,
                   "traffic_unit": "bytes per build (ncu, scaled from N=2^25)",
-                  "kernel": "build (10 kernels)",
+                  "kernel": "build (10 kernels)", "algorithmic_bytes_per_item": 32,
                   "peak_kind": peak_kind}
-    probe_gbs = (SAMPLE_BYTES_PER_DRAW * count / (probe_ms / 1e3) / 1e9) if probe else float("nan")
-    sample_roof = {"bound": "hbm", "achieved": sample_gbs, "peak": hbm, "unit": "GB/s",
-                   "frac": sample_gbs / hbm,
-                   "traffic": SAMPLE_TRAFFIC_PER_DRAW * count if count else None,
-                   "traffic_unit": "bytes per launch (ncu, scaled from 2^25 draws)",
-                   "kernel": "k_sample_naive",
-                   "peak_kind": peak_kind,
-                   "random_gather_probe": {"achieved": probe_gbs, "unit": "GB/s",
-                                           "frac_of_probe": (sample_gbs / probe_gbs) if probe else None,
-                                           "ms": {str(k): v for k, v in probe.items()}}}
+    sample_roof = None
+    if count:
+        sectors_peak = hbm * 1e9 / SECTOR_BYTES
+        sample_roof = {"bound": "hbm", "achieved": sample_gbs, "peak": hbm, "unit": "GB/s",
+                       "frac": sample_gbs / hbm,
+                       "traffic": SAMPLE_TRAFFIC_PER_DRAW * count / len(chunks),
+                       "traffic_unit": "bytes per launch (ncu, scaled from 2^25 draws)",
+                       "kernel": "k_sample_naive", "launches_per_step": len(chunks),
+                       "algorithmic_bytes_per_draw": SAMPLE_BYTES_PER_DRAW,
+                       "frac_of_sector_rate": (count / (sample_ms / 1e3)) / sectors_peak,
+                       "sector_rate_peak": sectors_peak,
+                       "peak_kind": peak_kind}
+        if sampling and sampling.get("random_gather_probe"):
+            pr = sampling["random_gather_probe"]
+            sample_roof["random_gather_probe"] = pr
+            sample_roof["frac_of_probe"] = (count / sample_ms) / (pr["count"] / pr["best_ms"])
     dominant = sample_roof if (count and sample_ms >= build_ms) else build_roof
 
     cpu = None
@@ -444,7 +438,19 @@ def run_gpu(args):
         nb = min(n, 10_000_000)
         ips, runs = oracle_build_items_per_s(w_host[:nb].copy())
         cpu = {"value": ips, "unit": "items/s", "cores": 1, "kind": "oracle",
-               "sample": f"Vose FP64 build of the first {nb} weights, median of {runs} runs"}
+               "sample": f"Vose FP64 build of the first {nb} of the N={n} weights, "
+                         f"median of {runs} runs"}
+        if count:
+            prob32, alias = wrs.rows_to_numpy(rows)
+            threads = os.cpu_count() or 1
+            per = max(1, min(count // threads, 20_000_000))
+            rate, drawn = oracle_sampler_rate(prob32, alias, per, threads)
+            cpu["sampler"] = {"value": rate, "unit": "samples/s", "cores": threads,
+                              "kind": "oracle",
+                              "sample": f"{drawn} draws (samples 0..{drawn - 1} of the timed "
+                                        f"stream) from the GPU-built N={n} table, one range "
+                                        f"per host thread"}
+            del prob32, alias
 
     if rank == 0:
         line = {
@@ -454,13 +460,16 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "u128 fixed point (build), u32 (sampling)",
             "data": "synthetic",
             "config": {"workload": f"single table N={n}, {args.dist} weights (seed {seed}); "
-                                   f"build + {count} naive Walker samples (Philox seed 2)",
-                       "n": n, "samples": count, "section_size": args.section,
-                       "dist": args.dist,
+                                   f"build + {count} naive Walker samples (Philox seed 2) "
+                                   f"in {len(chunks)} calls of at most {args.chunk}",
+                       "n": n, "samples": count, "chunk": args.chunk,
+                       "section_size": args.section, "dist": args.dist,
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas{world}"},
             "build_ms": build_ms, "sample_ms": sample_ms,
             "samples_per_s": (world * count / (sample_ms / 1e3)) if count else None,
-            "sectioned_sampling": sec,
+            "input_generation_s": gen_s,
+            "sampling": sampling,
+            "power_law_1e8": power_law,
             "batched": batched,
             "psa_plus": psa_plus,
             "serving": serving_res,
@@ -468,7 +477,7 @@ def run_gpu(args):
             **({"ablation": ablation} if ablation is not None else {}),
             "roofline": dominant, "build_roofline": build_roof, "sample_roofline": sample_roof,
             "cpu_baseline": cpu, "e2e": e2e, "accuracy": accuracy, "clocks": clk,
-            "gpu_launches": args.steps * (KERNELS_PER_BUILD + KERNELS_PER_SAMPLE),
+            "gpu_launches": args.steps * (KERNELS_PER_BUILD + len(chunks)),
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -476,11 +485,187 @@ def run_gpu(args):
     return 0
 
 
+def run_e2e(args, w_host, rows, cfg, n, world, dist):
+    """Build throughput through wrs_build_rows_host: pinned host weights in,
+    host rows and summary out, every copy inside the timed region."""
+    import torch
+
+    import paper_2106_12270_gb300 as wrs
+    from paper_2106_12270_gb300 import replicas
+
+    stream = torch.cuda.current_stream()
+    nbuf = 2
+    w_pin = torch.from_numpy(w_host).pin_memory()
+    rows_pin = [torch.empty(n, dtype=torch.int64).pin_memory() for _ in range(nbuf)]
+    info_pin = [torch.zeros(wrs.INFO_BYTES, dtype=torch.uint8).pin_memory()
+                for _ in range(nbuf)]
+    hws = [torch.empty(wrs.build_host_workspace_bytes(n, cfg), dtype=torch.uint8,
+                       device="cuda") for _ in range(nbuf)]
+    streams = [torch.cuda.Stream() for _ in range(nbuf)]
+
+    def e2e_steps(k0, k1):
+        for k in range(k0, k1):
+            b = k % nbuf
+            wrs.build_rows_host(w_pin, rows_pin[b], hws[b], info_pin[b], cfg, streams[b])
+
+    e2e_steps(0, max(2, args.warmup))
+    torch.cuda.synchronize()
+    a, b = _events(2)
+    a.record(stream)
+    for st in streams:
+        st.wait_event(a)
+    e2e_steps(0, args.steps)
+    for st in streams:
+        stream.wait_stream(st)
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = a.elapsed_time(b) / args.steps
+    bad = [wrs.parse_info(x)["status"] for x in info_pin if wrs.parse_info(x)["status"]]
+    if bad:
+        raise RuntimeError(f"host build failed: {bad}")
+    if not torch.equal(rows_pin[(args.steps - 1) % nbuf], rows.cpu()):
+        raise RuntimeError("host build differs from the device build")
+    e2e_ms = replicas.max_over_ranks([e2e_ms], dist, "cuda")[0]
+    del hws, rows_pin, w_pin
+    torch.cuda.empty_cache()
+    return {"value": replicas.job_rate(n, world, e2e_ms), "unit": "items/s",
+            "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 8 * n + wrs.INFO_BYTES,
+            "ms_per_step": e2e_ms, "api": "wrs_build_rows_host",
+            "pipelining": f"{nbuf} workspaces on {nbuf} streams"}
+
+
+def run_sampling_extras(args, rows, n, count, out, world, naive_ms, hbm):
+    """The sectioned samplers (Sec. 5) on the timed table with the same draw
+    count and chunking, the mode AUTO picks, the Philox-rate probe (their
+    arithmetic roofline) and the random-gather probe (the naive sampler's
+    access pattern alone: the random-sector rate this GPU sustains)."""
+    import torch
+
+    import paper_2106_12270_gb300 as wrs
+
+    stream = torch.cuda.current_stream()
+    chunks = _chunks(count, args.chunk)
+    res = {"naive": {"ms": naive_ms, "samples_per_s": world * count / (naive_ms / 1e3)}}
+    for mode, name, rows_per in ((wrs.SAMPLE_CACHED, "cached", 8192),
+                                 (wrs.SAMPLE_SMEM, "smem", 4096)):
+        nsec = wrs.sample_sections(n, rows_per)
+        cnt_t = torch.empty(nsec, dtype=torch.int64, device="cuda")
+        off_t = torch.empty(nsec, dtype=torch.int64, device="cuda")
+
+        def run():
+            for k, (_, c) in enumerate(chunks):
+                wrs.sample_sectioned_rows(rows, n, c, 2 + k, mode, rows_per, cnt_t, off_t, out[:c])
+
+        run()
+        torch.cuda.synchronize()
+        a, b = _events(2)
+        a.record(stream)
+        for _ in range(args.steps):
+            run()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+        res[name] = {"ms": ms, "samples_per_s": world * count / (ms / 1e3),
+                     "section_rows": rows_per, "speedup_vs_naive": naive_ms / ms,
+                     "output_gbs": 4 * count / (ms / 1e3) / 1e9}
+        del cnt_t, off_t
+    res["auto_choice"] = wrs.sample_auto_choice(n, min(count, args.chunk))
+
+    # Philox-rate probe: the sectioned samplers' generator calls and 4-byte
+    # stores alone (same draw count)
+    def philox():
+        for k, (_, c) in enumerate(chunks):
+            wrs.diag_philox(c, 7 + k, out[:c])
+
+    philox()
+    torch.cuda.synchronize()
+    a, b = _events(2)
+    a.record(stream)
+    for _ in range(args.steps):
+        philox()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ph_ms = a.elapsed_time(b) / args.steps
+    for k in ("cached", "smem"):
+        res[k]["frac_of_philox_probe"] = ph_ms / res[k]["ms"]
+    res["philox_probe"] = {"ms": ph_ms, "samples_per_s": world * count / (ph_ms / 1e3),
+                           "bound": "alu",
+                           "what": "the same Philox-4x32-10 calls and 4-byte stores, "
+                                   "no rows (wrs_diag_philox)"}
+
+    # random-gather probe on the timed table: one chunk's draws, every load path
+    c0 = chunks[0][1]
+    probe = {}
+    for flavor in (0, 1, 2):
+        wrs.diag_random_gather(rows, n, c0, 7, flavor, out[:c0])
+        torch.cuda.synchronize()
+        a, b = _events(2)
+        a.record(stream)
+        wrs.diag_random_gather(rows, n, c0, 7, flavor, out[:c0])
+        b.record(stream)
+        torch.cuda.synchronize()
+        probe[str(flavor)] = a.elapsed_time(b)
+    best = min(probe.values())
+    res["random_gather_probe"] = {
+        "count": c0, "ms": probe, "best_ms": best,
+        "gathers_per_s": c0 / (best / 1e3),
+        "frac_of_sector_rate": (c0 / (best / 1e3)) / (hbm * 1e9 / SECTOR_BYTES),
+        "what": "uniformly random 8-byte reads of the table and one 4-byte store each "
+                "(wrs_diag_random_gather; flavors 0/1/2 = ld.global.nc/.cg/.cs)"}
+    return res
+
+
+def run_power_law(args, world):
+    """The paper's shuffled power law at N = 1e8 (w = 1/rank, ranks permuted,
+    seed 3): build, 1e9 naive draws (Philox seed 2), mass error of the table."""
+    import torch
+
+    import paper_2106_12270_gb300 as wrs
+    from paper_2106_12270_gb300 import inputs
+
+    n, count = 100_000_000, 1_000_000_000
+    w = torch.from_numpy(inputs.zipf_permuted(n, 3)).cuda()
+    cfg = wrs.config(args.section)
+    b = wrs.Builder(n, cfg)
+    rows = torch.empty(n, dtype=torch.int64, device="cuda")
+    out = torch.empty(count, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        b.build(w, rows)
+        wrs.sample_rows(rows, n, 0, count, 2, out)
+    torch.cuda.synchronize()
+    bm, sm = [], []
+    for _ in range(args.steps):
+        e = _events(3)
+        e[0].record(stream)
+        b.build(w, rows)
+        e[1].record(stream)
+        wrs.sample_rows(rows, n, 0, count, 2, out)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        bm.append(e[0].elapsed_time(e[1]))
+        sm.append(e[1].elapsed_time(e[2]))
+    info = wrs.parse_info(b.info)
+    hbm, _ = peaks()
+    build_ms, sample_ms = statistics.mean(bm), statistics.mean(sm)
+    res = {"n": n, "samples": count, "weights": "w = 1/rank, ranks permuted (seed 3)",
+           "status": info["status"], "nh": info["nh"],
+           "build_ms": build_ms, "items_per_s": world * n / (build_ms / 1e3),
+           "build_frac": BUILD_BYTES_PER_ITEM * n / (build_ms / 1e3) / 1e9 / hbm,
+           "sample_ms": sample_ms, "samples_per_s": world * count / (sample_ms / 1e3),
+           "max_mass_error": device_mass_error(rows, w), "mass_error_bound": 1e-5}
+    del w, b, rows, out
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_batched(args, world, rank):
     """Batched uneven tables: sizes log-uniform in [16, 65536] (seed 6),
-    Gamma(0.1, 1) weights, one batched build launch plus 1e3 samples per
-    table; compared with building the same tables one launch sequence at a
-    time (timed on the first tables and scaled to the whole batch)."""
+    Gamma(0.1, 1) weights (seed 7, host-generated, the same arrays the
+    oracle reads in the tests), one batched build launch plus 1e3 samples per
+    table; compared with building every table of the batch with its own
+    launch sequence of the single-table pipeline, from a C loop
+    (wrs_diag_build_each)."""
     import numpy as np
     import torch
 
@@ -492,8 +677,7 @@ def run_batched(args, world, rank):
     off_np = np.zeros(ntab + 1, np.int64)
     off_np[1:] = np.cumsum(sizes)
     total = int(off_np[-1])
-    torch.cuda.manual_seed(7 + rank)
-    w = torch._standard_gamma(torch.full((total,), 0.1, device="cuda")).float()
+    w = torch.from_numpy(inputs.gamma(total, 7 + rank, 0.1)).cuda()
     off = torch.from_numpy(off_np).cuda()
     rows = torch.empty(total, dtype=torch.int64, device="cuda")
     order = torch.from_numpy(wrs.batch_order(off_np).astype(np.int32)).cuda()
@@ -548,29 +732,26 @@ def run_batched(args, world, rank):
         gms.append(ev[0].elapsed_time(ev[1]))
     graph_ms = statistics.mean(gms)
 
-    # baseline: the plain single-table path, one launch sequence per table
-    probe = min(ntab, 2000)
-    b1 = wrs.Builder(65536)
-    r1 = torch.empty(65536, dtype=torch.int64, device="cuda")
-    for t in range(min(probe, 50)):
-        b1.build(w[off_np[t]:off_np[t + 1]], r1[: sizes[t]])
+    # baseline: the plain single-table pipeline, one launch sequence per
+    # table for every table of the batch, issued by a C loop in the library
+    each_ms, each_bad = wrs.diag_build_each(w, off_np, rows, 5)
+    if each_bad:
+        raise RuntimeError(f"per-table builds failed: {each_bad} tables")
+    # the per-table rows equal the batched rows bit for bit (same arithmetic)
+    each_rows = rows.clone()
+    bb.build(w, off, rows, order)
     torch.cuda.synchronize()
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for t in range(probe):
-        b1.build(w[off_np[t]:off_np[t + 1]], r1[: sizes[t]])
-    b.record(stream)
-    torch.cuda.synchronize()
-    probe_ms = a.elapsed_time(b)
-    frac = sizes[:probe].sum() / sizes.sum()
-    per_table_ms = probe_ms / frac
+    same = bool(torch.equal(each_rows, rows))
+    del each_rows
     return {"tables": ntab, "items": total, "tables_ok": ok, "build_ms": build_ms,
             "items_per_s": total / (build_ms / 1e3),
             "build_gbs": 36 * total / (build_ms / 1e3) / 1e9,
-            "per_table_launch_ms": per_table_ms,
-            "per_table_probe": f"first {probe} tables timed, scaled by item share {frac:.4f}",
-            "speedup_vs_per_table": per_table_ms / build_ms,
+            "per_table_launch_ms": each_ms,
+            "per_table_baseline": "every table built by wrs_build_rows, one launch sequence "
+                                  "per table from a C loop (wrs_diag_build_each), mean of "
+                                  "5 passes over the batch",
+            "per_table_rows_equal_batched": same,
+            "speedup_vs_per_table": each_ms / build_ms,
             "samples": ntab * per_table, "sample_ms": sample_ms,
             "samples_per_s": ntab * per_table / (sample_ms / 1e3),
             "tuning": {"best": best,
@@ -661,17 +842,34 @@ def run_sampler_heatmap(args):
     return {"weights": "uniform [0,1) (seed 1)", "unit": "ms", "cells": cells}
 
 
-def run_psa_plus(args, w, w_host, n, cfg, psa_build_ms):
-    """PSA+ (Sec. 4 "PSA+") on the bench table: greedy packing per 512-item
+def _psa_plus_once(args, w, n, cfg, psa_ms=None):
+    """PSA+ (Sec. 4 "PSA+") on one table: greedy packing per 512-item
     partition chunk, PSA on the rest.  Each call reads the rest's size back
-    once (a host sync), which the events around it include."""
+    once (a host sync), which the events around it include.  PSA is timed on
+    the same table unless its time is given."""
     import numpy as np
     import torch
 
     import paper_2106_12270_gb300 as wrs
 
+    stream = torch.cuda.current_stream()
     rows = torch.empty(n, dtype=torch.int64, device="cuda")
     info = torch.zeros(wrs.INFO_BYTES, dtype=torch.uint8, device="cuda")
+    if psa_ms is None:
+        b = wrs.Builder(n, cfg)
+        for _ in range(3):
+            b.build(w, rows)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            a, e = _events(2)
+            a.record(stream)
+            b.build(w, rows)
+            e.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(e))
+        psa_ms = float(np.mean(ts))
+        del b
     ws = torch.empty(wrs.build_plus_workspace_bytes(n, cfg), dtype=torch.uint8, device="cuda")
     for _ in range(max(args.warmup, 3)):
         greedy = wrs.build_rows_plus(w, rows, ws, info, cfg, 1)
@@ -679,29 +877,37 @@ def run_psa_plus(args, w, w_host, n, cfg, psa_build_ms):
     st = wrs.parse_info(info)["status"]
     if st != wrs.OK:
         raise RuntimeError(f"PSA+ build failed: status {st}")
-    stream = torch.cuda.current_stream()
     ts = []
     for _ in range(args.steps):
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
+        a, e = _events(2)
         a.record(stream)
         wrs.build_rows_plus(w, rows, ws, info, cfg, 1)
-        b.record(stream)
+        e.record(stream)
         torch.cuda.synchronize()
-        ts.append(a.elapsed_time(b))
+        ts.append(a.elapsed_time(e))
     ms = float(np.mean(ts))
-    res = {"ms": ms, "items_per_s": n / (ms / 1e3), "min_items": 1, "tile": 512,
-           "greedy_items": greedy, "greedy_fraction": greedy / n,
-           "speedup_vs_psa": psa_build_ms / ms}
+    res = {"n": n, "ms": ms, "items_per_s": n / (ms / 1e3), "min_items": 1, "tile": 512,
+           "greedy_items": greedy, "greedy_fraction": greedy / n, "psa_ms": psa_ms,
+           "speedup_vs_psa": psa_ms / ms}
     if not args.no_accuracy:
-        raw = rows.cpu().numpy().view(np.uint32).reshape(-1, 2)
-        prob = raw[:, 0].view(np.float32).astype(np.float64)
-        mass = prob + np.bincount(raw[:, 1], weights=1.0 - prob, minlength=n)
-        wd = w_host.astype(np.float64)
-        expect = wd * (n / float(np.sum(wd)))
-        res["max_mass_error"] = float((np.abs(mass - expect) / np.maximum(1.0, expect)).max())
-        del raw, prob, mass, wd, expect
+        res["max_mass_error"] = device_mass_error(rows, w)
     del rows, info, ws
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_psa_plus(args, w, n, cfg, psa_build_ms):
+    """PSA+ on the timed table, and on uniform weights at the paper's sizes
+    (Sec. 6.1 compares PSA+ with PSA on uniform weights)."""
+    import torch
+
+    from paper_2106_12270_gb300 import inputs
+
+    res = {"main": _psa_plus_once(args, w, n, cfg, psa_build_ms)}
+    for nu in (10_000_000, 100_000_000):
+        wu = torch.from_numpy(inputs.uniform(nu, 1)).cuda()
+        res[f"uniform_{nu}"] = _psa_plus_once(args, wu, nu, cfg)
+        del wu
     torch.cuda.empty_cache()
     return res
 

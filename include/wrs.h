@@ -193,8 +193,9 @@ int wrs_build_rows_host(const float *h_w, uint64_t n, wrs_row *h_rows, void *d_w
  * holds until the process exits.
  *  - n must be at most 3,500,000; larger n returns WRS_EINVAL and enqueues
  *    nothing (use wrs_build_rows with a caller workspace instead).
- *  - The first call on a device looks up the array's device address (once per
- *    device, with that device current); make that first call before any
+ *  - Every call looks up the array's device address on the current device
+ *    (this allocates nothing); the first call on a device also loads the
+ *    library's device code there, so make that first call before any
  *    stream capture.
  *  - Every call on a device shares the one array: calls whose work overlaps
  *    on the GPU (different streams, or different host threads) race and give
@@ -389,6 +390,90 @@ int wrs_sample_batched_rows(const wrs_row *d_rows, const uint64_t *d_off, uint32
                             void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Tables and batches as objects (the problem statement's interface)       */
+/* ---------------------------------------------------------------------- */
+/* Sec. 1 states the problem as: build a structure from weights w_1..w_N,
+ * then draw samples i with probability w_i / W.  These calls give exactly
+ * that interface over the buffer calls above: a wrs_table owns the device
+ * rows of one alias table (Sec. 2.2), a wrs_batch those of many.  Objects
+ * belong to the device that was current when they were built; sampling
+ * from another device returns WRS_EINVAL.  Scratch memory of a call is
+ * taken with cudaMallocAsync on the call's stream and freed on it. */
+typedef struct wrs_table wrs_table;
+typedef struct wrs_batch wrs_batch;
+
+/* Process-wide build settings used by wrs_build (section size, split
+ * method); the buffer calls take theirs per call.  wrs_set_config checks
+ * the values as wrs_build_rows does (WRS_EINVAL, nothing changed);
+ * wrs_get_config returns the current ones (wrs_config_default until set). */
+int wrs_set_config(const wrs_config *cfg);
+int wrs_get_config(wrs_config *cfg);
+
+/* Build the alias table of n FP32 weights (PSA, Sec. 2.2 and Sec. 4):
+ * w is a device pointer (w_on_device != 0, 4-byte aligned) or a host
+ * pointer (copied in on `stream`).  The call synchronises `stream` and
+ * returns the build's status: WRS_OK with *out set, or an argument, memory
+ * or data error (WRS_EINVAL for a negative weight, WRS_ENONFINITE,
+ * WRS_EZEROSUM) with *out untouched and nothing left allocated.  The table
+ * equals wrs_build_rows of the same weights under wrs_get_config's settings
+ * bit for bit.  Free it with wrs_table_destroy. */
+int wrs_build(const float *w, uint64_t n, int w_on_device, void *stream, wrs_table **out);
+
+/* Draw `count` samples from a table into d_out (device, count uint32 item
+ * indices) with a sampling mode of Sec. 5 (enum wrs_sample_mode):
+ *  - WRS_SAMPLE_NAIVE: samples 0..count-1 of stream (seed, 0, WRS_TAG_NAIVE),
+ *    as wrs_sample_rows;
+ *  - WRS_SAMPLE_CACHED / WRS_SAMPLE_LIMITED (8192 rows per section) and
+ *    WRS_SAMPLE_SMEM (4096 rows per section): as wrs_sample_sectioned_rows,
+ *    output grouped by section;
+ *  - WRS_SAMPLE_AUTO: as wrs_sample_auto.
+ * Deterministic for (table, count, seed, mode).  Only enqueues work. */
+int wrs_sample(const wrs_table *t, uint64_t count, uint64_t seed, uint32_t *d_out, int mode,
+               void *stream);
+
+/* Size, exact total weight W and light/heavy counts of a built table
+ * (any out pointer may be NULL).  An imported table reports the W it was
+ * given and UINT64_MAX for nl and nh (unknown). */
+int wrs_table_info(const wrs_table *t, uint64_t *n, double *W, uint64_t *nl, uint64_t *nh);
+/* Device pointer to the table's n rows (valid until wrs_table_destroy), for
+ * the buffer calls. */
+int wrs_table_rows(const wrs_table *t, const wrs_row **d_rows);
+/* Copy the n rows into dst (host or device); blocks until done.  This is
+ * the checkpoint path: wrs_table_import restores the same table. */
+int wrs_table_export(const wrs_table *t, wrs_row *dst, int dst_on_device);
+/* A table from n rows (host or device, e.g. written by wrs_table_export)
+ * and its total weight W (NaN if unknown).  The rows are checked on the
+ * device: every prob in [0, 1] and every alias < n, else WRS_EINVAL. */
+int wrs_table_import(const wrs_row *src, uint64_t n, int src_on_device, double W,
+                     wrs_table **out);
+int wrs_table_destroy(wrs_table *t);
+
+/* Build ntab tables of a batch in one launch (as wrs_build_batched_rows,
+ * with the tables handed out largest first and the tiling that
+ * wrs_batch_autotune chose for this batch shape, if it has timed one, else
+ * the default).  d_w, d_off as for wrs_build_batched_rows (device).  The
+ * call synchronises `stream`.  Tables with a data error keep a status
+ * (wrs_batch_status); the others are built.  Returns WRS_EINVAL for
+ * offsets that do not start at 0 or decrease. */
+int wrs_build_batched(const float *d_w, const uint64_t *d_off, uint32_t ntab, void *stream,
+                      wrs_batch **out);
+/* Per-table status (host int32[ntab]) / summaries (host wrs_table_summary[ntab]). */
+int wrs_batch_status(const wrs_batch *b, int32_t *h_status);
+int wrs_batch_summaries(const wrs_batch *b, wrs_table_summary *h_out);
+/* Device rows, device offsets (ntab+1) and table count of a batch (any out
+ * pointer may be NULL). */
+int wrs_batch_rows(const wrs_batch *b, const wrs_row **d_rows, const uint64_t **d_off,
+                   uint32_t *ntab);
+/* Copy the rows of every table (d_off[ntab] rows, table-local aliases) into
+ * dst (host or device); blocks until done. */
+int wrs_batch_export(const wrs_batch *b, wrs_row *dst, int dst_on_device);
+/* Sample every table of a batch in one launch, as wrs_sample_batched_rows:
+ * d_cnt_off (device, ntab+1) delimits each table's samples in d_out. */
+int wrs_sample_batched(const wrs_batch *b, const uint64_t *d_cnt_off, uint64_t seed,
+                       uint32_t *d_out, void *stream);
+int wrs_batch_destroy(wrs_batch *b);
+
+/* ---------------------------------------------------------------------- */
 /* Request loop: resident tables, continuous batching                      */
 /* ---------------------------------------------------------------------- */
 /* A server owns one worker thread on the calling thread's current device.
@@ -451,12 +536,29 @@ int wrs_server_destroy(wrs_server *s);
 
 /* Random-gather probe (the paper has no counterpart; it measures the
  * hardware): `count` uniformly random 8-byte reads from d_rows[0..nrows),
- * one 4-byte store each into d_out[0..count).  The bench uses its rate as
- * the roofline of the naive sampler, whose cost is the same gather.
- * flavor: 0 = read-only path (ld.global.nc), 1 = L2-only (ld.global.cg),
- * 2 = streaming (ld.global.cs).  Contents of d_out are meaningless. */
+ * one 4-byte store each into d_out[0..count).  The bench uses the best rate
+ * over load paths and launch shapes as the roofline of the naive sampler,
+ * whose cost is the same gather.  flavor: 0 = read-only path
+ * (ld.global.nc), 1 = L2-only (ld.global.cg), 2 = streaming (ld.global.cs);
+ * ctas_per_sm: 1..64 CTAs of 256 threads per SM (grid-stride loop);
+ * loads_in_flight: 4, 8 or 16 independent loads per thread.  Contents of
+ * d_out (4-byte aligned) are meaningless. */
 int wrs_diag_random_gather(const wrs_row *d_rows, uint64_t nrows, uint64_t count,
-                           uint64_t seed, int flavor, uint32_t *d_out, void *stream);
+                           uint64_t seed, int flavor, uint32_t ctas_per_sm,
+                           uint32_t loads_in_flight, uint32_t *d_out, void *stream);
+
+/* Per-table baseline of the batched build (measurement support; the paper
+ * has no batched build): builds the tables of a batch laid out as for
+ * wrs_build_batched_rows one after another with wrs_build_rows, one launch
+ * sequence per table, from a loop on the host.  h_off: ntab+1 HOST offsets
+ * (empty tables are skipped); d_ws: a build workspace for the largest table
+ * (wrs_build_workspace_bytes); d_info: ntab device wrs_build_info records.
+ * Rows and summaries equal wrs_build_rows of each segment (so, bit for bit,
+ * the rows of wrs_build_batched_rows).  Returns the first argument or CUDA
+ * error; data errors land in d_info[t].status. */
+int wrs_diag_build_each(const float *d_w, const uint64_t *h_off, uint32_t ntab,
+                        wrs_row *d_rows, void *d_ws, uint64_t ws_bytes,
+                        const wrs_config *cfg, wrs_build_info *d_info, void *stream);
 
 /* Pack variants of Sec. 4.2 (Fig. 3), for measurement: the sweep-pack step
  * (wrs_step_pack) done by a sequential sweep per section instead of the

@@ -29,7 +29,7 @@ __all__ = [
 
 OK, EINVAL, EZEROSUM, ENONFINITE, ENOMEM, ETIMEOUT, ECUDA, EBUSY, ENOTFOUND = range(9)
 SPLIT_PARY, SPLIT_BINARY = 0, 1
-SAMPLE_NAIVE, SAMPLE_CACHED, SAMPLE_LIMITED, SAMPLE_SMEM = 0, 1, 2, 3
+SAMPLE_NAIVE, SAMPLE_CACHED, SAMPLE_LIMITED, SAMPLE_SMEM, SAMPLE_AUTO = 0, 1, 2, 3, 4
 TAG_NAIVE, TAG_SECTION, TAG_COUNTS, TAG_BATCH, TAG_DIAG = 0, 1, 2, 3, 4
 ROW_BYTES = 8
 
@@ -107,7 +107,26 @@ def lib():
                 "wrs_step_pack": (I, [U64, P, P, U64, CP, P]),
                 "wrs_step_info": (I, [U64, P, U64, CP, P, P]),
                 "wrs_sample_rows": (I, [P, U64, U64, U64, U64, U32, U32, P, P]),
-                "wrs_diag_random_gather": (I, [P, U64, U64, U64, I, P, P]),
+                "wrs_diag_random_gather": (I, [P, U64, U64, U64, I, U32, U32, P, P]),
+                "wrs_diag_build_each": (I, [P, P, U32, P, P, U64, CP, P, P]),
+                "wrs_set_config": (I, [CP]),
+                "wrs_get_config": (I, [CP]),
+                "wrs_build": (I, [P, U64, I, P, ctypes.POINTER(P)]),
+                "wrs_sample": (I, [P, U64, U64, P, I, P]),
+                "wrs_table_info": (I, [P, ctypes.POINTER(U64), ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(U64), ctypes.POINTER(U64)]),
+                "wrs_table_rows": (I, [P, ctypes.POINTER(P)]),
+                "wrs_table_export": (I, [P, P, I]),
+                "wrs_table_import": (I, [P, U64, I, ctypes.c_double, ctypes.POINTER(P)]),
+                "wrs_table_destroy": (I, [P]),
+                "wrs_build_batched": (I, [P, P, U32, P, ctypes.POINTER(P)]),
+                "wrs_batch_status": (I, [P, P]),
+                "wrs_batch_summaries": (I, [P, P]),
+                "wrs_batch_rows": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P),
+                                       ctypes.POINTER(U32)]),
+                "wrs_sample_batched": (I, [P, P, U64, P, P]),
+                "wrs_batch_export": (I, [P, P, I]),
+                "wrs_batch_destroy": (I, [P]),
                 "wrs_diag_philox": (I, [U64, U64, P, P]),
                 "wrs_diag_pack_variant": (I, [P, U64, P, P, U64, P, U32, P]),
                 "wrs_build_plus_workspace_bytes": (I, [U64, P, ctypes.POINTER(U64)]),
@@ -197,15 +216,37 @@ def build_rows(w, rows, ws, info, cfg: Config | None = None, stream=None):
     """Enqueue a full build (Sec. 2.2, Sec. 4): w (float32 [n], device) ->
     rows (int64 [n], device, {prob, alias} per row)."""
     n = w.numel()
+    if rows.numel() < n or rows.element_size() != 8:
+        raise ValueError("build_rows: rows must hold n 8-byte rows")
     _check(lib().wrs_build_rows(_ptr(w), n, _ptr(rows), _ptr(ws), ws.numel() * ws.element_size(),
                                 _cfg(cfg), _ptr(info), _stream(stream)), "wrs_build_rows")
 
 
+def _same_device(what: str, dev, *tensors):
+    for t in tensors:
+        if t is not None and t.device != dev:
+            raise ValueError(f"{what}: every tensor must be on {dev}, got {t.device}")
+
+
 def build_rows_noalloc(w, rows, info, cfg: Config | None = None, stream=None):
     """Enqueue a full build that allocates nothing (workspace inside the
-    library; n <= 3.5 million; calls on one device must not overlap)."""
-    _check(lib().wrs_build_rows_noalloc(_ptr(w), w.numel(), _ptr(rows), _cfg(cfg), _ptr(info),
-                                        _stream(stream)), "wrs_build_rows_noalloc")
+    library; n <= 3.5 million; calls on one device must not overlap).
+    w: float32 [n], rows: int64 [n], info: uint8 [INFO_BYTES], all on one
+    CUDA device; the call runs with that device current."""
+    import torch
+    n = w.numel()
+    if not w.is_cuda:
+        raise ValueError("build_rows_noalloc: weights must be on a CUDA device")
+    _same_device("build_rows_noalloc", w.device, rows, info)
+    if w.dtype != torch.float32 or rows.dtype != torch.int64 or rows.numel() != n:
+        raise ValueError("build_rows_noalloc: w must be float32 [n] and rows int64 [n]")
+    if info.numel() * info.element_size() < INFO_BYTES:
+        raise ValueError("build_rows_noalloc: info holds fewer than INFO_BYTES bytes")
+    if stream is not None and stream.device != w.device:
+        raise ValueError("build_rows_noalloc: the stream is on another device")
+    with torch.cuda.device(w.device):
+        _check(lib().wrs_build_rows_noalloc(_ptr(w), n, _ptr(rows), _cfg(cfg), _ptr(info),
+                                            _stream(stream)), "wrs_build_rows_noalloc")
 
 
 def build_host_workspace_bytes(n: int, cfg: Config | None = None) -> int:
@@ -445,10 +486,46 @@ class Server:
             pass
 
 
-def diag_random_gather(rows, nrows: int, count: int, seed: int, flavor: int, out, stream=None):
+def diag_random_gather(rows, nrows: int, count: int, seed: int, flavor: int, out,
+                       ctas_per_sm: int = 8, loads_in_flight: int = 8, stream=None):
     """Enqueue the random-gather probe (measurement support, not the method)."""
-    _check(lib().wrs_diag_random_gather(_ptr(rows), nrows, count, seed, flavor, _ptr(out),
-                                        _stream(stream)), "wrs_diag_random_gather")
+    _check(lib().wrs_diag_random_gather(_ptr(rows), nrows, count, seed, flavor, ctas_per_sm,
+                                        loads_in_flight, _ptr(out), _stream(stream)),
+           "wrs_diag_random_gather")
+
+
+def diag_build_each(w, off_host, rows, reps: int = 1, cfg: Config | None = None, stream=None):
+    """Build every table of a batch (weights w, host offsets off_host, rows
+    as for the batched build) with its own launch sequence of the
+    single-table pipeline (wrs_diag_build_each), `reps` times; returns (mean
+    ms per pass from CUDA events, number of tables whose status is not OK)."""
+    import torch
+    off = np.ascontiguousarray(off_host, np.uint64)
+    ntab = off.size - 1
+    sizes = off[1:] - off[:-1]
+    cap = int(sizes.max()) if ntab else 1
+    ws = torch.empty(build_workspace_bytes(max(cap, 1), cfg), dtype=torch.uint8, device=w.device)
+    info = torch.zeros(max(ntab, 1) * INFO_BYTES, dtype=torch.uint8, device=w.device)
+    st = torch.cuda.current_stream() if stream is None else stream
+
+    def once():
+        _check(lib().wrs_diag_build_each(_ptr(w), off.ctypes.data_as(ctypes.c_void_p), ntab,
+                                         _ptr(rows), _ptr(ws), ws.numel(), _cfg(cfg), _ptr(info),
+                                         ctypes.c_void_p(st.cuda_stream)), "wrs_diag_build_each")
+
+    once()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    for _ in range(reps):
+        once()
+    b.record(st)
+    torch.cuda.synchronize()
+    raw = info.cpu().numpy()[: ntab * INFO_BYTES].tobytes()
+    recs = np.frombuffer(raw, INFO_DTYPE, count=ntab)
+    bad = int(((recs["status"] != OK) & (sizes > 0)).sum())
+    return a.elapsed_time(b) / reps, bad
 
 
 def build_plus_workspace_bytes(n: int, cfg: Config | None = None) -> int:
@@ -525,3 +602,147 @@ class Builder:
             rows = torch.empty(n, dtype=torch.int64, device=w.device)
         build_rows(w, rows, self.ws, self.info, self.cfg, stream)
         return rows
+
+
+# ---------------------------------------------------------------------------
+# Table and batch objects (wrs_build / wrs_sample / wrs_table_* / wrs_batch_*)
+# ---------------------------------------------------------------------------
+
+def set_config(cfg: Config):
+    """Process-wide build settings of Table.build (wrs_set_config)."""
+    _check(lib().wrs_set_config(ctypes.byref(cfg)), "wrs_set_config")
+
+
+def get_config() -> Config:
+    c = Config()
+    _check(lib().wrs_get_config(ctypes.byref(c)), "wrs_get_config")
+    return c
+
+
+class Table:
+    """An alias table owned by the library (wrs_table).  Build it from
+    weights (a torch tensor on the device or the host, or a numpy array),
+    sample it, export and import its rows."""
+
+    def __init__(self, handle):
+        self.h = handle
+
+    @classmethod
+    def build(cls, w, stream=None) -> "Table":
+        """wrs_build: weights (float32, 1-D) -> table; raises WrsError on a
+        data error (negative, non-finite or all-zero weights)."""
+        import torch
+        if isinstance(w, np.ndarray):
+            w = torch.from_numpy(np.ascontiguousarray(w, np.float32))
+        if w.dtype != torch.float32 or w.dim() != 1 or not w.is_contiguous():
+            raise ValueError("weights must be a contiguous 1-D float32 tensor")
+        h = ctypes.c_void_p()
+        _check(lib().wrs_build(_ptr(w), w.numel(), int(w.is_cuda), _stream(stream),
+                               ctypes.byref(h)), "wrs_build")
+        return cls(h)
+
+    @classmethod
+    def import_rows(cls, rows, W: float = float("nan")) -> "Table":
+        """wrs_table_import: rows (int64 tensor, host or device) -> table."""
+        h = ctypes.c_void_p()
+        _check(lib().wrs_table_import(_ptr(rows), rows.numel(), int(rows.is_cuda), W,
+                                      ctypes.byref(h)), "wrs_table_import")
+        return cls(h)
+
+    def sample(self, count: int, seed: int, out, mode: int = SAMPLE_NAIVE, stream=None):
+        """wrs_sample: count draws into out (int32/uint32 tensor on the device)."""
+        _check(lib().wrs_sample(self.h, count, seed & (2**64 - 1), _ptr(out), mode,
+                                _stream(stream)), "wrs_sample")
+        return out
+
+    def info(self) -> dict:
+        n, W, nl, nh = ctypes.c_uint64(), ctypes.c_double(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().wrs_table_info(self.h, ctypes.byref(n), ctypes.byref(W), ctypes.byref(nl),
+                                    ctypes.byref(nh)), "wrs_table_info")
+        return {"n": n.value, "W": W.value, "nl": nl.value, "nh": nh.value}
+
+    def rows_ptr(self) -> int:
+        p = ctypes.c_void_p()
+        _check(lib().wrs_table_rows(self.h, ctypes.byref(p)), "wrs_table_rows")
+        return p.value
+
+    def export(self, dst=None, device=False):
+        """wrs_table_export into dst (int64 [n], host or device; allocated
+        on the host, or the device if device=True, when dst is None)."""
+        import torch
+        n = self.info()["n"]
+        if dst is None:
+            dst = torch.empty(n, dtype=torch.int64, device="cuda" if device else "cpu")
+        _check(lib().wrs_table_export(self.h, _ptr(dst), int(dst.is_cuda)), "wrs_table_export")
+        return dst
+
+    def close(self):
+        if self.h:
+            _check(lib().wrs_table_destroy(self.h), "wrs_table_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many tables built in one launch (wrs_build_batched / wrs_batch_*)."""
+
+    def __init__(self, handle):
+        self.h = handle
+
+    @classmethod
+    def build(cls, w, off, stream=None) -> "Batch":
+        """w: float32 device tensor of all tables' weights; off: int64 device
+        tensor of ntab+1 offsets."""
+        h = ctypes.c_void_p()
+        _check(lib().wrs_build_batched(_ptr(w), _ptr(off), off.numel() - 1, _stream(stream),
+                                       ctypes.byref(h)), "wrs_build_batched")
+        return cls(h)
+
+    def _rows(self):
+        r, o, nt = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_uint32()
+        _check(lib().wrs_batch_rows(self.h, ctypes.byref(r), ctypes.byref(o), ctypes.byref(nt)),
+               "wrs_batch_rows")
+        return r.value, o.value, nt.value
+
+    @property
+    def ntab(self) -> int:
+        return self._rows()[2]
+
+    def status(self) -> np.ndarray:
+        st = np.zeros(max(self.ntab, 1), np.int32)
+        _check(lib().wrs_batch_status(self.h, st.ctypes.data_as(ctypes.c_void_p)),
+               "wrs_batch_status")
+        return st[: self.ntab]
+
+    def summaries(self) -> np.ndarray:
+        out = np.zeros(max(self.ntab, 1), SUMMARY_DTYPE)
+        _check(lib().wrs_batch_summaries(self.h, out.ctypes.data_as(ctypes.c_void_p)),
+               "wrs_batch_summaries")
+        return out[: self.ntab]
+
+    def export(self, dst):
+        """wrs_batch_export: copy all rows of the batch (table-local aliases)
+        into dst (int64 [total items], host or device)."""
+        _check(lib().wrs_batch_export(self.h, _ptr(dst), int(dst.is_cuda)), "wrs_batch_export")
+        return dst
+
+    def sample(self, cnt_off, seed: int, out, stream=None):
+        _check(lib().wrs_sample_batched(self.h, _ptr(cnt_off), seed & (2**64 - 1), _ptr(out),
+                                        _stream(stream)), "wrs_sample_batched")
+        return out
+
+    def close(self):
+        if self.h:
+            _check(lib().wrs_batch_destroy(self.h), "wrs_batch_destroy")
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

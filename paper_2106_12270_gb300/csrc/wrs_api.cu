@@ -26,8 +26,8 @@ cudaError_t launch_sample_sectioned(const wrs_row *, uint64_t, uint64_t, uint64_
 
 cudaError_t launch_sample_batched(const wrs_row *, const uint64_t *, uint32_t, const uint64_t *,
                                   uint64_t, uint32_t *, cudaStream_t);
-cudaError_t launch_random_gather(const void *, uint64_t, uint64_t, uint64_t, int, uint32_t *,
-                                 cudaStream_t);
+cudaError_t launch_random_gather(const void *, uint64_t, uint64_t, uint64_t, int, uint32_t,
+                                 uint32_t, uint32_t *, cudaStream_t);
 cudaError_t launch_philox_rate(uint64_t, uint64_t, uint32_t *, cudaStream_t);
 cudaError_t launch_pack_variant(const float *, uint64_t, wrs_row *, unsigned char *, const Layout &,
                                 uint32_t, uint32_t, cudaStream_t);
@@ -92,7 +92,7 @@ const char *wrs_strerror(int s) {
 
 int wrs_last_cuda_error(void) { return g_last_cuda; }
 
-int wrs_abi_version(void) { return 1; }
+int wrs_abi_version(void) { return 2; }
 
 void wrs_config_default(wrs_config *cfg) {
     if (!cfg) return;
@@ -416,6 +416,17 @@ std::mutex g_tune_mu;
 std::map<std::pair<uint32_t, uint64_t>, wrs_batch_tuning> g_tune_cache;
 }  // namespace
 
+namespace wrs {
+// The autotuner's choice for a batch shape, if it has timed one.
+bool cached_batch_tuning(uint32_t ntab, uint64_t total, wrs_batch_tuning *out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(std::make_pair(ntab, total));
+    if (it == g_tune_cache.end()) return false;
+    *out = it->second;
+    return true;
+}
+}  // namespace wrs
+
 extern "C" {
 
 int wrs_batch_autotune(const float *d_w, const uint64_t *d_off, uint32_t ntab,
@@ -507,12 +518,15 @@ int wrs_sample_batched_rows(const wrs_row *d_rows, const uint64_t *d_off, uint32
 }
 
 int wrs_diag_random_gather(const wrs_row *d_rows, uint64_t nrows, uint64_t count, uint64_t seed,
-                           int flavor, uint32_t *d_out, void *stream) {
+                           int flavor, uint32_t ctas_per_sm, uint32_t loads_in_flight,
+                           uint32_t *d_out, void *stream) {
     if (!d_rows || nrows == 0 || ((uintptr_t)d_rows & 7u)) return WRS_EINVAL;
-    if (count && !d_out) return WRS_EINVAL;
+    if (count && (!d_out || ((uintptr_t)d_out & 3u))) return WRS_EINVAL;
     if (flavor < 0 || flavor > 2) return WRS_EINVAL;
-    return cuda_status(
-        launch_random_gather(d_rows, nrows, count, seed, flavor, d_out, (cudaStream_t)stream));
+    if (ctas_per_sm < 1 || ctas_per_sm > 64) return WRS_EINVAL;
+    if (loads_in_flight != 4 && loads_in_flight != 8 && loads_in_flight != 16) return WRS_EINVAL;
+    return cuda_status(launch_random_gather(d_rows, nrows, count, seed, flavor, ctas_per_sm,
+                                            loads_in_flight, d_out, (cudaStream_t)stream));
 }
 
 int wrs_diag_pack_variant(const float *d_w, uint64_t n, wrs_row *d_rows, void *d_ws,

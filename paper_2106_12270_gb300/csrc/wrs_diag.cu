@@ -33,12 +33,11 @@ __device__ __forceinline__ uint2 load_row(const uint2 *p) {
     return __ldcs(p);                     // streaming (evict first)
 }
 
-template <int kFlavor>
+template <int kFlavor, int U>
 __global__ void __launch_bounds__(256)
 k_random_gather(const uint2 *__restrict__ rows, uint64_t nrows, uint64_t count, uint64_t seed,
                 uint32_t *__restrict__ out) {
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
-    constexpr int U = 8;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += U * T) {
         uint2 r[U];
 #pragma unroll
@@ -91,16 +90,28 @@ cudaError_t launch_philox_rate(uint64_t count, uint64_t seed, uint32_t *out, cud
 }
 
 
-cudaError_t launch_random_gather(const void *rows, uint64_t nrows, uint64_t count, uint64_t seed,
-                                 int flavor, uint32_t *out, cudaStream_t st) {
-    unsigned blocks = (unsigned)num_sms() * 8;
-    const uint2 *r = reinterpret_cast<const uint2 *>(rows);
-    if (flavor == 0)
-        k_random_gather<0><<<blocks, 256, 0, st>>>(r, nrows, count, seed, out);
-    else if (flavor == 1)
-        k_random_gather<1><<<blocks, 256, 0, st>>>(r, nrows, count, seed, out);
+template <int kFlavor>
+static void launch_gather_u(const uint2 *r, uint64_t nrows, uint64_t count, uint64_t seed,
+                            unsigned blocks, uint32_t unroll, uint32_t *out, cudaStream_t st) {
+    if (unroll == 4)
+        k_random_gather<kFlavor, 4><<<blocks, 256, 0, st>>>(r, nrows, count, seed, out);
+    else if (unroll == 8)
+        k_random_gather<kFlavor, 8><<<blocks, 256, 0, st>>>(r, nrows, count, seed, out);
     else
-        k_random_gather<2><<<blocks, 256, 0, st>>>(r, nrows, count, seed, out);
+        k_random_gather<kFlavor, 16><<<blocks, 256, 0, st>>>(r, nrows, count, seed, out);
+}
+
+// Launch shape: ctas_per_sm CTAs of 256 threads per SM (a grid-stride loop),
+// `unroll` independent loads in flight per thread.
+cudaError_t launch_random_gather(const void *rows, uint64_t nrows, uint64_t count, uint64_t seed,
+                                 int flavor, uint32_t ctas_per_sm, uint32_t unroll, uint32_t *out,
+                                 cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    unsigned blocks = (unsigned)num_sms() * ctas_per_sm;
+    const uint2 *r = reinterpret_cast<const uint2 *>(rows);
+    if (flavor == 0) launch_gather_u<0>(r, nrows, count, seed, blocks, unroll, out, st);
+    else if (flavor == 1) launch_gather_u<1>(r, nrows, count, seed, blocks, unroll, out, st);
+    else launch_gather_u<2>(r, nrows, count, seed, blocks, unroll, out, st);
     return cudaGetLastError();
 }
 

@@ -9,8 +9,6 @@
 // takes a caller workspace; this variant takes none at all: its workspace is
 // a file-scope device array of a fixed size, kNoAllocBytes, which every GPU
 // that loads this library holds until the process exits.
-#include <mutex>
-
 #include "wrs_internal.cuh"
 
 namespace wrs {
@@ -33,24 +31,17 @@ constexpr uint64_t kNoAllocMaxItems = 3500000ull;    // a build's workspace fits
 // device array: its device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_ws[kNoAllocBytes];
 
-static std::mutex g_noalloc_mu;
-static unsigned char *g_noalloc_ptr[256];   // device address per device ordinal
-
-// Device address of the scratch on the current device, looked up once per
-// device (with that device current) on the first call made on it.
+// Device address of the scratch on the current device.  It is looked up on
+// every call (the lookup allocates nothing and costs little), so a call made
+// after the context was torn down and created again sees the array's new
+// address.  The first lookup on a device loads this library's module there,
+// which is why the first call on a device should come before any stream
+// capture.
 static cudaError_t noalloc_scratch(unsigned char **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_ws);
     if (e) return e;
-    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_ws);
-        if (e) return e;
-        g_noalloc_ptr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_noalloc_ptr[dev];
+    *out = static_cast<unsigned char *>(p);
     return cudaSuccess;
 }
 

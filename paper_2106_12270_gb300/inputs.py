@@ -16,29 +16,45 @@ those and the other shapes the workloads use:
 * ``batched``           many segments of the above, concatenated, with
                         64-bit offsets.
 
-All use ``numpy.random.default_rng(seed)`` and draw in chunks of 2^24 so the
-host never holds more than one FP64 chunk at a time.
+The elementwise draws (uniform, exponential, gamma) come in chunks of 2^24
+items: chunk k is drawn in FP64 by ``numpy.random.default_rng([seed, k])``
+and rounded to FP32, so every chunk is its own seeded stream and the chunks
+are filled by a pool of host threads (numpy releases the GIL while it
+draws).  The permutation of ``zipf_permuted`` comes from one
+``default_rng(seed)`` stream.
 """
 from __future__ import annotations
 
+import concurrent.futures as cf
 import math
+import os
 
 import numpy as np
 
 _CHUNK = 1 << 24
 
 
-def _chunked(n: int, draw) -> np.ndarray:
+def _chunked(n: int, seed: int, draw) -> np.ndarray:
+    """out[k*2^24 : (k+1)*2^24] = draw(default_rng([seed, k]), size) as FP32."""
     out = np.empty(n, np.float32)
-    for a in range(0, n, _CHUNK):
+
+    def fill(k):
+        a = k * _CHUNK
         b = min(n, a + _CHUNK)
-        out[a:b] = draw(b - a).astype(np.float32)
+        out[a:b] = draw(np.random.default_rng([seed, k]), b - a).astype(np.float32)
+
+    nchunks = (n + _CHUNK - 1) // _CHUNK
+    if nchunks <= 1:
+        for k in range(nchunks):
+            fill(k)
+    else:
+        with cf.ThreadPoolExecutor(max_workers=min(nchunks, os.cpu_count() or 1)) as ex:
+            list(ex.map(fill, range(nchunks)))
     return out
 
 
 def uniform(n: int, seed: int) -> np.ndarray:
-    rng = np.random.default_rng(seed)
-    return _chunked(n, lambda m: rng.random(m))
+    return _chunked(n, seed, lambda rng, m: rng.random(m))
 
 
 def zipf_permuted(n: int, seed: int, s: float = 1.0) -> np.ndarray:
@@ -52,13 +68,11 @@ def zipf_permuted(n: int, seed: int, s: float = 1.0) -> np.ndarray:
 
 
 def exponential(n: int, seed: int) -> np.ndarray:
-    rng = np.random.default_rng(seed)
-    return _chunked(n, lambda m: rng.exponential(1.0, m))
+    return _chunked(n, seed, lambda rng, m: rng.exponential(1.0, m))
 
 
 def gamma(n: int, seed: int, shape: float = 0.1) -> np.ndarray:
-    rng = np.random.default_rng(seed)
-    return _chunked(n, lambda m: rng.gamma(shape, 1.0, m))
+    return _chunked(n, seed, lambda rng, m: rng.gamma(shape, 1.0, m))
 
 
 def log_uniform_sizes(count: int, seed: int, lo: int, hi: int) -> np.ndarray:

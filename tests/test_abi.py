@@ -80,6 +80,51 @@ def test_host_argument_checks(lib):
     assert lib.wrs_strerror(wrs.EZEROSUM) == b"all weights are zero"
 
 
+def test_handle_calls_check_arguments_on_the_host(lib):
+    P = ctypes.c_void_p
+    h = P()
+    # build(weights) -> table: bad sizes and pointers fail before any CUDA call
+    assert lib.wrs_build(None, 10, 1, None, ctypes.byref(h)) == wrs.EINVAL
+    assert lib.wrs_build(P(256), 0, 1, None, ctypes.byref(h)) == wrs.EINVAL
+    assert lib.wrs_build(P(256), 2**31, 1, None, ctypes.byref(h)) == wrs.EINVAL
+    assert lib.wrs_build(P(258), 10, 1, None, ctypes.byref(h)) == wrs.EINVAL   # misaligned
+    assert lib.wrs_build(P(256), 10, 1, None, None) == wrs.EINVAL
+    assert h.value is None
+    assert lib.wrs_sample(None, 5, 1, P(256), wrs.SAMPLE_NAIVE, None) == wrs.EINVAL
+    assert lib.wrs_table_info(None, None, None, None, None) == wrs.EINVAL
+    assert lib.wrs_table_export(None, P(256), 0) == wrs.EINVAL
+    assert lib.wrs_table_import(None, 10, 0, 1.0, ctypes.byref(h)) == wrs.EINVAL
+    assert lib.wrs_table_destroy(None) == wrs.OK
+    assert lib.wrs_build_batched(None, None, 3, None, ctypes.byref(h)) == wrs.EINVAL
+    assert lib.wrs_build_batched(P(256), P(256), 0, None, ctypes.byref(h)) == wrs.EINVAL
+    assert lib.wrs_batch_status(None, None) == wrs.EINVAL
+    assert lib.wrs_sample_batched(None, P(256), 1, P(256), None) == wrs.EINVAL
+    assert lib.wrs_batch_destroy(None) == wrs.OK
+    # process-wide build settings: checked like a per-call config
+    cur = wrs.Config()
+    assert lib.wrs_get_config(ctypes.byref(cur)) == wrs.OK
+    assert lib.wrs_set_config(ctypes.byref(wrs.config(section_size=300))) == wrs.EINVAL
+    after = wrs.Config()
+    lib.wrs_get_config(ctypes.byref(after))
+    assert after.section_size == cur.section_size
+    # measurement calls
+    assert lib.wrs_diag_random_gather(P(256), 10, 5, 1, 0, 0, 8, P(256), None) == wrs.EINVAL
+    assert lib.wrs_diag_random_gather(P(256), 10, 5, 1, 0, 8, 3, P(256), None) == wrs.EINVAL
+    assert lib.wrs_diag_random_gather(P(256), 10, 5, 1, 3, 8, 8, P(256), None) == wrs.EINVAL
+    assert lib.wrs_diag_build_each(None, None, 3, None, None, 0, None, None, None) == wrs.EINVAL
+
+
+def test_noalloc_array_holds_the_largest_accepted_build(lib):
+    # the allocation-free build accepts n <= 3.5 million with any section
+    # size; its workspace is a 32 MiB array, and the layout is largest for
+    # the smallest sections
+    out = ctypes.c_uint64()
+    for sec in (256, 1024, 8192):
+        c = wrs.config(section_size=sec)
+        assert lib.wrs_build_workspace_bytes(3_500_000, ctypes.byref(c), ctypes.byref(out)) == wrs.OK
+        assert out.value <= 32 << 20, (sec, out.value)
+
+
 def test_layout_is_aligned_and_ordered(lib):
     for n in (1, 31, 4096, 10**6 + 3):
         L = wrs.build_layout(n)
