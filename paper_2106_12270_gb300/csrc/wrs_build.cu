@@ -817,6 +817,62 @@ __host__ __device__ inline uint32_t pack_slots(uint32_t S) { return pk16(S + 1) 
 __host__ __device__ inline uint32_t pack_smem_bytes(uint32_t S) { return 16 * pack_slots(S); }
 
 
+// Multi-word helpers of the pack's key pass: a 128-bit two's-complement
+// value in four 32-bit limbs, low limb first.
+struct Limbs4 {
+    uint32_t w0, w1, w2, w3;
+};
+__device__ __forceinline__ Limbs4 to_limbs(u128 v) {
+    return Limbs4{(uint32_t)v, (uint32_t)(v >> 32), (uint32_t)(v >> 64), (uint32_t)(v >> 96)};
+}
+__device__ __forceinline__ u128 from_limbs(const Limbs4 &a) {
+    return ((u128)(((uint64_t)a.w3 << 32) | a.w2) << 64) | (((uint64_t)a.w1 << 32) | a.w0);
+}
+// low 64 bits of N q (exact when N q < 2^64)
+__device__ __forceinline__ uint64_t mul_lo_nq(uint32_t N, uint64_t q) {
+    const uint64_t lo = (uint64_t)(uint32_t)q * N;
+    return lo + ((uint64_t)((uint32_t)(q >> 32) * N) << 32);
+}
+// a += v for v < 2^64, where the sum stays below 2^96 (the top limb is left as is)
+__device__ __forceinline__ void add96(Limbs4 &a, uint64_t v) {
+    asm("add.cc.u32 %0, %0, %3;\n\t"
+        "addc.cc.u32 %1, %1, %4;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "+r"(a.w0), "+r"(a.w1), "+r"(a.w2)
+        : "r"((uint32_t)v), "r"((uint32_t)(v >> 32)));
+}
+// a += N q - Q (a heavy's scaled excess, below 2^95; q < 2^63, Q < 2^63)
+__device__ __forceinline__ void add_excess(Limbs4 &a, uint32_t N, uint64_t q, uint64_t Q) {
+    const uint64_t lo = (uint64_t)(uint32_t)q * N;           // bits 0..63
+    const uint64_t hi = (uint64_t)(uint32_t)(q >> 32) * N;   // bits 32..95
+    uint32_t e0, e1, e2;
+    asm("add.cc.u32 %1, %4, %6;\n\t"     // e1 = lo.hi + hi.lo
+        "addc.u32 %2, %7, 0;\n\t"        // e2 = hi.hi + carry
+        "sub.cc.u32 %0, %3, %8;\n\t"     // e0 = lo.lo - Q.lo
+        "subc.cc.u32 %1, %1, %9;\n\t"    // e1 -= Q.hi
+        "subc.u32 %2, %2, 0;"
+        : "=r"(e0), "=r"(e1), "=r"(e2)
+        : "r"((uint32_t)lo), "r"((uint32_t)(lo >> 32)), "r"(0u), "r"((uint32_t)hi),
+          "r"((uint32_t)(hi >> 32)), "r"((uint32_t)Q), "r"((uint32_t)(Q >> 32)));
+    asm("add.cc.u32 %0, %0, %4;\n\t"
+        "addc.cc.u32 %1, %1, %5;\n\t"
+        "addc.cc.u32 %2, %2, %6;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "+r"(a.w0), "+r"(a.w1), "+r"(a.w2), "+r"(a.w3)
+        : "r"(e0), "r"(e1), "r"(e2));
+}
+// floor(a / 2^15) as a signed 64-bit key, for |a| < 2^78
+__device__ __forceinline__ int64_t key15(const Limbs4 &a) {
+    const uint32_t lo = __funnelshift_r(a.w0, a.w1, kKeyShift);
+    const uint32_t hi = __funnelshift_r(a.w1, a.w2, kKeyShift);
+    return (int64_t)(((uint64_t)hi << 32) | lo);
+}
+// the same, capped at 2^62 (a heavy that cannot close in its section)
+__device__ __forceinline__ int64_t key15_capped(const Limbs4 &a) {
+    const bool big = (int32_t)a.w3 > 0 || (a.w3 == 0 && a.w2 >= (1u << (kKeyCap62 + kKeyShift - 64)));
+    return big ? ((int64_t)1 << kKeyCap62) : key15(a);
+}
+
 template <int kPer>
 __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
                                              const Entry *__restrict__ lh,
@@ -869,27 +925,36 @@ __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
     // - N q and over heavies of e' = N q - Q, i.e. (nl - nh) Q + N (sum of
     // heavy q - sum of light q); then a block scan of the thread sums.
     const uint32_t b0 = tid * kPer;
+    // positions b0 .. b0+nlt-1 are lights, b0+nlt .. b0+nvt-1 heavies
+    const uint32_t nlt = L > b0 ? min(L - b0, (uint32_t)kPer) : 0u;
+    const uint32_t nvt = K > b0 ? min(K - b0, (uint32_t)kPer) : 0u;
     uint64_t qv[kPer];
     uint64_t sql = 0, sqh = 0;
-    uint32_t nlt = 0, nht = 0;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
-        const uint32_t e = b0 + k;
-        qv[k] = 0;
-        if (e < K) {
-            const uint64_t q = fixed_q(__uint_as_float(sE[pk16(e)].y), qsc);
-            if (e < L) {
-                qv[k] = q > Qn ? Qn : q;
-                sql += qv[k];
-                ++nlt;
-            } else {
-                qv[k] = q <= Qn ? Qn + 1 : q;
-                sqh += qv[k];
-                ++nht;
-            }
+        uint64_t q = fixed_q(__uint_as_float(sE[pk16(b0 + k)].y), qsc);
+        if ((uint32_t)k < nlt) {
+            q = q > Qn ? Qn : q;
+            sql += q;
+        } else {
+            q = q <= Qn ? Qn + 1 : q;
+            sqh += (uint32_t)k < nvt ? q : 0ull;
         }
+        qv[k] = q;
     }
-    const u128 run = (u128)nlt * Q - (u128)nht * Q + (u128)N * sqh - (u128)N * sql;
+    // the thread's value sum N (sqh - sql) + (nlt - nht) Q, two's complement
+    u128 run;
+    {
+        const bool neg = sqh < sql;
+        const uint64_t mag = neg ? sql - sqh : sqh - sql;   // < 2^63
+        const uint64_t lo = (uint64_t)(uint32_t)mag * N;
+        const uint64_t hi = (uint64_t)(uint32_t)(mag >> 32) * N;
+        u128 v = (u128)lo + ((u128)hi << 32);
+        const int c = 2 * (int)nlt - (int)nvt;                // nlt - nht
+        const uint64_t cm = (uint64_t)(c < 0 ? -c : c);
+        const u128 cq = (u128)((uint64_t)(uint32_t)Q * cm) + ((u128)((Q >> 32) * cm) << 32);
+        run = (neg ? (u128)0 - v : v) + (c < 0 ? (u128)0 - cq : cq);
+    }
     u128 inc = run;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -903,9 +968,10 @@ __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
     // D0 + P(x), so A(x) = floor((D0 mod 2^15 + P(x)) / 2^15); E'(j0+y+1) =
     // E0 + P(L+y+1) - P(L) with P(L) = D1 - D0 (the section's light deficit,
     // fixed by the split), so B(y) = floor((E0 - D1 + D0 mod 2^15 +
-    // P(L+y+1)) / 2^15).
+    // P(L+y+1)) / 2^15).  The running value is kept in 32-bit limbs: a light
+    // adds its deficit Q - N q (< 2^63), a heavy its excess N q - Q; the heavy
+    // keys run on ch + p.
     {
-        // p = P(x) + (D0 mod 2^15): the light keys are p >> 15 directly
         const u128 d0l = R0.D & (u128)((1u << kKeyShift) - 1);
         u128 p = inc - run + d0l;
         for (int k = 0; k < warp; ++k) p += s_w[k];
@@ -914,23 +980,26 @@ __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
             sK[pk16(0)] = 0;
             sK[pk16(K + 1)] = INT64_MAX;   // after the last heavy: never closes
         }
+        Limbs4 a = to_limbs(nlt > 0 ? p : ch + p);
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             const uint32_t e = b0 + k;
-            if (e < K) {
-                if (e < L) {
-                    p += (u128)(Q - (uint64_t)N * qv[k]);
-                    sK[pk16(e + 1)] = (int64_t)(p >> kKeyShift);   // < 2^61
-                } else {
-                    p += mul_nq(N, qv[k]) - Q;
-                    sK[pk16(e + 1)] = sweep_key(ch, p);
-                }
+            if ((uint32_t)k < nlt) {
+                add96(a, Q - mul_lo_nq(N, qv[k]));
+                sK[pk16(e + 1)] = key15(a);   // < 2^61
+                if ((uint32_t)k + 1 == nlt && nlt < nvt) a = to_limbs(ch + from_limbs(a));
+            } else if ((uint32_t)k < nvt) {
+                add_excess(a, N, qv[k], Q);
+                sK[pk16(e + 1)] = key15_capped(a);
             }
         }
         // the section's own sums must meet the split's: the thread holding
         // position K-1 has P(K) = D1 - D0 + E1 - E0
-        if (b0 < K && b0 + kPer >= K && p - d0l != (R1.D - R0.D) + (R1.E - R0.E))
-            atomicOr(const_cast<uint32_t *>(&P->status), ERR_INTERNAL);
+        if (b0 < K && b0 + kPer >= K) {
+            const u128 pend = from_limbs(a) - (nvt > nlt ? ch : (u128)0);
+            if (pend - d0l != (R1.D - R0.D) + (R1.E - R0.E))
+                atomicOr(const_cast<uint32_t *>(&P->status), ERR_INTERNAL);
+        }
     }
     __syncthreads();
 
