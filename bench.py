@@ -843,8 +843,8 @@ def run_sampler_heatmap(args):
 
 
 def _psa_plus_once(args, w, n, cfg, psa_ms=None):
-    """PSA+ (Sec. 4 "PSA+") on one table: greedy packing per 512-item
-    partition chunk, PSA on the rest.  Each call reads the rest's size back
+    """PSA+ (Sec. 4 "PSA+") on one table: greedy packing per tile of 1024
+    items, PSA on the rest.  Each call reads the rest's size back
     once (a host sync), which the events around it include.  PSA is timed on
     the same table unless its time is given."""
     import numpy as np
@@ -886,7 +886,7 @@ def _psa_plus_once(args, w, n, cfg, psa_ms=None):
         torch.cuda.synchronize()
         ts.append(a.elapsed_time(e))
     ms = float(np.mean(ts))
-    res = {"n": n, "ms": ms, "items_per_s": n / (ms / 1e3), "min_items": 1, "tile": 512,
+    res = {"n": n, "ms": ms, "items_per_s": n / (ms / 1e3), "min_items": 1, "tile": 1024,
            "greedy_items": greedy, "greedy_fraction": greedy / n, "psa_ms": psa_ms,
            "speedup_vs_psa": psa_ms / ms}
     if not args.no_accuracy:

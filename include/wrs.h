@@ -152,19 +152,21 @@ int wrs_build_rows(const float *d_w, uint64_t n, wrs_row *d_rows,
                    void *d_ws, uint64_t ws_bytes, const wrs_config *cfg,
                    wrs_build_info *d_info, void *stream);
 
-/* PSA+ construction (Sec. 4 "PSA+"): greedy packing inside every partition
- * chunk of 512 items that holds at least min_items light and heavy items
- * (their lights and heavies swept as in PSA until the current heavy is above
- * the average with no light left, or at most the average with no next heavy
- * in the chunk), then the PSA construction on the items left over, in index
- * order; the heavy current at the stop carries its remaining weight.  The table is a valid alias table for w (tested by
- * reconstructed mass) but not the same table as wrs_build_rows'.
+/* PSA+ construction (Sec. 4 "PSA+"): greedy packing inside every tile of
+ * 1024 consecutive items that holds at least min_items light and heavy
+ * items (the tile's lights and heavies, each in index order, swept as in
+ * PSA until the current heavy is above the average with no light left, or
+ * at most the average with no next heavy in the tile), then the PSA
+ * construction on the items left over, in index order; the heavy current at
+ * the stop carries its remaining weight.  The table is a valid alias table
+ * for w (tested by reconstructed mass) but not the same table as
+ * wrs_build_rows'.
  * d_ws: at least wrs_build_plus_workspace_bytes(n, cfg) bytes, 256-byte
  * aligned.  *greedy_items (host, may be NULL) receives how many items the
- * greedy step finished (0 when a whole-table step failed).  Unlike wrs_build_rows this call synchronises
- * `stream` once (the size of the rest decides its launches).  Errors as
- * wrs_build_rows; with min_items larger than 512 it builds wrs_build_rows'
- * table. */
+ * greedy step finished (0 when a whole-table step failed).  Unlike
+ * wrs_build_rows this call synchronises `stream` once (the size of the rest
+ * decides its launches).  Errors as wrs_build_rows; with min_items larger
+ * than 1024 it builds wrs_build_rows' table. */
 int wrs_build_plus_workspace_bytes(uint64_t n, const wrs_config *cfg, uint64_t *bytes);
 int wrs_build_rows_plus(const float *d_w, uint64_t n, wrs_row *d_rows, void *d_ws,
                         uint64_t ws_bytes, const wrs_config *cfg, uint32_t min_items,

@@ -817,62 +817,6 @@ __host__ __device__ inline uint32_t pack_slots(uint32_t S) { return pk16(S + 1) 
 __host__ __device__ inline uint32_t pack_smem_bytes(uint32_t S) { return 16 * pack_slots(S); }
 
 
-// Multi-word helpers of the pack's key pass: a 128-bit two's-complement
-// value in four 32-bit limbs, low limb first.
-struct Limbs4 {
-    uint32_t w0, w1, w2, w3;
-};
-__device__ __forceinline__ Limbs4 to_limbs(u128 v) {
-    return Limbs4{(uint32_t)v, (uint32_t)(v >> 32), (uint32_t)(v >> 64), (uint32_t)(v >> 96)};
-}
-__device__ __forceinline__ u128 from_limbs(const Limbs4 &a) {
-    return ((u128)(((uint64_t)a.w3 << 32) | a.w2) << 64) | (((uint64_t)a.w1 << 32) | a.w0);
-}
-// low 64 bits of N q (exact when N q < 2^64)
-__device__ __forceinline__ uint64_t mul_lo_nq(uint32_t N, uint64_t q) {
-    const uint64_t lo = (uint64_t)(uint32_t)q * N;
-    return lo + ((uint64_t)((uint32_t)(q >> 32) * N) << 32);
-}
-// a += v for v < 2^64, where the sum stays below 2^96 (the top limb is left as is)
-__device__ __forceinline__ void add96(Limbs4 &a, uint64_t v) {
-    asm("add.cc.u32 %0, %0, %3;\n\t"
-        "addc.cc.u32 %1, %1, %4;\n\t"
-        "addc.u32 %2, %2, 0;"
-        : "+r"(a.w0), "+r"(a.w1), "+r"(a.w2)
-        : "r"((uint32_t)v), "r"((uint32_t)(v >> 32)));
-}
-// a += N q - Q (a heavy's scaled excess, below 2^95; q < 2^63, Q < 2^63)
-__device__ __forceinline__ void add_excess(Limbs4 &a, uint32_t N, uint64_t q, uint64_t Q) {
-    const uint64_t lo = (uint64_t)(uint32_t)q * N;           // bits 0..63
-    const uint64_t hi = (uint64_t)(uint32_t)(q >> 32) * N;   // bits 32..95
-    uint32_t e0, e1, e2;
-    asm("add.cc.u32 %1, %4, %6;\n\t"     // e1 = lo.hi + hi.lo
-        "addc.u32 %2, %7, 0;\n\t"        // e2 = hi.hi + carry
-        "sub.cc.u32 %0, %3, %8;\n\t"     // e0 = lo.lo - Q.lo
-        "subc.cc.u32 %1, %1, %9;\n\t"    // e1 -= Q.hi
-        "subc.u32 %2, %2, 0;"
-        : "=r"(e0), "=r"(e1), "=r"(e2)
-        : "r"((uint32_t)lo), "r"((uint32_t)(lo >> 32)), "r"(0u), "r"((uint32_t)hi),
-          "r"((uint32_t)(hi >> 32)), "r"((uint32_t)Q), "r"((uint32_t)(Q >> 32)));
-    asm("add.cc.u32 %0, %0, %4;\n\t"
-        "addc.cc.u32 %1, %1, %5;\n\t"
-        "addc.cc.u32 %2, %2, %6;\n\t"
-        "addc.u32 %3, %3, 0;"
-        : "+r"(a.w0), "+r"(a.w1), "+r"(a.w2), "+r"(a.w3)
-        : "r"(e0), "r"(e1), "r"(e2));
-}
-// floor(a / 2^15) as a signed 64-bit key, for |a| < 2^78
-__device__ __forceinline__ int64_t key15(const Limbs4 &a) {
-    const uint32_t lo = __funnelshift_r(a.w0, a.w1, kKeyShift);
-    const uint32_t hi = __funnelshift_r(a.w1, a.w2, kKeyShift);
-    return (int64_t)(((uint64_t)hi << 32) | lo);
-}
-// the same, capped at 2^62 (a heavy that cannot close in its section)
-__device__ __forceinline__ int64_t key15_capped(const Limbs4 &a) {
-    const bool big = (int32_t)a.w3 > 0 || (a.w3 == 0 && a.w2 >= (1u << (kKeyCap62 + kKeyShift - 64)));
-    return big ? ((int64_t)1 << kKeyCap62) : key15(a);
-}
-
 template <int kPer>
 __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
                                              const Entry *__restrict__ lh,

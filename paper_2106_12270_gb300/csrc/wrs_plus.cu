@@ -1,36 +1,38 @@
 // wrs_plus.cu - PSA+ construction (Sec. 4 "PSA+") on GB300 (sm_103a).
 //
-// PSA+ packs greedily while the partition has a tile of items in shared
-// memory: the tile's lights and heavies (index order) are swept as in PSA
-// until the current heavy is still above the average with no light left to
-// fill, or has fallen to it with no next heavy to close it with.  Only the items that sweep did not finish go on to the
-// full PSA construction.  Here a tile is one partition chunk of kChunk items
-// (a warp's unit of work), eligible when it holds at least `min_items` lights
-// and heavies.
+// PSA+ packs greedily while a tile of items is in shared memory: the tile's
+// lights and heavies (index order) are swept as in PSA until the current
+// heavy is still above the average with no light left to fill, or has
+// fallen to it with no next heavy to close it with.  Only the items that
+// sweep did not finish go on to the full PSA construction.  A tile is kTile
+// consecutive items, swept by one CTA, eligible when it holds at least
+// `min_items` lights and heavies.
 //
 //   k_sum, k_count, k_qsum   W, the fixed-point scale, Q = sum of the q_i
 //                            (shared with PSA, wrs_build.cu).
-//   k_greedy                 per chunk: stage lights and heavies in list
-//                            order, form the 64-bit sweep keys of the chunk
-//                            from its exact prefix sums (floors at 2^15 units
-//                            as in the pack, prefixes starting at 0 in the
-//                            chunk), find how far the sweep reaches, close
-//                            those buckets (merge path, rows by item index),
-//                            and append the items left over, in index order,
-//                            to the warp's region of the rest arrays.  The
-//                            heavy current at the stop keeps its remaining
-//                            excess r = E'(y+1) - D'(x) (read from the two
-//                            keys it stopped at, within 2^-46 of a bucket),
-//                            carried as the weight (Q + r) / (N 2^S) in FP32.
-//   k_rest_scan, k_rest_copy the leftover counts of the sub-segments, scanned;
-//                            the leftovers copied to one dense array.
+//   k_greedy_tile            one CTA per tile: load and classify the weights,
+//                            rank and stage them in list order, form the
+//                            64-bit sweep keys of the tile from its exact
+//                            prefix sums (floors at 2^15 units as in the
+//                            pack, prefixes starting at 0 in the tile), find
+//                            how far the sweep reaches, close those buckets
+//                            (merge path, rows by item index), and write the
+//                            items left over, in index order, to the tile's
+//                            region of the rest arrays.  The heavy current at
+//                            the stop keeps its remaining excess r = E'(y+1)
+//                            - D'(x) (read from the two keys it stopped at,
+//                            within 2^-46 of a bucket), carried as the weight
+//                            (Q + r) / (N 2^S) in FP32.
+//   k_rest_sum, k_rest_scan, k_rest_copy
+//                            the leftover counts summed per sub-segment (a
+//                            run of tiles), scanned, and the leftovers copied
+//                            to one dense array in tile order.
 //   PSA on the rest          the unchanged PSA pipeline on the dense weights.
 //   k_rest_remap             its rows moved to the original item indices.
 //
-// Every sum of q fits 64 bits (they all add up to Q < 2^63), so the chunk's
-// prefixes are u64 q sums; D'(x) = x Q - N sum_l(x) and E'(y) = N sum_h(y) -
-// y Q are 128-bit values, formed once per lane and then stepped by one
-// item's deficit (64 bits) or excess.
+// D'(x) = x Q - N sum_l(x) and E'(y) = N sum_h(y) - y Q are 128-bit values;
+// the tile's block scan gives each thread its starting value, which it then
+// steps by one item's deficit (64 bits) or excess (96 bits).
 #include "wrs_device.cuh"
 
 namespace wrs {
@@ -47,16 +49,16 @@ cudaError_t launch_info(unsigned char *, const Layout &, wrs_build_info *, cudaS
 uint32_t num_segments(uint64_t n);
 int num_sms();
 
-constexpr int kGreedyThreads = 128;   // four warps, one sub-segment each
-constexpr int kKeySlots = kChunk + 2 + (kChunk + 2) / 16 + 2;
+// Greedy tiles: one CTA of kTileThreads threads sweeps a tile of kTile
+// consecutive items, kTilePer list positions per thread (the pack's layout:
+// keys and entries in padded shared memory).
+constexpr int kTile = 1024;
+constexpr int kTilePer = 8;
+constexpr int kTileThreads = kTile / kTilePer;   // 128: four warps
+constexpr int kTileWarps = kTileThreads / 32;
+constexpr uint32_t kTileSlots = kTile + 2 + (kTile + 2) / 16 + 2;
 
-struct GreedyStage {
-    float wv[kChunk + kChunk / 32];   // staged weights (input order, padded)
-    Entry e[kChunk + kChunk / 16];    // entries in list order (padded)
-    int64_t key[kKeySlots];           // A(x) at x, B(y) at tl + 1 + y (padded)
-};
-
-__device__ __forceinline__ uint32_t pk16g(uint32_t e) { return e + (e >> 4); }
+__device__ __forceinline__ uint32_t pk16t(uint32_t e) { return e + (e >> 4); }
 
 // a * b as 128 bits from two 32x32 -> 64 products.
 __device__ __forceinline__ u128 mul32x64(uint32_t a, uint64_t b) {
@@ -65,153 +67,184 @@ __device__ __forceinline__ u128 mul32x64(uint32_t a, uint64_t b) {
     return ((u128)hi << 32) + lo;
 }
 
-template <bool kAligned>
-__global__ void __launch_bounds__(kGreedyThreads, 4)
-k_greedy(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__ P,
-         uint2 *__restrict__ rows, uint32_t *__restrict__ rest_idx, float *__restrict__ rest_w,
-         uint32_t *__restrict__ seg_rest, uint64_t C, uint32_t NS, uint32_t min_items) {
-    __shared__ GreedyStage stage[kGreedyThreads / 32];
+// Block-wide exclusive scan of one 32-bit value per thread (kTileThreads
+// threads); returns the thread's prefix, *total the sum.  Contains barriers.
+__device__ __forceinline__ uint32_t tile_scan_u32(uint32_t v, uint32_t *tot_smem, uint32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) tot_smem[warp] = inc;
+    __syncthreads();
+    uint32_t pre = inc - v, all = 0;
+#pragma unroll
+    for (int k = 0; k < kTileWarps; ++k) {
+        const uint32_t c = tot_smem[k];
+        pre += k < warp ? c : 0u;
+        all += c;
+    }
+    __syncthreads();
+    *total = all;
+    return pre;
+}
+
+// The greedy pass of PSA+ (Sec. 4 "PSA+"): persistent CTAs, CTA s owning
+// the tiles of sub-segment s.  Per tile:
+//   - load the weights (thread t: items 8t .. 8t+7), classify light/heavy,
+//     rank them with a block scan and stage the entries in list order
+//     (lights in index order, then heavies in index order);
+//   - if the tile holds at least min_items lights and heavies: the clamped
+//     fixed point q of every position, an exact block scan of the scaled
+//     deficits/excesses, the sweep keys with prefixes starting at 0 in the
+//     tile (as the pack forms them for a section), how far the sweep
+//     reaches, and the rows of the buckets it closes (merge path);
+//   - the items it did not finish, in index order, to this sub-segment's
+//     region of the rest arrays; the heavy current at the stop carries its
+//     remaining excess as the weight (Q + r) / (N 2^S) in FP32.
+__global__ void __launch_bounds__(kTileThreads, 10)
+k_greedy_tile(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__ P,
+              uint2 *__restrict__ rows, uint32_t *__restrict__ rest_idx,
+              float *__restrict__ rest_w, uint32_t *__restrict__ tile_rest, uint32_t min_items,
+              int aligned) {
+    __shared__ int64_t sK[kTileSlots];
+    __shared__ uint2 sE[kTileSlots];
+    __shared__ u128 s_w[kTileWarps];
+    __shared__ uint64_t s_q[2 * kTileWarps];
+    __shared__ uint32_t s_c[kTileWarps];
+    __shared__ __int128 s_rex;   // the remaining scaled excess of the carried heavy
     if (P->status) return;
-    const int lane = threadIdx.x & 31;
-    const uint32_t s = blockIdx.x * (kGreedyThreads / 32) + (threadIdx.x >> 5);
-    if (s >= NS) return;
-    GreedyStage &sm = stage[threadIdx.x >> 5];
+    const uint32_t tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const uint64_t Q = P->Q, Qn = P->Qn;
     const uint32_t N = (uint32_t)n;
+    const QScale qsc = qscale(P->qshift);
     const float lmax = P->light_max, inv_avg = P->inv_avg;
     const float invQk = P->invQ * (float)(1u << kKeyShift);
-    const double wscale = ldexp(1.0, -P->scale) / (double)n;   // q units to weight, per N
-    uint64_t a, b;
-    sub_range(s, NS, C, n, a, b);
-    uint64_t out = a;                   // next free slot of this sub-segment's rest region
-    const int e0 = lane * kPartItems;   // this lane's first item of the chunk
-    const int s0 = lane * kPartItems;   // this lane's first list slot
-    float4 pv[4];
-    auto load_chunk = [&](uint64_t base) {
-        const uint64_t lim = n - base;
+    const uint32_t b0 = tid * kTilePer;
+    auto Av = [&](uint32_t x) { return sK[pk16t(x)]; };
+    const uint64_t tile = blockIdx.x;
+    const uint64_t out = tile * kTile;   // this tile's region of the rest arrays
+    {
+        const uint64_t base = tile * kTile;
+        const uint32_t tv = (uint32_t)min((uint64_t)kTile, n - base);   // valid items
+        const uint32_t vt = tv > b0 ? min(tv - b0, (uint32_t)kTilePer) : 0u;
+        // ---- load and classify this thread's items (index order)
+        float wv[kTilePer];
+        if (aligned && vt == (uint32_t)kTilePer) {
+            const float4 a = __ldcs(reinterpret_cast<const float4 *>(w + base + b0));
+            const float4 c = __ldcs(reinterpret_cast<const float4 *>(w + base + b0 + 4));
+            wv[0] = a.x; wv[1] = a.y; wv[2] = a.z; wv[3] = a.w;
+            wv[4] = c.x; wv[5] = c.y; wv[6] = c.z; wv[7] = c.w;
+        } else {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            int e = r * 128 + lane * 4;
-            if (kAligned && (uint64_t)e + 3 < lim) {
-                pv[r] = __ldcs(reinterpret_cast<const float4 *>(w + base + e));
-            } else {
-                pv[r].x = (uint64_t)e + 0 < lim ? w[base + e + 0] : 0.f;
-                pv[r].y = (uint64_t)e + 1 < lim ? w[base + e + 1] : 0.f;
-                pv[r].z = (uint64_t)e + 2 < lim ? w[base + e + 2] : 0.f;
-                pv[r].w = (uint64_t)e + 3 < lim ? w[base + e + 3] : 0.f;
-            }
+            for (int k = 0; k < kTilePer; ++k) wv[k] = (uint32_t)k < vt ? w[base + b0 + k] : 0.f;
         }
-    };
-    if (a < b) load_chunk(a);
-    for (uint64_t base = a; base < b; base += kChunk) {
-        const uint64_t lim = b - base;
-        __syncwarp();
+        uint32_t lmask = 0;
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            int e = r * 128 + lane * 4;
-            sm.wv[pad32(e + 0)] = pv[r].x;
-            sm.wv[pad32(e + 1)] = pv[r].y;
-            sm.wv[pad32(e + 2)] = pv[r].z;
-            sm.wv[pad32(e + 3)] = pv[r].w;
-        }
-        if (base + kChunk < b) load_chunk(base + kChunk);
-        __syncwarp();
-        // ---- classify (input order), count, stage in list order
-        uint32_t lmask = 0, vmask = 0;
-#pragma unroll
-        for (int k = 0; k < kPartItems; ++k) {
-            const float x = sm.wv[pad32(e0 + k)];
-            const bool valid = (uint64_t)(e0 + k) < lim;
-            vmask |= (uint32_t)valid << k;
-            lmask |= (uint32_t)(valid && x <= lmax) << k;
-        }
-        const uint32_t cnt = __popc(lmask);
-        uint32_t icnt = cnt;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t c2 = __shfl_up_sync(0xffffffffu, icnt, d);
-            if (lane >= d) icnt += c2;
-        }
-        const uint32_t tl = __shfl_sync(0xffffffffu, icnt, 31);
-        const uint32_t tv = lim < (uint64_t)kChunk ? (uint32_t)lim : (uint32_t)kChunk;
+        for (int k = 0; k < kTilePer; ++k)
+            lmask |= (uint32_t)((uint32_t)k < vt && wv[k] <= lmax) << k;
+        uint32_t tl;
+        const uint32_t lrank0 = tile_scan_u32(__popc(lmask), s_c, &tl);
+        const uint32_t hrank0 = min(b0, tv) - lrank0;
         const uint32_t tnh = tv - tl;
-        const uint32_t lrank0 = icnt - cnt;                 // lights before this lane's items
-        const uint32_t hrank0 = (uint32_t)e0 - lrank0;      // heavies before them
+        // ---- stage entries in list order: light r at slot r, heavy r at tl + r
         {
-            uint32_t lrank = lrank0, hslot = kChunk - 1 - hrank0;
+            uint32_t lr = lrank0, hr = tl + hrank0;
 #pragma unroll
-            for (int k = 0; k < kPartItems; ++k) {
-                const bool lt = (lmask >> k) & 1u;
-                const uint32_t slot = lt ? lrank : hslot;
-                if ((vmask >> k) & 1u)
-                    sm.e[pad16(slot)] = Entry{(uint32_t)(base + e0 + k), sm.wv[pad32(e0 + k)]};
-                lrank += lt;
-                hslot -= !lt;
+            for (int k = 0; k < kTilePer; ++k) {
+                if ((uint32_t)k < vt) {
+                    const bool lt = (lmask >> k) & 1u;
+                    sE[pk16t(lt ? lr : hr)] = make_uint2((uint32_t)(base + b0 + k),
+                                                         __float_as_uint(wv[k]));
+                    lr += lt;
+                    hr += !lt;
+                }
             }
         }
-        __syncwarp();
         const bool elig = tl >= min_items && tnh >= min_items && tl > 0 && tnh > 0;
         uint32_t xk = 0, yk = 0;
-        float wres = 0.f;   // the carried weight of heavy yk (when elig)
+        __syncthreads();   // entries staged
         if (elig) {
-            const uint32_t hstart = kChunk - tnh;
-            const int qshift = P->qshift;
-            // q of this lane's slots (integer form: the conversion to 64 bits
-            // would occupy the FP64 pipe), clamped by class; lane sums
-            uint64_t qv[kPartItems];
-            uint64_t accL = 0, accH = 0;
+            // ---- values of positions b0 .. b0+7 (list order)
+            const uint32_t nlt = tl > b0 ? min(tl - b0, (uint32_t)kTilePer) : 0u;
+            const uint32_t nvt = tv > b0 ? min(tv - b0, (uint32_t)kTilePer) : 0u;
+            uint64_t qv[kTilePer];
+            uint64_t sql = 0, sqh = 0;
 #pragma unroll
-            for (int k = 0; k < kPartItems; ++k) {
-                const uint32_t slot = (uint32_t)(s0 + k);
-                const uint64_t q = fixed_q_bits(sm.e[pad16(slot)].w, qshift);
-                qv[k] = 0;
-                if (slot < tl) { qv[k] = q > Qn ? Qn : q; accL += qv[k]; }
-                else if (slot >= hstart) { qv[k] = q <= Qn ? Qn + 1 : q; accH += qv[k]; }
+            for (int k = 0; k < kTilePer; ++k) {
+                uint64_t q = fixed_q(__uint_as_float(sE[pk16t(b0 + k)].y), qsc);
+                if ((uint32_t)k < nlt) {
+                    q = q > Qn ? Qn : q;
+                    sql += q;
+                } else {
+                    q = q <= Qn ? Qn + 1 : q;
+                    sqh += (uint32_t)k < nvt ? q : 0ull;
+                }
+                qv[k] = q;
             }
-            uint64_t incL = accL, incH = accH;
+            u128 run;
+            {
+                const bool neg = sqh < sql;
+                const uint64_t mag = neg ? sql - sqh : sqh - sql;
+                const u128 v = mul32x64(N, mag);
+                const int c = 2 * (int)nlt - (int)nvt;   // lights - heavies of the thread
+                const u128 cq = mul32x64((uint32_t)(c < 0 ? -c : c), Q);
+                run = (neg ? (u128)0 - v : v) + (c < 0 ? (u128)0 - cq : cq);
+            }
+            u128 inc = run;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                const uint64_t oL = __shfl_up_sync(0xffffffffu, incL, d);
-                const uint64_t oH = __shfl_up_sync(0xffffffffu, incH, d);
-                if (lane >= d) { incL += oL; incH += oH; }
+                const u128 o = shfl_up_u128(inc, d);
+                if (lane >= d) inc += o;
             }
-            const uint64_t exL = incL - accL, exH = incH - accH;
-            const uint64_t THq = __shfl_sync(0xffffffffu, incH, 31);
-            // keys: A(x) = floor(D'(x) / 2^15), D'(x) = x Q - N sum_l(x), at
-            // slot x; B(y) = floor(E'(y+1) / 2^15), E'(y+1) = N sum_h(y+1) -
-            // (y+1) Q, at slot tl + 1 + y.  Heavy y sits at list slot
-            // kChunk - 1 - y, so walking the slots upwards walks y down:
-            // each light adds its deficit Q - N q to D', each heavy takes its
-            // excess N q - Q off E'.  Only the lane's starting values need
-            // full products.
-            {
-                if (lane == 0) sm.key[pk16g(0)] = 0;
-                u128 D = mul32x64((uint32_t)s0, Q) - mul32x64(N, exL);   // D'(s0)
-                const uint32_t s1 = (uint32_t)s0 > hstart ? (uint32_t)s0 : hstart;
-                // E'(y+1) of the lane's first heavy slot s1 (y + 1 = kChunk - s1)
-                u128 E = mul32x64(N, THq - exH) - mul32x64(kChunk - s1, Q);
+            uint64_t wsl = sql;
 #pragma unroll
-                for (int k = 0; k < kPartItems; ++k) {
-                    const uint32_t slot = (uint32_t)(s0 + k);
-                    if (slot < tl) {
-                        D += Q - (uint64_t)N * qv[k];   // N q <= Q: 64 bits
-                        sm.key[pk16g(slot + 1)] = (int64_t)(D >> kKeyShift);
-                    } else if (slot >= hstart) {
-                        const u128 v = E >> kKeyShift;
-                        sm.key[pk16g(tl + 1 + (kChunk - 1 - slot))] =
-                            v < ((u128)1 << 62) ? (int64_t)v : ((int64_t)1 << 62);
-                        E -= mul32x64(N, qv[k]) - Q;
+            for (int d = 16; d > 0; d >>= 1) wsl += __shfl_xor_sync(0xffffffffu, wsl, d);
+            if (lane == 31) s_w[warp] = inc;
+            if (lane == 0) s_q[warp] = wsl;
+            __syncthreads();
+            // ---- keys: A(x) = floor(D'(x) / 2^15) at slot x, B(y) =
+            // floor(E'(y+1) / 2^15) at slot tl + 1 + y, prefixes from the
+            // tile's start; the light total D_L = tl Q - N (sum of light q)
+            // turns the running value into the heavy excess (ch = -D_L)
+            {
+                u128 p = inc - run;
+                uint64_t SL = 0;
+#pragma unroll
+                for (int k = 0; k < kTileWarps; ++k) {
+                    p += k < warp ? s_w[k] : (u128)0;
+                    SL += s_q[k];
+                }
+                const u128 ch = mul32x64(N, SL) - mul32x64(tl, Q);
+                if (tid == 0) {
+                    sK[pk16t(0)] = 0;
+                    sK[pk16t(tv + 1)] = INT64_MAX;   // after the last heavy
+                }
+                Limbs4 a = to_limbs(nlt > 0 ? p : ch + p);
+#pragma unroll
+                for (int k = 0; k < kTilePer; ++k) {
+                    const uint32_t e = b0 + k;
+                    if ((uint32_t)k < nlt) {
+                        add96(a, Q - mul_lo_nq(N, qv[k]));
+                        sK[pk16t(e + 1)] = key15(a);
+                        if ((uint32_t)k + 1 == nlt && nlt < nvt) a = to_limbs(ch + from_limbs(a));
+                    } else if ((uint32_t)k < nvt) {
+                        add_excess(a, N, qv[k], Q);
+                        sK[pk16t(e + 1)] = key15_capped(a);
                     }
                 }
             }
-            __syncwarp();
-            auto Av = [&](uint32_t x) { return sm.key[pk16g(x)]; };
-            auto Bv = [&](uint32_t y) { return sm.key[pk16g(tl + 1 + y)]; };
-            // how far the sweep reaches.  With every light filled (x = tl)
-            // the sweep still closes the heavies that have fallen to the
-            // average, B(y) <= A(tl), and stops at the first that has not;
-            // heavy tnh-1 cannot close (no next heavy in the chunk), and the
-            // lights with A < B(tnh-1) close before it
+            __syncthreads();
+            auto Bv = [&](uint32_t y) { return sK[pk16t(tl + 1 + y)]; };
+            // ---- how far the sweep reaches (every warp finds the same).
+            // With every light filled (x = tl) the sweep still closes the
+            // heavies that have fallen to the average, B(y) <= A(tl), and
+            // stops at the first that has not; heavy tnh-1 cannot close (no
+            // next heavy in the tile), and the lights with A < B(tnh-1) close
+            // before it
             auto count_below = [&](uint32_t len, auto below) {
                 uint32_t lo = 0, hi = len;   // the count lies in [lo, hi]
                 while (lo < hi) {
@@ -234,10 +267,8 @@ k_greedy(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict_
             uint32_t Kc;
             if (KL <= KH) { Kc = KL; xk = tl; yk = cntB; }
             else { Kc = KH; xk = cntA; yk = tnh - 1; }
-            // close the first Kc buckets: lane takes positions [s0, s0 + 16)
-            // (A(tl), the chunk's whole deficit, orders the heavies that
-            // close after the last light)
-            const uint32_t d0 = (uint32_t)s0;
+            // ---- close the first Kc buckets: thread takes positions [b0, b0 + 8)
+            const uint32_t d0 = b0;
             if (d0 < Kc) {
                 uint32_t lo = d0 > tnh ? d0 - tnh : 0, hi = d0 < tl ? d0 : tl;
                 while (lo < hi) {
@@ -247,96 +278,113 @@ k_greedy(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict_
                 }
                 uint32_t x = lo, y = d0 - lo;
                 int64_t av = Av(x), bv = Bv(y);
-                // hcur: item of heavy y, the one that fills the next light
-                uint32_t hcur = sm.e[pad16(kChunk - 1 - y)].item;
+                uint32_t hcur = sE[pk16t(tl + y)].x;   // heavy y fills the next light
 #pragma unroll
-                for (int k = 0; k < kPartItems; ++k) {
+                for (int k = 0; k < kTilePer; ++k) {
                     if (d0 + k < Kc) {
                         // inside the reach a closing heavy has a next heavy
-                        // and a filled light exists (x < tl)
+                        // and a light to fill exists
                         const bool heavy = bv <= av;
-                        // one entry load per step: the closed light, or the
-                        // heavy after the closed one
-                        const Entry ld = sm.e[pad16(heavy ? kChunk - 2 - y : x)];
-                        const uint32_t item = heavy ? hcur : ld.item;
-                        const uint32_t alias = heavy ? ld.item : hcur;
+                        const uint2 ld = sE[pk16t(heavy ? tl + y + 1 : x)];
+                        const uint32_t item = heavy ? hcur : ld.x;
+                        const uint32_t alias = heavy ? ld.x : hcur;
                         const float prob =
                             heavy ? fminf(fmaxf(1.0f - __ll2float_rn(av - bv) * invQk, 0.0f), 1.0f)
-                                  : fminf(ld.w * inv_avg, 1.0f);
+                                  : fminf(__uint_as_float(ld.y) * inv_avg, 1.0f);
                         rows[item] = make_uint2(__float_as_uint(prob), alias);
-                        const int64_t v = sm.key[pk16g(heavy ? tl + 2 + y : x + 1)];
-                        if (heavy) { ++y; bv = v; hcur = ld.item; }
+                        const int64_t v = sK[pk16t(heavy ? tl + y + 2 : x + 1)];
+                        if (heavy) { ++y; bv = v; hcur = ld.x; }
                         else { ++x; av = v; }
                     }
                 }
             }
-            // the remaining excess of heavy yk, r = E'(yk+1) - D'(xk), from
-            // the two keys the sweep stopped at: within 2^15 units of the
-            // exact value (2^-46 of a bucket), far below the FP32 rounding
-            // of the carried weight.  A key at the cap (E' >= 2^77) takes
-            // the exact sums instead.
+            // ---- the remaining excess of heavy yk, r = E'(yk+1) - D'(xk),
+            // from the two keys the sweep stopped at (within 2^15 units, 2^-46
+            // of a bucket); a key at the cap (E' >= 2^77) takes exact sums
             const int64_t bk = Bv(yk), ak = Av(xk);
-            double qrem;   // N q' of the remaining weight
             if (bk < ((int64_t)1 << 62)) {
-                qrem = (double)Q + (double)(bk - ak) * (double)(1u << kKeyShift);
+                if (tid == 0) s_rex = (__int128)(bk - ak) << kKeyShift;
             } else {
                 uint64_t pl = 0, ph = 0;
 #pragma unroll
-                for (int k = 0; k < kPartItems; ++k) {
-                    const uint32_t slot = (uint32_t)(s0 + k);
-                    const uint64_t q = fixed_q_bits(sm.e[pad16(slot)].w, qshift);
-                    if (slot < xk) pl += q > Qn ? Qn : q;   // lights below xk
-                    if (slot >= hstart && slot < kChunk - 1 - yk) ph += q <= Qn ? Qn + 1 : q;
+                for (int k = 0; k < kTilePer; ++k) {
+                    const uint32_t e = b0 + k;
+                    const uint64_t q = fixed_q(__uint_as_float(sE[pk16t(e)].y), qsc);
+                    if (e < xk) pl += q > Qn ? Qn : q;                    // lights below xk
+                    if (e >= tl && e <= tl + yk && e < tv) ph += q <= Qn ? Qn + 1 : q;   // heavies up to yk
                 }
 #pragma unroll
                 for (int d = 16; d > 0; d >>= 1) {
                     pl += __shfl_xor_sync(0xffffffffu, pl, d);
                     ph += __shfl_xor_sync(0xffffffffu, ph, d);
                 }
-                const __int128 Dx = (__int128)(mul32x64(xk, Q) - mul32x64(N, pl));
-                const __int128 Ey = (__int128)mul32x64(N, THq - ph) - (__int128)mul32x64(yk + 1, Q);
-                qrem = (double)Q + (double)(Ey - Dx);
+                __syncthreads();   // every thread has read s_q above
+                if (lane == 0) { s_q[warp] = pl; s_q[kTileWarps + warp] = ph; }
+                __syncthreads();
+                uint64_t PL = 0, PH = 0;
+#pragma unroll
+                for (int k = 0; k < kTileWarps; ++k) { PL += s_q[k]; PH += s_q[kTileWarps + k]; }
+                const __int128 Dx = (__int128)(mul32x64(xk, Q) - mul32x64(N, PL));
+                const __int128 Ey = (__int128)mul32x64(N, PH) - (__int128)mul32x64(yk + 1, Q);
+                if (tid == 0) s_rex = Ey - Dx;
             }
-            wres = (float)(qrem > 0.0 ? qrem * wscale : 0.0);
         }
         // ---- the items left over, in index order, to this sub-segment's region
         uint32_t left = 0;
         {
             uint32_t lr = lrank0, hr = hrank0;
 #pragma unroll
-            for (int k = 0; k < kPartItems; ++k) {
-                const bool valid = (vmask >> k) & 1u, lt = (lmask >> k) & 1u;
+            for (int k = 0; k < kTilePer; ++k) {
+                const bool valid = (uint32_t)k < vt, lt = (lmask >> k) & 1u;
                 const bool keep = valid && (!elig || (lt ? lr >= xk : hr >= yk));
                 left |= (uint32_t)keep << k;
                 lr += valid && lt;
                 hr += valid && !lt;
             }
         }
-        const uint32_t nleft = __popc(left);
-        uint32_t ileft = nleft;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t c2 = __shfl_up_sync(0xffffffffu, ileft, d);
-            if (lane >= d) ileft += c2;
-        }
+        uint32_t nleft;
+        const uint32_t lpre = tile_scan_u32(__popc(left), s_c, &nleft);
         {
-            uint64_t pos = out + (ileft - nleft);
-            uint32_t hr = hrank0;
+            uint64_t pos = out + lpre;
+            uint32_t lr = lrank0, hr = hrank0;
 #pragma unroll
-            for (int k = 0; k < kPartItems; ++k) {
-                const bool lt = (lmask >> k) & 1u, valid = (vmask >> k) & 1u;
+            for (int k = 0; k < kTilePer; ++k) {
+                const bool lt = (lmask >> k) & 1u, valid = (uint32_t)k < vt;
                 if ((left >> k) & 1u) {
-                    const float x = sm.wv[pad32(e0 + k)];
-                    rest_idx[pos] = (uint32_t)(base + e0 + k);
-                    rest_w[pos] = (elig && !lt && hr == yk) ? wres : x;
+                    rest_idx[pos] = (uint32_t)(base + b0 + k);
+                    float wl;
+                    if (elig && !lt && hr == yk) {
+                        // the carried weight (Q + r) / (N 2^S)
+                        const double qrem = (double)Q + (double)s_rex;   // set before the scan
+                        wl = (float)(qrem > 0.0 ? ldexp(qrem, -P->scale) / (double)n : 0.0);
+                    } else {
+                        wl = __uint_as_float(sE[pk16t(lt ? lr : tl + hr)].y);
+                    }
+                    rest_w[pos] = wl;
                     ++pos;
                 }
+                lr += valid && lt;
                 hr += valid && !lt;
             }
         }
-        out += __shfl_sync(0xffffffffu, ileft, 31);
+        if (tid == 0) tile_rest[tile] = nleft;
     }
-    if (lane == 0) seg_rest[s] = (uint32_t)(out - a);
+}
+
+// The leftover count of every sub-segment: its tiles' counts summed (one
+// warp per sub-segment; sub-segment s holds tiles [s NT / NS, (s+1) NT / NS)).
+__global__ void __launch_bounds__(256)
+k_rest_sum(const BuildParams *__restrict__ P, const uint32_t *__restrict__ tile_rest,
+           uint32_t *__restrict__ seg_rest, uint64_t NT, uint32_t NS) {
+    if (P->status) return;
+    const uint32_t s = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (s >= NS) return;
+    const int lane = threadIdx.x & 31;
+    const uint64_t a = (uint64_t)s * NT / NS, b = (uint64_t)(s + 1) * NT / NS;
+    uint32_t c = 0;
+    for (uint64_t t = a + lane; t < b; t += 32) c += tile_rest[t];
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) seg_rest[s] = c;
 }
 
 // One CTA (1024 threads): exclusive scan of the leftover counts of the
@@ -379,23 +427,28 @@ k_rest_scan(const BuildParams *__restrict__ P, const uint32_t *__restrict__ seg_
     if (threadIdx.x == 0) *n_rest = all;
 }
 
-// One warp per sub-segment: its leftovers to their place in the dense arrays.
+// One warp per sub-segment: the leftovers of its tiles, in order, to their
+// place in the dense arrays (tile t's leftovers start at item t * kTile of
+// the rest arrays).
 __global__ void __launch_bounds__(256)
 k_rest_copy(const BuildParams *__restrict__ P, const uint32_t *__restrict__ rest_idx,
-            const float *__restrict__ rest_w, const uint32_t *__restrict__ seg_rest,
+            const float *__restrict__ rest_w, const uint32_t *__restrict__ tile_rest,
             const uint64_t *__restrict__ rest_off, uint32_t *__restrict__ dense_idx,
-            float *__restrict__ dense_w, uint64_t C, uint32_t NS, uint64_t n) {
+            float *__restrict__ dense_w, uint64_t NT, uint32_t NS) {
     if (P->status) return;   // the greedy pass wrote no counts
     const uint32_t s = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (s >= NS) return;
     const int lane = threadIdx.x & 31;
-    uint64_t a, b;
-    sub_range(s, NS, C, n, a, b);
-    const uint32_t cnt = seg_rest[s];
-    const uint64_t o = rest_off[s];
-    for (uint32_t k = lane; k < cnt; k += 32) {
-        dense_idx[o + k] = rest_idx[a + k];
-        dense_w[o + k] = rest_w[a + k];
+    const uint64_t a = (uint64_t)s * NT / NS, b = (uint64_t)(s + 1) * NT / NS;
+    uint64_t o = rest_off[s];
+    for (uint64_t t = a; t < b; ++t) {
+        const uint32_t cnt = tile_rest[t];
+        const uint64_t src = t * kTile;
+        for (uint32_t k = lane; k < cnt; k += 32) {
+            dense_idx[o + k] = rest_idx[src + k];
+            dense_w[o + k] = rest_w[src + k];
+        }
+        o += cnt;
     }
 }
 
@@ -437,12 +490,12 @@ __global__ void k_plus_info(const BuildParams *__restrict__ P, const uint64_t *_
     *out = r;
 }
 
-// Workspace: [whole-table layout][rest_idx 4n][rest_w 4n][seg_rest][rest_off]
+// Workspace: [whole-table layout][rest_idx 4n][rest_w 4n][tile_rest][seg_rest][rest_off]
 // [n_rest][dense_idx 4n][dense_w 4n][rest layout][rest rows 8n][rest info].
 struct PlusLayout {
     Layout L;
-    uint64_t rest_idx, rest_w, seg_rest, rest_off, n_rest, dense_idx, dense_w, rest_ws,
-        rest_rows, rest_info, total;
+    uint64_t rest_idx, rest_w, tile_rest, seg_rest, rest_off, n_rest, dense_idx, dense_w,
+        rest_ws, rest_rows, rest_info, total;
 };
 
 PlusLayout make_plus_layout(uint64_t n, uint32_t S) {
@@ -456,6 +509,7 @@ PlusLayout make_plus_layout(uint64_t n, uint32_t S) {
     };
     p.rest_idx = take(4 * n);
     p.rest_w = take(4 * n);
+    p.tile_rest = take(4 * ((n + kTile - 1) / kTile));
     p.seg_rest = take(4ull * kMaxSegs);
     p.rest_off = take(8ull * (kMaxSegs + 1));
     p.n_rest = take(8);
@@ -477,15 +531,17 @@ cudaError_t launch_build_plus(const float *d_w, uint64_t n, wrs_row *d_rows, uns
     cudaError_t e = launch_total(d_w, n, ws, L, st);
     if (!e) e = launch_count(d_w, n, ws, L, st);
     if (e) return e;
-    const uint64_t C = (n + kChunk - 1) / kChunk;
     const uint32_t NSc = num_segments(n);   // the count pass's sub-segments
-    // the greedy pass: one wave of four-warp CTAs (four per SM)
-    uint64_t g = (uint64_t)num_sms() * 4 * (kGreedyThreads / 32);
+    // the greedy pass: one CTA per tile; the leftover counts are summed per
+    // sub-segment, scanned, and the leftovers compacted in tile order
+    const uint64_t NT = (n + kTile - 1) / kTile;
+    uint64_t g = (uint64_t)num_sms() * 8;
     if (g > (uint64_t)kMaxSegs - 1) g = kMaxSegs - 1;
-    if (g > C) g = C;
+    if (g > NT) g = NT;
     const uint32_t NS = (uint32_t)(g ? g : 1);
     auto *rest_idx = reinterpret_cast<uint32_t *>(ws + pl.rest_idx);
     auto *rest_w = reinterpret_cast<float *>(ws + pl.rest_w);
+    auto *tile_rest = reinterpret_cast<uint32_t *>(ws + pl.tile_rest);
     auto *seg_rest = reinterpret_cast<uint32_t *>(ws + pl.seg_rest);
     auto *rest_off = reinterpret_cast<uint64_t *>(ws + pl.rest_off);
     auto *n_rest = reinterpret_cast<uint64_t *>(ws + pl.n_rest);
@@ -493,19 +549,15 @@ cudaError_t launch_build_plus(const float *d_w, uint64_t n, wrs_row *d_rows, uns
     auto *dense_w = reinterpret_cast<float *>(ws + pl.dense_w);
     auto *rest_rows = reinterpret_cast<wrs_row *>(ws + pl.rest_rows);
     auto *rest_info = reinterpret_cast<wrs_build_info *>(ws + pl.rest_info);
-    const unsigned gblocks = (NS + kGreedyThreads / 32 - 1) / (kGreedyThreads / 32);
     const int aligned = ((uintptr_t)d_w % 16) == 0;
-    if (aligned)
-        k_greedy<true><<<gblocks, kGreedyThreads, 0, st>>>(
-            d_w, n, P, reinterpret_cast<uint2 *>(d_rows), rest_idx, rest_w, seg_rest, C, NS,
-            min_items);
-    else
-        k_greedy<false><<<gblocks, kGreedyThreads, 0, st>>>(
-            d_w, n, P, reinterpret_cast<uint2 *>(d_rows), rest_idx, rest_w, seg_rest, C, NS,
-            min_items);
+    k_greedy_tile<<<(unsigned)NT, kTileThreads, 0, st>>>(d_w, n, P,
+                                                           reinterpret_cast<uint2 *>(d_rows),
+                                                           rest_idx, rest_w, tile_rest, min_items,
+                                                           aligned);
+    k_rest_sum<<<(NS + 7) / 8, 256, 0, st>>>(P, tile_rest, seg_rest, NT, NS);
     k_rest_scan<<<1, 1024, 0, st>>>(P, seg_rest, rest_off, n_rest, NS);
-    k_rest_copy<<<(NS + 7) / 8, 256, 0, st>>>(P, rest_idx, rest_w, seg_rest, rest_off, dense_idx,
-                                              dense_w, C, NS, n);
+    k_rest_copy<<<(NS + 7) / 8, 256, 0, st>>>(P, rest_idx, rest_w, tile_rest, rest_off, dense_idx,
+                                              dense_w, NT, NS);
     e = cudaGetLastError();
     if (e) return e;
     // the rest's size decides its launches: one read back

@@ -99,3 +99,64 @@ def gpu_sample(rows_t, n, first, count, seed, stream_lo=0, stream_hi=0, offset=0
     wrs.sample_rows(rows_t, n, first, count, seed, out, stream_lo, stream_hi)
     torch.cuda.synchronize()
     return out.cpu().numpy().view(np.uint32)
+
+
+def fixed_q_exact(w, S):
+    """q_i = floor(w_i 2^S + 1/2) for FP32 weights, exact: w 2^S is exact in
+    FP64 (a 24-bit significand scaled by a power of two), the half is added
+    exactly below 2^52, and from 2^52 on w 2^S is already an integer."""
+    x = np.ldexp(np.asarray(w, np.float32).astype(np.float64), S)
+    return np.where(x < 2.0**52, np.floor(x + 0.5), x).astype(np.uint64)
+
+
+def alias_differences_at_ties(w, info, alias, orc_alias):
+    """Rows whose alias differs from the oracle's PSA table, each checked to
+    sit at a near-tie of the sweep's decision (Sec. 2.2: heavy h[y] closes
+    before light l[x] iff its remaining weight fits in one bucket, i.e. the
+    excess prefix E'(y+1) does not exceed the deficit prefix D'(x)).
+
+    For a light row l[x] the two tables name different heavies only if some
+    heavy y between them has E'(y+1) - D'(x) within the oracle's own FP64
+    rounding of the two prefix sums (x + y + 2 terms, bounded by
+    gamma_k * sum with gamma_k = k 2^-53 / (1 - k 2^-53)) plus the GPU's key
+    resolution (2^-46 of a bucket).  The gaps are exact: D' and E' are formed
+    from the fixed point q = round(w 2^S) with the build's S and Q.  Returns
+    (number of differing rows, list of rows that are NOT near-ties)."""
+    w = np.asarray(w, np.float32)
+    n = w.size
+    diff = np.flatnonzero(np.asarray(alias) != np.asarray(orc_alias))
+    if diff.size == 0:
+        return 0, []
+    import oracle
+    W = oracle.exact_sum(w)
+    l, h = oracle.classify(w, W / n)
+    S, Q = info["scale"], info["Q"]
+    Qn = Q // n
+    q = fixed_q_exact(w, S)
+    ql = np.minimum(q[l], np.uint64(Qn))
+    qh = np.maximum(q[h], np.uint64(Qn + 1))
+    sl = np.concatenate([[0], np.cumsum(ql, dtype=np.uint64)])
+    sh = np.concatenate([[0], np.cumsum(qh, dtype=np.uint64)])
+    light = np.zeros(n, bool)
+    light[l] = True
+    eps = 2.0**-53
+    bad = []
+    for i in diff:
+        if not light[i]:
+            bad.append(int(i))   # a heavy closes with the next heavy in both tables
+            continue
+        x = int(np.searchsorted(l, i))
+        ya = int(np.searchsorted(h, alias[i]))
+        yb = int(np.searchsorted(h, orc_alias[i]))
+        D = x * Q - n * int(sl[x])
+        tie = False
+        for y in range(min(ya, yb), max(ya, yb)):
+            E = n * int(sh[y + 1]) - (y + 1) * Q
+            k = x + y + 2
+            gamma = k * eps / (1.0 - k * eps)
+            # the two FP64 prefix sums in buckets: N sigma / Q
+            bound = gamma * n * (float(sl[x]) + float(sh[y + 1])) / Q + 2.0**-46
+            tie = tie or abs(E - D) / Q <= bound
+        if not tie:
+            bad.append(int(i))
+    return int(diff.size), bad

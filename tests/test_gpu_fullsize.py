@@ -18,6 +18,7 @@ import torch
 
 import oracle
 import paper_2106_12270_gb300 as wrs
+from gpu_util import alias_differences_at_ties
 from paper_2106_12270_gb300 import inputs
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -72,7 +73,9 @@ def test_full_size_1e8_power_law_build_and_samples():
     prob, alias = wrs.rows_to_numpy(rows)
     t = oracle.psa(w_host, 1024)
     same = alias == t["alias"]
-    assert (~same).sum() <= n // 10000
+    # a row may differ only at a near-tie of the oracle's FP64 sweep
+    _, not_ties = alias_differences_at_ties(w_host, info, alias, t["alias"])
+    assert not not_ties, not_ties[:10]
     assert np.max(np.abs(prob[same] - t["prob"][same])) < 1e-6
     # sampled draws of the bench's 1e9-draw stream (seed 2)
     count = 1_000_000_000
@@ -96,7 +99,7 @@ def test_full_size_2pow30_exponential_build():
     assert (info["nl"], info["nh"]) == (nl, n - nl)
     assert device_mass_error(rows, w, W) <= 1e-5
     # PSA+ on the same weights: every item's mass, and the greedy share of
-    # 512-item chunks (the oracle's PSA+ at this size would need ~35 GB of
+    # 1024-item tiles (the oracle's PSA+ at this size would need ~35 GB of
     # host memory; its greedy count is compared at 4e6 items and below)
     del b
     torch.cuda.empty_cache()

@@ -1,12 +1,15 @@
 """PSA+ construction (Sec. 4 "PSA+") on the GPU against the CPU oracle.
 
-The greedy step packs each 512-item partition chunk that holds at least
-`min_items` lights and heavies; the rest goes through PSA.  The GPU table is
+The greedy step packs each tile of 1024 consecutive items that holds at
+least `min_items` lights and heavies; the rest goes through PSA.  The GPU table is
 not the oracle's row for row (the rest's PSA recomputes its own total in FP32
 weights, the oracle keeps the FP64 average), so parity is checked on:
 * the reconstructed masses: |mass_i - N w_i/W| <= 1e-5 max(1, N w_i/W);
-* the number of items the greedy step finished: the oracle's psa_plus with
-  tiles of 512, up to near-ties of its FP64 sweep;
+* the number of items the greedy step finished: equal to the oracle's
+  psa_plus with tiles of 1024 (the two sweeps decide at different
+  resolutions -- the oracle in FP64, the GPU on exact prefixes at 2^-46 of a
+  bucket -- so only an exact near-tie could separate them, and none occurs on
+  these seeded inputs);
 * rows bit-identical to the PSA build when no chunk is eligible;
 * status codes of the whole-table steps.
 """
@@ -23,9 +26,9 @@ from paper_2106_12270_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 MASS_TOL = 1e-5
-TILE = 512
+TILE = 1024
 KINDS = ["uniform", "zipf", "exponential", "gamma"]
-SIZES = [1, 2, 3, 511, 512, 513, 4097, 100003]
+SIZES = [1, 2, 3, 1023, 1024, 1025, 4097, 100003]
 
 
 def build_plus(w_np, min_items=1, cfg=None, offset=0):
@@ -52,11 +55,6 @@ def mass_err(w, prob, alias):
     return float((np.abs(m - e) / np.maximum(1.0, e)).max())
 
 
-def greedy_tol(n):
-    # a near-tie of the FP64 sweep can move one chunk's stop by a few items
-    return max(8, n // 2000)
-
-
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("n", SIZES)
 def test_plus_masses_and_greedy_count(kind, n):
@@ -71,7 +69,7 @@ def test_plus_masses_and_greedy_count(kind, n):
     assert np.all(alias < n)
     assert mass_err(w, prob, alias) <= MASS_TOL
     _, _, g_orc = oracle.psa_plus(w, cfg.section_size, TILE, 1)
-    assert abs(greedy - g_orc) <= greedy_tol(n), (greedy, g_orc)
+    assert greedy == g_orc, (greedy, g_orc)
     if n >= 4 * TILE:
         assert greedy > n // 2   # most of the table is packed greedily
 
@@ -84,7 +82,7 @@ def test_plus_min_items(m):
     assert inf["status"] == wrs.OK
     assert mass_err(w, prob, alias) <= MASS_TOL
     _, _, g_orc = oracle.psa_plus(w, wrs.config().section_size, TILE, m)
-    assert abs(greedy - g_orc) <= greedy_tol(n), (greedy, g_orc)
+    assert greedy == g_orc, (greedy, g_orc)
 
 
 @pytest.mark.parametrize("kind", KINDS)
@@ -163,7 +161,7 @@ def test_plus_large():
     assert inf["status"] == wrs.OK
     assert mass_err(w, prob, alias) <= MASS_TOL
     _, _, g_orc = oracle.psa_plus(w, wrs.config().section_size, TILE, 1)
-    assert abs(greedy - g_orc) <= greedy_tol(n), (greedy, g_orc)
+    assert greedy == g_orc, (greedy, g_orc)
 
 
 @pytest.mark.parametrize("kind,pos", [("uniform", 777), ("exponential", 1000)])
@@ -178,7 +176,7 @@ def test_plus_dominant_heavy(kind, pos):
     assert inf["status"] == wrs.OK
     assert mass_err(w, prob, alias) <= MASS_TOL
     _, _, g_orc = oracle.psa_plus(w, wrs.config().section_size, TILE, 1)
-    assert abs(greedy - g_orc) <= greedy_tol(n), (greedy, g_orc)
+    assert greedy == g_orc, (greedy, g_orc)
 
 
 @pytest.mark.parametrize("section,method", [(256, 0), (8192, 0), (1024, 1)])
@@ -191,7 +189,7 @@ def test_plus_config(section, method):
     assert inf["status"] == wrs.OK
     assert mass_err(w, prob, alias) <= MASS_TOL
     _, _, g_orc = oracle.psa_plus(w, section, TILE, 1)
-    assert abs(greedy - g_orc) <= greedy_tol(n), (greedy, g_orc)
+    assert greedy == g_orc, (greedy, g_orc)
     # the greedy step does not depend on cfg: same greedy rows as the default
     p0, a0, _, g0 = build_plus(w, 1)
     assert g0 == greedy

@@ -470,3 +470,32 @@ def test_psa_plus_greedy_share_uniform():
     w = inputs.uniform(1_000_000, 1)
     _, _, greedy = oracle.psa_plus(w, 1024, 512, 1)
     assert greedy / w.size >= 0.85
+
+
+def test_near_tie_check_flags_a_planted_alias():
+    """The parity tests' near-tie check (gpu_util.alias_differences_at_ties)
+    accepts an identical table and flags a light row whose alias names a
+    heavy three places away from the sweep's choice (no tie there)."""
+    from fractions import Fraction
+
+    from gpu_util import alias_differences_at_ties, fixed_q_exact
+    w = inputs.exponential(5000, 3)
+    n = w.size
+    t = oracle.psa(w, 1024)
+    W = oracle.exact_sum(w)
+    Wx = sum((Fraction(float(x)) for x in w), Fraction(0))
+    S = 0
+    while Wx * Fraction(2) ** S >= 2**62:
+        S -= 1
+    while Wx * Fraction(2) ** S < 2**61:
+        S += 1
+    q = fixed_q_exact(w, S)
+    exact = [int((Fraction(float(x)) * Fraction(2) ** S + Fraction(1, 2)) // 1) for x in w]
+    assert list(map(int, q)) == exact
+    info = {"scale": S, "Q": sum(exact)}
+    assert alias_differences_at_ties(w, info, t["alias"], t["alias"]) == (0, [])
+    l, h = oracle.classify(w, W / n)
+    bad = t["alias"].copy()
+    y = int(np.searchsorted(h, bad[l[100]]))
+    bad[l[100]] = h[min(len(h) - 1, y + 3)]
+    assert alias_differences_at_ties(w, info, bad, t["alias"]) == (1, [int(l[100])])
