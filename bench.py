@@ -593,25 +593,27 @@ def run_sampling_extras(args, rows, n, count, out, world, naive_ms, hbm):
                            "what": "the same Philox-4x32-10 calls and 4-byte stores, "
                                    "no rows (wrs_diag_philox)"}
 
-    # random-gather probe on the timed table: one chunk's draws, every load path
+    # random-gather probe on the timed table: one chunk's draws, every load
+    # path and a few launch shapes (CTAs per SM x loads in flight per thread);
+    # the best is the random-sector rate this GPU sustains
     c0 = chunks[0][1]
     probe = {}
-    for flavor in (0, 1, 2):
-        wrs.diag_random_gather(rows, n, c0, 7, flavor, out[:c0])
+    for flavor, ctas, loads in ((0, 8, 8), (1, 8, 8), (2, 8, 8), (0, 16, 8), (0, 32, 16)):
+        wrs.diag_random_gather(rows, n, c0, 7, flavor, out[:c0], ctas, loads)
         torch.cuda.synchronize()
         a, b = _events(2)
         a.record(stream)
-        wrs.diag_random_gather(rows, n, c0, 7, flavor, out[:c0])
+        wrs.diag_random_gather(rows, n, c0, 7, flavor, out[:c0], ctas, loads)
         b.record(stream)
         torch.cuda.synchronize()
-        probe[str(flavor)] = a.elapsed_time(b)
+        probe[f"path{flavor}_ctas{ctas}_loads{loads}"] = a.elapsed_time(b)
     best = min(probe.values())
     res["random_gather_probe"] = {
-        "count": c0, "ms": probe, "best_ms": best,
+        "count": c0, "ms": probe, "best_ms": best, "best": min(probe, key=probe.get),
         "gathers_per_s": c0 / (best / 1e3),
         "frac_of_sector_rate": (c0 / (best / 1e3)) / (hbm * 1e9 / SECTOR_BYTES),
         "what": "uniformly random 8-byte reads of the table and one 4-byte store each "
-                "(wrs_diag_random_gather; flavors 0/1/2 = ld.global.nc/.cg/.cs)"}
+                "(wrs_diag_random_gather; path 0/1/2 = ld.global.nc/.cg/.cs)"}
     return res
 
 
