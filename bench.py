@@ -650,12 +650,31 @@ def run_power_law(args, world):
     info = wrs.parse_info(b.info)
     hbm, _ = peaks()
     build_ms, sample_ms = statistics.mean(bm), statistics.mean(sm)
+    # precision study: the split and pack steps with exact fixed point (the
+    # build's), FP64 and paired-FP32 prefix arithmetic on the same lists
+    precision = []
+    ws2 = torch.empty(wrs.build_workspace_bytes(n, cfg), dtype=torch.uint8, device="cuda")
+    pws = torch.empty(wrs.diag_prec_workspace_bytes(n, cfg), dtype=torch.uint8, device="cuda")
+    rows2 = torch.empty(n, dtype=torch.int64, device="cuda")
+    wrs.step_total(w, ws2, cfg)
+    wrs.step_partition(w, ws2, cfg)
+    for name, fn in (("exact fixed point (the build)",
+                      lambda: (wrs.step_split(n, ws2, cfg), wrs.step_pack(n, rows2, ws2, cfg))),
+                     ("FP64", lambda: wrs.diag_prec_split_pack(n, rows2, ws2, pws, cfg,
+                                                               wrs.PREC_FP64)),
+                     ("paired FP32 (compensated)",
+                      lambda: wrs.diag_prec_split_pack(n, rows2, ws2, pws, cfg, wrs.PREC_FF))):
+        ms = _time_ms(fn, max(3, args.steps))
+        precision.append({"arithmetic": name, "split_pack_ms": ms,
+                          "max_mass_error": device_mass_error(rows2, w)})
+    del ws2, pws, rows2
     res = {"n": n, "samples": count, "weights": "w = 1/rank, ranks permuted (seed 3)",
            "status": info["status"], "nh": info["nh"],
            "build_ms": build_ms, "items_per_s": world * n / (build_ms / 1e3),
            "build_frac": BUILD_BYTES_PER_ITEM * n / (build_ms / 1e3) / 1e9 / hbm,
            "sample_ms": sample_ms, "samples_per_s": world * count / (sample_ms / 1e3),
-           "max_mass_error": device_mass_error(rows, w), "mass_error_bound": 1e-5}
+           "max_mass_error": device_mass_error(rows, w), "mass_error_bound": 1e-5,
+           "precision": precision}
     del w, b, rows, out
     torch.cuda.empty_cache()
     return res

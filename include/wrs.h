@@ -580,6 +580,26 @@ int wrs_diag_pack_variant(const float *d_w, uint64_t n, wrs_row *d_rows, void *d
                           uint64_t ws_bytes, const wrs_config *cfg, uint32_t variant,
                           void *stream);
 
+/* Precision study (Sec. 2.2 keeps the prefix sums of the light and heavy
+ * weights, the split comparisons and the sweep's residual in FP64; the
+ * build does them in exact fixed point): the split and pack steps redone on
+ * a build's lists with floating-point prefix arithmetic, for measurement.
+ *   prec 0: FP64;  prec 1: pairs of FP32 values (hi + lo, about 48 bits)
+ *   with compensated additions (TwoSum / Fast2Sum).
+ * Checkpoint sums every 32 list entries (scanned), splits by a 32-ary search
+ * over them and a warp search inside one interval, then the merge-path pack
+ * of every section on keys A(i) = i avg - sl(i) and B(j) = sh(j+1) - (j+1) avg
+ * (heavy h[j] closes before light l[i] iff B(j) <= A(i)); rows by item index.
+ * d_ws: a build's workspace after wrs_step_partition (same n and cfg);
+ * d_pws: wrs_diag_prec_workspace_bytes(n, cfg) bytes, 256-byte aligned.
+ * section_size at most 1024.  The table is valid (tested by reconstructed
+ * mass); it is not the exact build's table.  Errors: WRS_EINVAL for another
+ * prec, a larger section or short/misaligned buffers. */
+int wrs_diag_prec_workspace_bytes(uint64_t n, const wrs_config *cfg, uint64_t *bytes);
+int wrs_diag_prec_split_pack(uint64_t n, wrs_row *d_rows, void *d_ws, uint64_t ws_bytes,
+                             void *d_pws, uint64_t pws_bytes, const wrs_config *cfg,
+                             uint32_t prec, void *stream);
+
 /* Philox-rate probe (measures the hardware; no counterpart in the paper):
  * ceil(count/2) Philox-4x32-10 calls, call c on counter
  * (c_lo, c_hi, 0, WRS_TAG_DIAG) under key (seed_lo, seed_hi), writing

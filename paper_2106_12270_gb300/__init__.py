@@ -128,6 +128,8 @@ def lib():
                 "wrs_batch_export": (I, [P, P, I]),
                 "wrs_batch_destroy": (I, [P]),
                 "wrs_diag_philox": (I, [U64, U64, P, P]),
+                "wrs_diag_prec_workspace_bytes": (I, [U64, CP, ctypes.POINTER(U64)]),
+                "wrs_diag_prec_split_pack": (I, [U64, P, P, U64, P, U64, CP, U32, P]),
                 "wrs_diag_pack_variant": (I, [P, U64, P, P, U64, P, U32, P]),
                 "wrs_build_plus_workspace_bytes": (I, [U64, P, ctypes.POINTER(U64)]),
                 "wrs_build_rows_plus": (I, [P, U64, P, P, U64, P, U32, P, ctypes.POINTER(U64), P]),
@@ -557,6 +559,26 @@ def diag_pack_variant(w, n: int, rows, ws, cfg: Config | None = None, variant: i
     _check(lib().wrs_diag_pack_variant(_ptr(w), n, _ptr(rows),
                                        _ptr(ws), ws.numel() * ws.element_size(), _cfg(cfg),
                                        variant, _stream(stream)), "wrs_diag_pack_variant")
+
+
+PREC_FP64, PREC_FF = 0, 1
+
+
+def diag_prec_workspace_bytes(n: int, cfg: Config | None = None) -> int:
+    out = ctypes.c_uint64()
+    _check(lib().wrs_diag_prec_workspace_bytes(n, _cfg(cfg), ctypes.byref(out)),
+           "wrs_diag_prec_workspace_bytes")
+    return out.value
+
+
+def diag_prec_split_pack(n: int, rows, ws, pws, cfg: Config | None = None,
+                         prec: int = PREC_FP64, stream=None):
+    """Split and pack with FP64 (prec 0) or paired-FP32 (prec 1) prefix
+    arithmetic on a build's lists (ws after step_partition): the precision
+    study of Sec. 2.2's prefix sums (measurement, not the library's build)."""
+    _check(lib().wrs_diag_prec_split_pack(n, _ptr(rows), _ptr(ws), ws.numel() * ws.element_size(),
+                                          _ptr(pws), pws.numel() * pws.element_size(), _cfg(cfg),
+                                          prec, _stream(stream)), "wrs_diag_prec_split_pack")
 
 
 def diag_philox(count: int, seed: int, out, stream=None):

@@ -32,6 +32,10 @@ cudaError_t launch_philox_rate(uint64_t, uint64_t, uint32_t *, cudaStream_t);
 cudaError_t launch_pack_variant(const float *, uint64_t, wrs_row *, unsigned char *, const Layout &,
                                 uint32_t, uint32_t, cudaStream_t);
 
+uint64_t prec_workspace_bytes(uint64_t n, uint32_t S);
+cudaError_t launch_prec_split_pack(uint64_t n, wrs_row *d_rows, unsigned char *ws, const Layout &L,
+                                   unsigned char *pws, uint32_t S, uint32_t prec, cudaStream_t st);
+
 struct PlusLayout;
 uint64_t plus_workspace_bytes(uint64_t n, uint32_t S);
 cudaError_t launch_build_plus_ws(const float *d_w, uint64_t n, wrs_row *d_rows, unsigned char *ws,
@@ -540,6 +544,31 @@ int wrs_diag_pack_variant(const float *d_w, uint64_t n, wrs_row *d_rows, void *d
     if (variant == 0 && (!d_w || ((uintptr_t)d_w & 3u))) return WRS_EINVAL;
     return cuda_status(launch_pack_variant(d_w, n, d_rows, (unsigned char *)d_ws, L,
                                            c.section_size, variant, (cudaStream_t)stream));
+}
+
+int wrs_diag_prec_workspace_bytes(uint64_t n, const wrs_config *cfg, uint64_t *bytes) {
+    wrs_config c;
+    if (!bytes || n == 0 || n > kMaxN) return WRS_EINVAL;
+    int rc = resolve_cfg(cfg, &c);
+    if (rc) return rc;
+    if (c.section_size > 1024) return WRS_EINVAL;
+    *bytes = prec_workspace_bytes(n, c.section_size);
+    return WRS_OK;
+}
+
+int wrs_diag_prec_split_pack(uint64_t n, wrs_row *d_rows, void *d_ws, uint64_t ws_bytes,
+                             void *d_pws, uint64_t pws_bytes, const wrs_config *cfg,
+                             uint32_t prec, void *stream) {
+    wrs_config c;
+    Layout L;
+    int rc = prep(n, d_ws, ws_bytes, cfg, &c, &L);
+    if (rc) return rc;
+    if (prec > 1 || c.section_size > 1024 || !d_rows || ((uintptr_t)d_rows & 7u)) return WRS_EINVAL;
+    if (!d_pws || ((uintptr_t)d_pws & 255u) || pws_bytes < prec_workspace_bytes(n, c.section_size))
+        return WRS_EINVAL;
+    return cuda_status(launch_prec_split_pack(n, d_rows, (unsigned char *)d_ws, L,
+                                              (unsigned char *)d_pws, c.section_size, prec,
+                                              (cudaStream_t)stream));
 }
 
 int wrs_diag_philox(uint64_t count, uint64_t seed, uint32_t *d_out, void *stream) {
