@@ -1076,9 +1076,13 @@ cudaError_t launch_total(const float *d_w, uint64_t n, unsigned char *ws, const 
     return cudaGetLastError();
 }
 
+// One wave of partition CTAs (kSegPerSM resident per SM, one sub-segment per
+// warp); tables of 2^28 items and more take two waves of half-size
+// sub-segments, which evens out the CTAs that finish last.
 uint32_t num_segments(uint64_t n) {
     const uint64_t C = (n + kChunk - 1) / kChunk;
-    uint64_t g = (uint64_t)num_sms() * kSegPerSM * (kPartThreads / 32);
+    const uint64_t waves = n >= (1ull << 28) ? 2 : 1;
+    uint64_t g = (uint64_t)num_sms() * kSegPerSM * (kPartThreads / 32) * waves;
     if (g > (uint64_t)kMaxSegs - 1) g = kMaxSegs - 1;
     if (g > C) g = C;
     return (uint32_t)(g ? g : 1);

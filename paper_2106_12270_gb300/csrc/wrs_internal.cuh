@@ -117,7 +117,7 @@ constexpr int kSumBands = 16;   // total weight: bands of 16 binades
 constexpr int kSumMaxBlocks = 1216;   // 8 x 152 SMs
 constexpr int kPartThreads = 256;
 constexpr int kPartItems = 16;
-constexpr int kSegPerSM = 4;          // partition CTAs per SM (8 warps, one sub-segment each)
+constexpr int kSegPerSM = 3;          // partition CTAs resident per SM (8 warps, one sub-segment each)
 constexpr int kMaxSegs = 8192;        // sub-segments (a multiple of 1024)
 constexpr int kChunk = 512;           // items a partition warp handles at a time
 constexpr int kSplitThreads = 256;    // also p of the partial p-ary search
