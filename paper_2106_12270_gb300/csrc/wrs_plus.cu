@@ -91,8 +91,8 @@ __device__ __forceinline__ uint32_t tile_scan_u32(uint32_t v, uint32_t *tot_smem
     return pre;
 }
 
-// The greedy pass of PSA+ (Sec. 4 "PSA+"): persistent CTAs, CTA s owning
-// the tiles of sub-segment s.  Per tile:
+// The greedy pass of PSA+ (Sec. 4 "PSA+"): one CTA per tile (tile =
+// blockIdx.x).  Per tile:
 //   - load the weights (thread t: items 8t .. 8t+7), classify light/heavy,
 //     rank them with a block scan and stage the entries in list order
 //     (lights in index order, then heavies in index order);
@@ -101,7 +101,7 @@ __device__ __forceinline__ uint32_t tile_scan_u32(uint32_t v, uint32_t *tot_smem
 //     deficits/excesses, the sweep keys with prefixes starting at 0 in the
 //     tile (as the pack forms them for a section), how far the sweep
 //     reaches, and the rows of the buckets it closes (merge path);
-//   - the items it did not finish, in index order, to this sub-segment's
+//   - the items it did not finish, in index order, to this tile's
 //     region of the rest arrays; the heavy current at the stop carries its
 //     remaining excess as the weight (Q + r) / (N 2^S) in FP32.
 __global__ void __launch_bounds__(kTileThreads, 10)
