@@ -25,8 +25,9 @@
 //                            (Q + r) / (N 2^S) in FP32.
 //   k_rest_sum, k_rest_scan, k_rest_copy
 //                            the leftover counts summed per sub-segment (a
-//                            run of tiles), scanned, and the leftovers copied
-//                            to one dense array in tile order.
+//                            run of tiles) with each tile's offset in it,
+//                            scanned, and the leftovers copied (one warp per
+//                            tile) to one dense array in tile order.
 //   PSA on the rest          the unchanged PSA pipeline on the dense weights.
 //   k_rest_remap             its rows moved to the original item indices.
 //
@@ -371,20 +372,38 @@ k_greedy_tile(const float *__restrict__ w, uint64_t n, const BuildParams *__rest
     }
 }
 
-// The leftover count of every sub-segment: its tiles' counts summed (one
-// warp per sub-segment; sub-segment s holds tiles [s NT / NS, (s+1) NT / NS)).
+// The leftover count of every sub-segment and, for every tile, where its
+// leftovers start within the sub-segment's (one warp per sub-segment;
+// sub-segment s holds tiles [s NT / NS, (s+1) NT / NS)).  The warp takes 64
+// tiles per step (two coalesced loads in flight, two warp scans).
 __global__ void __launch_bounds__(256)
 k_rest_sum(const BuildParams *__restrict__ P, const uint32_t *__restrict__ tile_rest,
-           uint32_t *__restrict__ seg_rest, uint64_t NT, uint32_t NS) {
+           uint32_t *__restrict__ tile_off, uint32_t *__restrict__ seg_rest, uint64_t NT,
+           uint32_t NS) {
     if (P->status) return;
     const uint32_t s = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (s >= NS) return;
     const int lane = threadIdx.x & 31;
     const uint64_t a = (uint64_t)s * NT / NS, b = (uint64_t)(s + 1) * NT / NS;
-    uint32_t c = 0;
-    for (uint64_t t = a + lane; t < b; t += 32) c += tile_rest[t];
-    c = __reduce_add_sync(0xffffffffu, c);
-    if (lane == 0) seg_rest[s] = c;
+    uint32_t run = 0;
+    for (uint64_t t0 = a; t0 < b; t0 += 64) {
+        const uint64_t t1 = t0 + lane, t2 = t0 + 32 + lane;
+        const uint32_t c1 = t1 < b ? tile_rest[t1] : 0u;
+        const uint32_t c2 = t2 < b ? tile_rest[t2] : 0u;
+        uint32_t i1 = c1, i2 = c2;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t o1 = __shfl_up_sync(0xffffffffu, i1, d);
+            const uint32_t o2 = __shfl_up_sync(0xffffffffu, i2, d);
+            if (lane >= d) { i1 += o1; i2 += o2; }
+        }
+        const uint32_t tot1 = __shfl_sync(0xffffffffu, i1, 31);
+        const uint32_t tot2 = __shfl_sync(0xffffffffu, i2, 31);
+        if (t1 < b) tile_off[t1] = run + i1 - c1;
+        if (t2 < b) tile_off[t2] = run + tot1 + i2 - c2;
+        run += tot1 + tot2;
+    }
+    if (lane == 0) seg_rest[s] = run;
 }
 
 // One CTA (1024 threads): exclusive scan of the leftover counts of the
@@ -427,28 +446,29 @@ k_rest_scan(const BuildParams *__restrict__ P, const uint32_t *__restrict__ seg_
     if (threadIdx.x == 0) *n_rest = all;
 }
 
-// One warp per sub-segment: the leftovers of its tiles, in order, to their
-// place in the dense arrays (tile t's leftovers start at item t * kTile of
-// the rest arrays).
+// One warp per tile: the tile's leftovers, in order, to their place in the
+// dense arrays (tile t's leftovers start at item t * kTile of the rest
+// arrays; its place is its sub-segment's offset plus its offset within the
+// sub-segment).
 __global__ void __launch_bounds__(256)
 k_rest_copy(const BuildParams *__restrict__ P, const uint32_t *__restrict__ rest_idx,
             const float *__restrict__ rest_w, const uint32_t *__restrict__ tile_rest,
-            const uint64_t *__restrict__ rest_off, uint32_t *__restrict__ dense_idx,
-            float *__restrict__ dense_w, uint64_t NT, uint32_t NS) {
+            const uint32_t *__restrict__ tile_off, const uint64_t *__restrict__ rest_off,
+            uint32_t *__restrict__ dense_idx, float *__restrict__ dense_w, uint64_t NT,
+            uint32_t NS) {
     if (P->status) return;   // the greedy pass wrote no counts
-    const uint32_t s = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (s >= NS) return;
+    const uint64_t t = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (t >= NT) return;
     const int lane = threadIdx.x & 31;
-    const uint64_t a = (uint64_t)s * NT / NS, b = (uint64_t)(s + 1) * NT / NS;
-    uint64_t o = rest_off[s];
-    for (uint64_t t = a; t < b; ++t) {
-        const uint32_t cnt = tile_rest[t];
-        const uint64_t src = t * kTile;
-        for (uint32_t k = lane; k < cnt; k += 32) {
-            dense_idx[o + k] = rest_idx[src + k];
-            dense_w[o + k] = rest_w[src + k];
-        }
-        o += cnt;
+    const uint32_t cnt = tile_rest[t];
+    if (cnt == 0) return;
+    // the sub-segment holding tile t: the s with s NT / NS <= t < (s+1) NT / NS
+    const uint64_t s = ((t + 1) * NS + NT - 1) / NT - 1;
+    const uint64_t o = rest_off[s] + tile_off[t];
+    const uint64_t src = t * kTile;
+    for (uint32_t k = lane; k < cnt; k += 32) {
+        dense_idx[o + k] = rest_idx[src + k];
+        dense_w[o + k] = rest_w[src + k];
     }
 }
 
@@ -490,11 +510,11 @@ __global__ void k_plus_info(const BuildParams *__restrict__ P, const uint64_t *_
     *out = r;
 }
 
-// Workspace: [whole-table layout][rest_idx 4n][rest_w 4n][tile_rest][seg_rest][rest_off]
+// Workspace: [whole-table layout][rest_idx 4n][rest_w 4n][tile_rest][tile_off][seg_rest][rest_off]
 // [n_rest][dense_idx 4n][dense_w 4n][rest layout][rest rows 8n][rest info].
 struct PlusLayout {
     Layout L;
-    uint64_t rest_idx, rest_w, tile_rest, seg_rest, rest_off, n_rest, dense_idx, dense_w,
+    uint64_t rest_idx, rest_w, tile_rest, tile_off, seg_rest, rest_off, n_rest, dense_idx, dense_w,
         rest_ws, rest_rows, rest_info, total;
 };
 
@@ -510,6 +530,7 @@ PlusLayout make_plus_layout(uint64_t n, uint32_t S) {
     p.rest_idx = take(4 * n);
     p.rest_w = take(4 * n);
     p.tile_rest = take(4 * ((n + kTile - 1) / kTile));
+    p.tile_off = take(4 * ((n + kTile - 1) / kTile));
     p.seg_rest = take(4ull * kMaxSegs);
     p.rest_off = take(8ull * (kMaxSegs + 1));
     p.n_rest = take(8);
@@ -542,6 +563,7 @@ cudaError_t launch_build_plus(const float *d_w, uint64_t n, wrs_row *d_rows, uns
     auto *rest_idx = reinterpret_cast<uint32_t *>(ws + pl.rest_idx);
     auto *rest_w = reinterpret_cast<float *>(ws + pl.rest_w);
     auto *tile_rest = reinterpret_cast<uint32_t *>(ws + pl.tile_rest);
+    auto *tile_off = reinterpret_cast<uint32_t *>(ws + pl.tile_off);
     auto *seg_rest = reinterpret_cast<uint32_t *>(ws + pl.seg_rest);
     auto *rest_off = reinterpret_cast<uint64_t *>(ws + pl.rest_off);
     auto *n_rest = reinterpret_cast<uint64_t *>(ws + pl.n_rest);
@@ -554,10 +576,10 @@ cudaError_t launch_build_plus(const float *d_w, uint64_t n, wrs_row *d_rows, uns
                                                            reinterpret_cast<uint2 *>(d_rows),
                                                            rest_idx, rest_w, tile_rest, min_items,
                                                            aligned);
-    k_rest_sum<<<(NS + 7) / 8, 256, 0, st>>>(P, tile_rest, seg_rest, NT, NS);
+    k_rest_sum<<<(NS + 7) / 8, 256, 0, st>>>(P, tile_rest, tile_off, seg_rest, NT, NS);
     k_rest_scan<<<1, 1024, 0, st>>>(P, seg_rest, rest_off, n_rest, NS);
-    k_rest_copy<<<(NS + 7) / 8, 256, 0, st>>>(P, rest_idx, rest_w, tile_rest, rest_off, dense_idx,
-                                              dense_w, NT, NS);
+    k_rest_copy<<<(unsigned)((NT + 7) / 8), 256, 0, st>>>(P, rest_idx, rest_w, tile_rest, tile_off,
+                                                          rest_off, dense_idx, dense_w, NT, NS);
     e = cudaGetLastError();
     if (e) return e;
     // the rest's size decides its launches: one read back
