@@ -329,7 +329,8 @@ typedef struct wrs_table_summary {
     uint64_t nl, nh;  /* light and heavy counts */
 } wrs_table_summary;
 
-/* Device workspace bytes for a batch of `total` items (all tables). */
+/* Device workspace bytes for a batch of `total` items (all tables) in ntab
+ * tables: about 9 bytes per item and 150 per table. */
 int wrs_build_batched_workspace_bytes(uint64_t total, uint32_t ntab, uint64_t *bytes);
 
 /* Host-side plan: h_order receives the table ids largest first, the order in
@@ -337,29 +338,38 @@ int wrs_build_batched_workspace_bytes(uint64_t total, uint32_t ntab, uint64_t *b
  * first keeps the CTAs evenly loaded).  h_off: ntab+1 host offsets. */
 int wrs_batch_order(const uint64_t *h_off, uint32_t ntab, uint32_t *h_order);
 
-/* a8: build ntab tables in one launch.  Table t has the weights
+/* a8: build ntab tables with one launch sequence.  Table t has the weights
  * d_w[d_off[t] .. d_off[t+1]) and gets the rows d_rows[d_off[t] ..
- * d_off[t+1]) with table-local alias indices (PSA per table: exact total,
- * partition, chunked sweep-pack, Sec. 2.2 and Sec. 4.2).  d_off: ntab+1
- * device uint64 offsets, non-decreasing, d_off[0] = 0; d_order: ntab device
- * table ids (a permutation, e.g. from wrs_batch_order) or NULL for 0..ntab-1;
- * d_info: ntab device summaries.  A table with an error gets a status in its
- * summary and its rows are left untouched; the others are still built. */
+ * d_off[t+1]) with table-local alias indices (PSA per table, Sec. 2.2 and
+ * Sec. 4).  The default (segmented) build: one persistent CTA per table
+ * computes its exact total, Q and stable partition with the prefix-sum
+ * checkpoints; then the single-table split and pack run over the sections
+ * (1024 buckets) of every table at once.  d_off: ntab+1 device uint64
+ * offsets, non-decreasing, d_off[0] = 0; d_order: ntab device table ids (a
+ * permutation, e.g. from wrs_batch_order) or NULL for 0..ntab-1; d_info:
+ * ntab device summaries.  A table with an error gets a status in its
+ * summary and its rows are left untouched; the others are still built.  A
+ * workspace smaller than wrs_build_batched_workspace_bytes of the batch
+ * leaves the tables that do not fit with WRS_EINVAL.  No host sync. */
 int wrs_build_batched_rows(const float *d_w, const uint64_t *d_off, uint32_t ntab,
                            const uint32_t *d_order, wrs_row *d_rows, void *d_ws,
                            uint64_t ws_bytes, wrs_table_summary *d_info, void *stream);
 
-/* Tiling of the batched build.  The table does not depend on it (chunk ends
+/* How the batched build runs.  threads = 0 (and chunk = 0): the segmented
+ * build above.  Otherwise the chunked kernel: one persistent CTA per table
+ * runs the whole pipeline and sweeps in chunks (Sec. 4.2 "chunked loading"),
+ * carrying the exact Vose state from chunk to chunk instead of a split
+ * search.  The tables do not depend on the choice (chunk ends and sections
  * are splits of the same sweep), only the time does. */
 typedef struct wrs_batch_tuning {
-    uint32_t threads;      /* threads of a CTA: 256 or 512 */
-    uint32_t chunk;        /* buckets swept per chunk: 512, 1024, 2048 or 4096 */
+    uint32_t threads;      /* 0 (segmented) or threads of a chunked CTA: 256 or 512 */
+    uint32_t chunk;        /* 0 (segmented) or buckets per chunk: 512, 1024, 2048, 4096 */
     uint32_t ctas_per_sm;  /* resident CTAs per SM; 0 = as many as fit */
     float ms;              /* measured time of one build (wrs_batch_autotune) */
     uint32_t reserved[4];
 } wrs_batch_tuning;
 
-/* The default tiling: 256 threads, chunks of 1024 buckets, full occupancy. */
+/* The default: the segmented build (threads = chunk = 0). */
 int wrs_batch_tuning_default(wrs_batch_tuning *t);
 
 /* wrs_build_batched_rows with an explicit tiling (NULL = the default).
@@ -370,7 +380,8 @@ int wrs_build_batched_rows_tuned(const float *d_w, const uint64_t *d_off, uint32
                                  const wrs_batch_tuning *tuning, void *stream);
 
 /* Autotuner for the batched build: builds this batch once with every
- * candidate tiling (threads x chunk), times each with CUDA events on
+ * candidate (the segmented build and every threads x chunk tiling of the
+ * chunked kernel), times each with CUDA events on
  * `stream` (best of two runs after a warm-up), and returns the fastest in
  * *best; `all` (room for up to *nall entries, may be NULL) receives every
  * candidate with its time and *nall their number.  The buffers hold a valid

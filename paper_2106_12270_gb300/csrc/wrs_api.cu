@@ -362,8 +362,7 @@ int wrs_sample_auto(const wrs_row *d_rows, uint64_t n, uint64_t count, uint64_t 
 
 int wrs_build_batched_workspace_bytes(uint64_t total, uint32_t ntab, uint64_t *bytes) {
     if (!bytes) return WRS_EINVAL;
-    (void)ntab;
-    *bytes = 256 + align_up(total * sizeof(Entry), 256);
+    *bytes = batch_seg_layout(total, ntab).total;
     return WRS_OK;
 }
 
@@ -380,9 +379,7 @@ int wrs_batch_order(const uint64_t *h_off, uint32_t ntab, uint32_t *h_order) {
 
 int wrs_batch_tuning_default(wrs_batch_tuning *t) {
     if (!t) return WRS_EINVAL;
-    memset(t, 0, sizeof *t);
-    t->threads = 256;
-    t->chunk = 1024;
+    memset(t, 0, sizeof *t);   // threads 0: the segmented build
     return WRS_OK;
 }
 
@@ -396,10 +393,24 @@ int wrs_build_batched_rows_tuned(const float *d_w, const uint64_t *d_off, uint32
         return WRS_EINVAL;
     if (ws_bytes < 256) return WRS_EINVAL;
     if (tuning && !batch_tuning_valid(*tuning)) return WRS_EINVAL;
-    // the workspace must hold one l/h entry per item; the total is on the
-    // device, so the kernel trusts ws_bytes >= 256 + 8 * total (checked by
-    // the caller through wrs_build_batched_workspace_bytes)
     unsigned char *ws = (unsigned char *)d_ws;
+    if (!tuning || tuning->threads == 0) {
+        // the segmented build: the largest item count whose layout fits
+        // ws_bytes (the total is on the device; a table beyond it fails
+        // with WRS_EINVAL in its summary)
+        uint64_t lo = 0, hi = ws_bytes / sizeof(Entry);
+        while (lo < hi) {
+            const uint64_t mid = lo + (hi - lo + 1) / 2;
+            if (batch_seg_layout(mid, ntab).total <= ws_bytes) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchSegLayout L = batch_seg_layout(lo, ntab);
+        if (L.total > ws_bytes) return WRS_EINVAL;
+        return cuda_status(launch_build_batched_seg(d_w, d_off, ntab, d_order, ws, L, d_rows,
+                                                    nullptr, d_info, (cudaStream_t)stream));
+    }
+    // the chunked kernel: one l/h entry per item after the counter; the total
+    // is on the device, so the kernel trusts ws_bytes >= 256 + 8 * total
     return cuda_status(launch_build_batched(d_w, d_off, ntab, d_order,
                                             reinterpret_cast<uint32_t *>(ws),
                                             reinterpret_cast<Entry *>(ws + 256), d_rows, nullptr,
@@ -456,6 +467,11 @@ int wrs_batch_autotune(const float *d_w, const uint64_t *d_off, uint32_t ntab,
     static const uint32_t kThreads[] = {256, 512};
     static const uint32_t kChunks[] = {512, 1024, 2048, 4096};
     std::vector<wrs_batch_tuning> cand;
+    {
+        wrs_batch_tuning x;   // the segmented build
+        wrs_batch_tuning_default(&x);
+        cand.push_back(x);
+    }
     for (uint32_t t : kThreads)
         for (uint32_t c : kChunks) {
             wrs_batch_tuning x;

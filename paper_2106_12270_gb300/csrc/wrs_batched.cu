@@ -622,7 +622,382 @@ static cudaError_t launch_bb(const float *d_w, const uint64_t *d_off, uint32_t n
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Segmented batched build, first kernel.  A CTA takes the next table (work
+// counter, largest first) and runs the exact total, Q, and the stable
+// partition into the table's lh region as the chunked kernel does, and in
+// the same pass the clamped q prefix sums of both lists at every 32nd entry
+// (the checkpoints of the single-table build, table-local).  It then leaves
+// the table's BuildParams (W, the scale, Q, nl, nh, D'(nl), E'(nh)), takes
+// ceil(n / kBSeg) sections and their split records from two counters, marks
+// the sections with the table and writes splits 0 and s.  The split and pack
+// of the sections are the single-table kernels (k_bseg_split, k_bseg_pack).
+// ---------------------------------------------------------------------------
+template <int BT>
+struct BsegShared {
+    union {
+        uint64_t bins[kBands][BT];
+        struct {
+            float wv[kBTile + kBTile / 32];
+            Entry e[kBTile + kBTile / 16];
+        } part;
+    } u;
+    u128 band[kBands];
+    uint64_t qred[BT / 32], qred2[BT / 32];
+    uint32_t cred[BT / 32];
+    double W, avg;
+    uint64_t Q, Qn, nl;
+    float lmax, inv_avg, Qf, invQ;
+    int qshift, scale;
+    uint32_t status;
+    uint32_t table;
+    uint32_t sec0, rec0;
+};
+
+__device__ __forceinline__ void bseg_put_ck(CkRec *ck, uint64_t idx, uint64_t v) {
+    *reinterpret_cast<uint4 *>(ck + idx) = make_uint4(0u, 0u, (uint32_t)v, (uint32_t)(v >> 32));
+}
+
+template <int BT>
+__global__ void __launch_bounds__(BT, 1024 / BT)
+k_bseg_part(const float *__restrict__ w, const uint64_t *__restrict__ off,
+            const uint32_t *__restrict__ order, uint32_t ntab, uint32_t *__restrict__ ctr,
+            uint64_t cap, Entry *__restrict__ lh, BuildParams *__restrict__ tp,
+            BatchTab *__restrict__ tabs, uint32_t *__restrict__ sec_tab, CkRec *__restrict__ ckl,
+            CkRec *__restrict__ ckh, SplitRec *__restrict__ recs,
+            wrs_table_summary *__restrict__ info) {
+    constexpr int kItems = kBTile / BT;   // items of a thread in a partition tile
+    extern __shared__ __align__(16) unsigned char bsm_raw[];
+    BsegShared<BT> &sm = *reinterpret_cast<BsegShared<BT> *>(bsm_raw);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (;;) {
+        if (tid == 0) {
+            uint32_t k = atomicAdd(ctr, 1u);
+            sm.table = k < ntab ? (order ? order[k] : k) : 0xffffffffu;
+        }
+        __syncthreads();
+        const uint32_t t = sm.table;
+        if (t == 0xffffffffu) return;
+        const uint64_t base = off[t], n = off[t + 1] - base;
+        auto fail = [&](uint32_t st, int status) {
+            // no sections: the split and pack kernels never see this table
+            if (tid == 0) {
+                BuildParams z;
+                memset(&z, 0, sizeof z);
+                z.status = st;
+                z.n = n;
+                tp[t] = z;
+                tabs[t] = BatchTab{base, 0u, 0u};
+                wrs_table_summary r;
+                r.status = status; r.n = (uint32_t)n; r.W = 0.0; r.nl = r.nh = 0;
+                info[t] = r;
+            }
+            __syncthreads();
+        };
+        if (n == 0 || n > kBatchMaxItems || base + n > cap) {
+            fail(ERR_INTERNAL, WRS_EINVAL);
+            continue;
+        }
+        const float *wt = w + base;
+
+        // ---- exact total of this table
+        for (int b = 0; b < kBands; ++b) sm.u.bins[b][tid] = 0;
+        uint32_t bad = 0;
+        for (uint64_t a = tid; a < n; a += BT) {
+            uint32_t band;
+            uint64_t val;
+            band_of(__ldg(wt + a), band, val, bad);
+            sm.u.bins[band][tid] += val;
+        }
+        bad = __reduce_or_sync(0xffffffffu, bad);
+        if (lane == 0) sm.cred[warp] = bad;
+        __syncthreads();
+        for (int b = warp; b < kBands; b += BT / 32) {
+            u128 s = 0;
+            for (int k = 0; k < BT / 32; ++k) s += sm.u.bins[b][lane + 32 * k];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                uint64_t lo = __shfl_xor_sync(0xffffffffu, (uint64_t)s, d);
+                uint64_t hi = __shfl_xor_sync(0xffffffffu, (uint64_t)(s >> 64), d);
+                s += ((u128)hi << 64) | lo;
+            }
+            if (lane == 0) sm.band[b] = s;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t st = 0;
+            for (int k = 0; k < BT / 32; ++k) st |= sm.cred[k];
+            double W = 0.0;
+            int top = -1;
+            if (!st && !exact_total(sm.band, W, top)) st |= ERR_ZEROSUM;
+            sm.status = st;
+            if (!st) {
+                double avg = W / (double)n;
+                sm.W = W;
+                sm.avg = avg;
+                sm.qshift = 61 - top;
+                sm.scale = 211 - top;
+                sm.lmax = __double2float_rd(avg);
+                sm.inv_avg = __double2float_rn(1.0 / avg);
+            }
+        }
+        __syncthreads();
+        if (sm.status) {
+            const uint32_t st = sm.status;
+            fail(st, (st & ERR_NONFINITE) ? WRS_ENONFINITE
+                     : (st & ERR_NEGATIVE) ? WRS_EINVAL : WRS_EZEROSUM);
+            continue;
+        }
+        const QScale qsc = qscale(sm.qshift);
+        const float lmax = sm.lmax;
+
+        // ---- Q = sum of q over the table, and the light count
+        {
+            uint64_t qs = 0;
+            uint32_t c = 0;
+            for (uint64_t a = tid; a < n; a += BT) {
+                float x = __ldg(wt + a);
+                qs += fixed_q(x, qsc);
+                c += x <= lmax;
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) {
+                qs += __shfl_xor_sync(0xffffffffu, qs, d);
+                c += __shfl_xor_sync(0xffffffffu, c, d);
+            }
+            if (lane == 0) {
+                sm.qred[warp] = qs;
+                sm.cred[warp] = c;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                uint64_t Q = 0, nl = 0;
+                for (int k = 0; k < BT / 32; ++k) {
+                    Q += sm.qred[k];
+                    nl += sm.cred[k];
+                }
+                sm.Q = Q;
+                sm.Qn = Q / n;
+                sm.nl = nl;
+                sm.Qf = __ull2float_rn(Q);
+                sm.invQ = __frcp_rn(sm.Qf);
+            }
+            __syncthreads();
+        }
+        const uint64_t Q = sm.Q, Qn = sm.Qn, nl = sm.nl, nh = n - nl;
+        const uint64_t ckb = bseg_ck(base, t, 0);
+
+        // ---- stable partition of the table into its lh region, with the
+        // clamped q prefix sums at every 32nd list entry
+        uint64_t run_sl = 0, run_sh = 0;   // clamped q sums of the lights / heavies placed
+        {
+            uint64_t run_l = 0;
+            const int e0 = warp * (32 * kItems) + lane * kItems;
+            const int s0 = tid * kItems;   // this thread's list slots of the tile
+            for (uint64_t tb = 0; tb < n; tb += kBTile) {
+                const uint64_t lim = n - tb;
+#pragma unroll
+                for (int r = 0; r < kItems / 4; ++r) {
+                    int e = warp * (32 * kItems) + r * 128 + lane * 4;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        sm.u.part.wv[pad32(e + c)] =
+                            (uint64_t)(e + c) < lim ? __ldg(wt + tb + e + c) : 0.f;
+                }
+                __syncwarp();
+                const bool fullt = lim >= (uint64_t)kBTile;   // every tile but the table's last
+                uint32_t lmask = 0, vmask = 0;
+                if (fullt) {
+                    vmask = (kItems == 32) ? 0xffffffffu : ((1u << kItems) - 1u);
+#pragma unroll
+                    for (int k = 0; k < kItems; ++k)
+                        lmask |= (uint32_t)(sm.u.part.wv[pad32(e0 + k)] <= lmax) << k;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < kItems; ++k) {
+                        float x = sm.u.part.wv[pad32(e0 + k)];
+                        bool valid = (uint64_t)(e0 + k) < lim;
+                        vmask |= (uint32_t)valid << k;
+                        lmask |= (uint32_t)(valid && x <= lmax) << k;
+                    }
+                }
+                const uint32_t cnt = __popc(lmask);
+                uint32_t icnt = cnt;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    uint32_t c2 = __shfl_up_sync(0xffffffffu, icnt, d);
+                    if (lane >= d) icnt += c2;
+                }
+                if (lane == 31) sm.cred[warp] = icnt;
+                __syncthreads();
+                uint32_t wl = 0, tl = 0;
+                for (int k = 0; k < BT / 32; ++k) {
+                    wl += (k < warp) ? sm.cred[k] : 0u;
+                    tl += sm.cred[k];
+                }
+                const uint64_t run_h = tb - run_l;
+                const uint32_t tv = lim < (uint64_t)kBTile ? (uint32_t)lim : (uint32_t)kBTile;
+                const uint32_t tnh = tv - tl;
+                uint32_t lrank = wl + icnt - cnt, hrank = (uint32_t)e0 - lrank;
+#pragma unroll
+                for (int k = 0; k < kItems; ++k) {
+                    if (!fullt && !((vmask >> k) & 1u)) break;
+                    Entry en{(uint32_t)(tb + e0 + k), sm.u.part.wv[pad32(e0 + k)]};
+                    if ((lmask >> k) & 1u) sm.u.part.e[pad16(lrank++)] = en;
+                    else sm.u.part.e[pad16(kBTile - 1 - hrank++)] = en;
+                }
+                __syncthreads();
+                // clamped q of this thread's slots in list order (lights at
+                // [0, tl), heavy rank b at slot kBTile-1-b); the light
+                // checkpoint slot (light rank a multiple of 32) snapshots the
+                // exclusive light sum, the heavy one the inclusive heavy sum
+                {
+                    const uint32_t hs = kBTile - tnh;   // first heavy slot
+                    const int kl = (int)((((32u - (uint32_t)(run_l & 31u)) & 31u) - (uint32_t)s0) & 31u);
+                    const int kh = (int)((((uint32_t)(run_h + kBTile - 1) & 31u) - (uint32_t)s0) & 31u);
+                    uint64_t sl = 0, sh = 0, snap_l = 0, snap_h = 0;
+#pragma unroll
+                    for (int k = 0; k < kItems; ++k) {
+                        const uint32_t slot = (uint32_t)(s0 + k);
+                        if (k == kl) snap_l = sl;
+                        const uint64_t q = fixed_q(sm.u.part.e[pad16(slot)].w, qsc);
+                        sl += slot < tl ? (q > Qn ? Qn : q) : 0ull;
+                        sh += slot >= hs ? (q <= Qn ? Qn + 1 : q) : 0ull;
+                        if (k == kh) snap_h = sh;
+                    }
+                    uint64_t il = sl, ih = sh;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const uint64_t ol = __shfl_up_sync(0xffffffffu, il, d);
+                        const uint64_t oh = __shfl_up_sync(0xffffffffu, ih, d);
+                        if (lane >= d) { il += ol; ih += oh; }
+                    }
+                    if (lane == 31) { sm.qred[warp] = il; sm.qred2[warp] = ih; }
+                    __syncthreads();
+                    uint64_t pl = il - sl, ph = ih - sh, TL = 0, TH = 0;
+                    for (int k = 0; k < BT / 32; ++k) {
+                        pl += k < warp ? sm.qred[k] : 0ull;
+                        ph += k < warp ? sm.qred2[k] : 0ull;
+                        TL += sm.qred[k];
+                        TH += sm.qred2[k];
+                    }
+                    if (kl < kItems && (uint32_t)(s0 + kl) < tl)
+                        bseg_put_ck(ckl, ckb + ((run_l + s0 + kl) >> 5), run_sl + pl + snap_l);
+                    if (kh < kItems && (uint32_t)(s0 + kh) >= hs)
+                        bseg_put_ck(ckh, ckb + ((run_h + kBTile - 1 - (s0 + kh)) >> 5),
+                                    run_sh + TH - (ph + snap_h));
+                    run_sl += TL;
+                    run_sh += TH;
+                }
+                uint2 *lh2 = reinterpret_cast<uint2 *>(lh + base);
+                const uint2 *e2 = reinterpret_cast<const uint2 *>(sm.u.part.e);
+                for (uint32_t a = tid; a < tl; a += BT) lh2[run_l + a] = e2[pad16(a)];
+                for (uint32_t b = tid; b < tnh; b += BT)
+                    lh2[n - 1 - (run_h + b)] = e2[pad16(kBTile - 1 - b)];
+                run_l += tl;
+                __syncthreads();
+            }
+        }
+
+        // ---- the table's parameters, sections and end splits
+        const uint32_t ns = (uint32_t)((n + kBSeg - 1) / kBSeg);
+        const u128 Dtot = (u128)nl * Q - (u128)run_sl * n;
+        const u128 Etot = (u128)run_sh * n - (u128)nh * Q;
+        if (tid == 0) {
+            sm.sec0 = atomicAdd(ctr + 1, ns);
+            sm.rec0 = atomicAdd(ctr + 2, ns + 1);
+            BuildParams p;
+            memset(&p, 0, sizeof p);
+            p.Dtot = Dtot;
+            p.Etot = Etot;
+            p.W = sm.W;
+            p.avg = sm.avg;
+            p.Q = Q;
+            p.Qn = Qn;
+            p.n = n;
+            p.nl = nl;
+            p.nh = nh;
+            p.status = 0;
+            p.scale = sm.scale;
+            p.qshift = sm.qshift;
+            p.light_max = lmax;
+            p.inv_avg = sm.inv_avg;
+            p.Qf = sm.Qf;
+            p.invQ = sm.invQ;
+            p.sections = ns;
+            tp[t] = p;
+            if ((nl & 31u) == 0) bseg_put_ck(ckl, ckb + (nl >> 5), run_sl);
+            if ((nh & 31u) == 0) bseg_put_ck(ckh, ckb + (nh >> 5), run_sh);
+            wrs_table_summary r;
+            r.status = WRS_OK;
+            r.n = (uint32_t)n;
+            r.W = sm.W;
+            r.nl = nl;
+            r.nh = nh;
+            info[t] = r;
+        }
+        __syncthreads();
+        const uint32_t sec0 = sm.sec0, rec0 = sm.rec0;
+        for (uint32_t k = tid; k < ns; k += BT) sec_tab[sec0 + k] = t;
+        if (tid == 0) {
+            tabs[t] = BatchTab{base, sec0, rec0};
+            SplitRec r0, rs;
+            r0.i = r0.j = 0; r0.pad[0] = r0.pad[1] = 0; r0.D = 0; r0.E = 0;
+            rs.i = (uint32_t)nl; rs.j = (uint32_t)nh; rs.pad[0] = rs.pad[1] = 0;
+            rs.D = Dtot; rs.E = Etot;
+            recs[rec0] = r0;
+            recs[rec0 + ns] = rs;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_bseg_split_pack(unsigned char *ws, const BatchSegLayout &L, uint32_t ntab,
+                                   wrs_row *d_rows, wrs_row *const *d_row_ptrs,
+                                   wrs_table_summary *d_info, cudaStream_t st);
+
+// The segmented batched build: partition (one persistent CTA per table),
+// then the single-table split and pack over every table's sections.
+cudaError_t launch_build_batched_seg(const float *d_w, const uint64_t *d_off, uint32_t ntab,
+                                     const uint32_t *d_order, unsigned char *ws,
+                                     const BatchSegLayout &L, wrs_row *d_rows,
+                                     wrs_row *const *d_row_ptrs, wrs_table_summary *d_info,
+                                     cudaStream_t st) {
+    constexpr int BT = 256;
+    const int smem = (int)sizeof(BsegShared<BT>);
+    cudaError_t e = ensure_dynamic_smem<k_bseg_part<BT>>((uint32_t)smem);
+    if (e) return e;
+    static std::atomic<int> resident[kMaxDevices];
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e) return e;
+    const int slot = dev >= 0 && dev < kMaxDevices ? dev : 0;
+    int per_sm = resident[slot].load(std::memory_order_relaxed);
+    if (per_sm <= 0) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bseg_part<BT>, BT, smem);
+        if (e) return e;
+        if (per_sm < 1) per_sm = 1;
+        resident[slot].store(per_sm, std::memory_order_relaxed);
+    }
+    auto *ctr = reinterpret_cast<uint32_t *>(ws + L.counters);
+    e = cudaMemsetAsync(ctr, 0, 3 * sizeof(uint32_t), st);
+    if (!e) e = cudaMemsetAsync(ws + L.zero, 0, sizeof(SegVal), st);
+    if (e) return e;
+    unsigned blocks = (unsigned)num_sms() * (unsigned)per_sm;
+    if (blocks > ntab) blocks = ntab ? ntab : 1;
+    k_bseg_part<BT><<<blocks, BT, smem, st>>>(
+        d_w, d_off, d_order, ntab, ctr, L.cap, reinterpret_cast<Entry *>(ws + L.lh),
+        reinterpret_cast<BuildParams *>(ws + L.tp), reinterpret_cast<BatchTab *>(ws + L.tabs),
+        reinterpret_cast<uint32_t *>(ws + L.sec_tab), reinterpret_cast<CkRec *>(ws + L.ckl),
+        reinterpret_cast<CkRec *>(ws + L.ckh), reinterpret_cast<SplitRec *>(ws + L.recs), d_info);
+    e = cudaGetLastError();
+    if (e) return e;
+    return launch_bseg_split_pack(ws, L, ntab, d_rows, d_row_ptrs, d_info, st);
+}
+
 bool batch_tuning_valid(const wrs_batch_tuning &t) {
+    if (t.threads == 0) return t.chunk == 0;   // the segmented build
     return (t.threads == 256 || t.threads == 512) &&
            (t.chunk == 512 || t.chunk == 1024 || t.chunk == 2048 || t.chunk == 4096) &&
            t.ctas_per_sm <= 64;

@@ -821,7 +821,8 @@ template <int kPer>
 __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
                                              const Entry *__restrict__ lh,
                                              const SplitRec *__restrict__ splits,
-                                             uint2 *__restrict__ rows, uint64_t n, uint32_t S) {
+                                             uint2 *__restrict__ rows, uint64_t n, uint32_t S,
+                                             uint32_t t) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ u128 s_w[16];
     if (P->status) return;
@@ -831,7 +832,6 @@ __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
     const uint32_t T = blockDim.x;
     const uint32_t tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const uint32_t t = blockIdx.x;
     const uint64_t nh = P->nh;
     const uint64_t Q = P->Q, Qn = P->Qn;
     const uint32_t N = (uint32_t)n;
@@ -1009,13 +1009,153 @@ __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
 __global__ void __maxnreg__(48)
 k_pack8(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
         const SplitRec *__restrict__ splits, uint2 *__restrict__ rows, uint64_t n, uint32_t S) {
-    pack_section<8>(P, lh, splits, rows, n, S);
+    pack_section<8>(P, lh, splits, rows, n, S, blockIdx.x);
 }
 // Larger sections: 16 positions per thread, 512 threads.
 __global__ void __launch_bounds__(512)
 k_pack16(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
          const SplitRec *__restrict__ splits, uint2 *__restrict__ rows, uint64_t n, uint32_t S) {
-    pack_section<16>(P, lh, splits, rows, n, S);
+    pack_section<16>(P, lh, splits, rows, n, S, blockIdx.x);
+}
+
+
+// ===========================================================================
+// Segmented batched build: split and pack of every table's sections
+// ===========================================================================
+
+BatchSegLayout batch_seg_layout(uint64_t cap, uint32_t ntab) {
+    BatchSegLayout L;
+    uint64_t off = 0;
+    auto take = [&](uint64_t bytes) {
+        const uint64_t o = off;
+        off = align_up(off + (bytes ? bytes : 1), 256);
+        return o;
+    };
+    L.cap = cap;
+    L.counters = take(256);
+    L.lh = take(cap * sizeof(Entry));
+    L.tp = take((uint64_t)ntab * sizeof(BuildParams));
+    L.tabs = take((uint64_t)ntab * sizeof(BatchTab));
+    L.sec_tab = take((cap / kBSeg + ntab + 1) * 4);
+    L.ckl = take(((cap >> 5) + 2ull * ntab + 2) * sizeof(CkRec));
+    L.ckh = take(((cap >> 5) + 2ull * ntab + 2) * sizeof(CkRec));
+    L.recs = take((cap / kBSeg + 2ull * ntab + 1) * sizeof(SplitRec));
+    L.zero = take(sizeof(SegVal));
+    L.total = off;
+    return L;
+}
+
+__device__ __forceinline__ SplitCtx bseg_ctx(const BuildParams &Pm, const BatchTab &tb, uint32_t t,
+                                             const Entry *lh, const CkRec *ckl, const CkRec *ckh,
+                                             const SegVal *zero) {
+    SplitCtx C;
+    const uint64_t ckb = bseg_ck(tb.base, t, 0);
+    C.ckl = ckl + ckb;
+    C.ckh = ckh + ckb;
+    C.seg_pre = zero;   // checkpoints hold table-local sums (segment 0, prefix 0)
+    C.lh = lh + tb.base;
+    C.n = Pm.n;
+    C.nl = Pm.nl;
+    C.nh = Pm.nh;
+    C.Q = Pm.Q;
+    return C;
+}
+
+// Interior splits of every table: one warp per section j >= 1 of a table
+// finds split j (k = j kBSeg buckets): a 32-ary search over the table's
+// checkpoints for the smallest c with E'(k - 32c) <= D'(32c) (under the
+// sweep's rule), then the fine search inside 32 entries (split_fine).  The
+// partition kernel wrote splits 0 and s of each table.
+__global__ void __launch_bounds__(256)
+k_bseg_split(const uint32_t *__restrict__ ctr, const uint32_t *__restrict__ sec_tab,
+             const BatchTab *__restrict__ tabs, const BuildParams *__restrict__ tp,
+             const Entry *__restrict__ lh, const CkRec *__restrict__ ckl,
+             const CkRec *__restrict__ ckh, const SegVal *__restrict__ zero,
+             SplitRec *__restrict__ recs) {
+    const uint32_t sec = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (sec >= ctr[1]) return;
+    const uint32_t t = sec_tab[sec];
+    const BatchTab tb = tabs[t];
+    const uint32_t j = sec - tb.sec0;
+    if (j == 0) return;
+    const BuildParams Pm = tp[t];
+    if (Pm.status) return;
+    const SplitCtx C = bseg_ctx(Pm, tb, t, lh, ckl, ckh, zero);
+    const uint64_t k = (uint64_t)j * kBSeg;
+    uint64_t a, b;
+    crange(C, k, a, b);   // the answer c lies in [a, b]; P(b) holds
+    while (a < b) {
+        const uint64_t step = (b - a + 31) / 32;
+        const uint64_t p = a + (uint64_t)lane * step;
+        const uint32_t bal = __ballot_sync(0xffffffffu, p < b && pred_c(C, k, p));
+        if (bal) {
+            const uint32_t f = __ffs(bal) - 1;   // P false before a + f step, true there
+            b = a + f * step;
+            if (f) a = a + (f - 1) * step + 1;
+        } else {
+            const uint64_t last = min((uint64_t)31, (b - 1 - a) / step);
+            a = a + last * step + 1;
+        }
+    }
+    u128 Dbase, Ebase;
+    if (a > 0) {
+        Dbase = ck_D(C, a - 1);
+        Ebase = ck_E(C, (k - 32 * a) >> 5);
+    } else {
+        Dbase = 0;
+        Ebase = ck_E(C, k >> 5);
+    }
+    split_fine(C, Pm, k, a, Dbase, Ebase, recs + tb.rec0 + j, lane);
+}
+
+// Pack of every table's sections: one CTA of kBSeg / 8 threads per section,
+// the single-table pack on the table's lists, parameters and splits; rows
+// by table-local item index.
+__global__ void __maxnreg__(48)
+k_bseg_pack(const uint32_t *__restrict__ ctr, const uint32_t *__restrict__ sec_tab,
+            const BatchTab *__restrict__ tabs, BuildParams *__restrict__ tp,
+            const Entry *__restrict__ lh, const SplitRec *__restrict__ recs,
+            uint2 *__restrict__ rows, uint2 *const *__restrict__ row_ptrs) {
+    const uint32_t sec = blockIdx.x;
+    if (sec >= ctr[1]) return;
+    const uint32_t t = sec_tab[sec];
+    const BatchTab tb = tabs[t];
+    uint2 *rt = row_ptrs ? row_ptrs[t] : rows + tb.base;
+    pack_section<8>(tp + t, lh + tb.base, recs + tb.rec0, rt, tp[t].n, kBSeg, sec - tb.sec0);
+}
+
+// A table whose split or pack found an inconsistency reports it.
+__global__ void k_bseg_info(const BuildParams *__restrict__ tp, uint32_t ntab,
+                            wrs_table_summary *__restrict__ info) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < ntab && (tp[t].status & ERR_INTERNAL)) info[t].status = WRS_EINVAL;
+}
+
+cudaError_t launch_bseg_split_pack(unsigned char *ws, const BatchSegLayout &L, uint32_t ntab,
+                                   wrs_row *d_rows, wrs_row *const *d_row_ptrs,
+                                   wrs_table_summary *d_info, cudaStream_t st) {
+    const uint32_t smem = pack_smem_bytes(kBSeg);
+    cudaError_t e = ensure_dynamic_smem<k_bseg_pack>(smem);
+    if (e) return e;
+    auto *ctr = reinterpret_cast<const uint32_t *>(ws + L.counters);
+    auto *sec_tab = reinterpret_cast<const uint32_t *>(ws + L.sec_tab);
+    auto *tabs = reinterpret_cast<const BatchTab *>(ws + L.tabs);
+    auto *tp = reinterpret_cast<BuildParams *>(ws + L.tp);
+    auto *lh = reinterpret_cast<const Entry *>(ws + L.lh);
+    auto *ckl = reinterpret_cast<const CkRec *>(ws + L.ckl);
+    auto *ckh = reinterpret_cast<const CkRec *>(ws + L.ckh);
+    auto *zero = reinterpret_cast<const SegVal *>(ws + L.zero);
+    auto *recs = reinterpret_cast<SplitRec *>(ws + L.recs);
+    const uint64_t maxsec = L.cap / kBSeg + ntab;   // an upper bound of the sections
+    if (maxsec >= (1ull << 31)) return cudaErrorInvalidValue;
+    k_bseg_split<<<(unsigned)((maxsec + 7) / 8), 256, 0, st>>>(ctr, sec_tab, tabs, tp, lh, ckl, ckh,
+                                                              zero, recs);
+    k_bseg_pack<<<(unsigned)maxsec, kBSeg / 8, smem, st>>>(
+        ctr, sec_tab, tabs, tp, lh, recs, reinterpret_cast<uint2 *>(d_rows),
+        reinterpret_cast<uint2 *const *>(d_row_ptrs));
+    k_bseg_info<<<(ntab + 255) / 256, 256, 0, st>>>(tp, ntab, d_info);
+    return cudaGetLastError();
 }
 
 // ===========================================================================

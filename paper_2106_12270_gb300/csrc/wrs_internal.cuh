@@ -101,6 +101,37 @@ struct __align__(16) SplitRec {  // Vose state after k_t buckets
     u128 E;       // E'(j)
 };
 
+// Segmented batched build: each table of a batch is built by the single-
+// table split and pack kernels over its own sections (of kBSeg buckets).
+// The partition kernel leaves, per table, a BuildParams record, its place in
+// the batch and its first section and split record.
+constexpr uint32_t kBSeg = 1024;
+struct __align__(16) BatchTab {
+    uint64_t base;   // first item of the table in the batch
+    uint32_t sec0;   // first section
+    uint32_t rec0;   // first split record (sections + 1 per table)
+};
+// Workspace of the segmented batched build for up to `cap` items and ntab
+// tables (all offsets 256-byte aligned); the counters and lh sit where the
+// chunked kernel expects its counter and lh.
+struct BatchSegLayout {
+    uint64_t counters;   // [0] tables taken, [1] sections, [2] split records
+    uint64_t lh;         // cap Entry
+    uint64_t tp;         // ntab BuildParams
+    uint64_t tabs;       // ntab BatchTab
+    uint64_t sec_tab;    // cap / kBSeg + ntab + 1 uint32: table of each section
+    uint64_t ckl, ckh;   // (cap >> 5) + 2 ntab + 2 CkRec each
+    uint64_t recs;       // cap / kBSeg + 2 ntab + 1 SplitRec
+    uint64_t zero;       // one zero SegVal (the checkpoints' segment prefix)
+    uint64_t total;
+    uint64_t cap;
+};
+BatchSegLayout batch_seg_layout(uint64_t cap, uint32_t ntab);
+// Checkpoint index of checkpoint c of the table at `base` (table t).
+__host__ __device__ inline uint64_t bseg_ck(uint64_t base, uint32_t t, uint64_t c) {
+    return (base >> 5) + 2ull * t + c;
+}
+
 // One sampling request of the request loop (device-resident descriptor).
 struct __align__(16) SampleReq {
     const wrs_row *rows;
@@ -148,13 +179,21 @@ inline cudaError_t ensure_dynamic_smem(uint32_t bytes) {
 
 Layout make_layout(uint64_t n, uint32_t section_size);
 
-// Batched build (wrs_batched.cu); tune == nullptr is the default tiling.
+// Batched build, chunked kernel (wrs_batched.cu); tune == nullptr is its
+// default tiling (256 threads, chunks of 1024).
 bool batch_tuning_valid(const wrs_batch_tuning &t);
 cudaError_t launch_build_batched(const float *d_w, const uint64_t *d_off, uint32_t ntab,
                                  const uint32_t *d_order, uint32_t *d_counter, Entry *d_lh,
                                  wrs_row *d_rows, wrs_row *const *d_row_ptrs,
                                  wrs_table_summary *d_info, const wrs_batch_tuning *tune,
                                  cudaStream_t st);
+// The segmented batched build (wrs_batched.cu, wrs_build.cu) in a workspace
+// laid out by batch_seg_layout.
+cudaError_t launch_build_batched_seg(const float *d_w, const uint64_t *d_off, uint32_t ntab,
+                                     const uint32_t *d_order, unsigned char *ws,
+                                     const BatchSegLayout &L, wrs_row *d_rows,
+                                     wrs_row *const *d_row_ptrs, wrs_table_summary *d_info,
+                                     cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Small device helpers

@@ -119,8 +119,8 @@ TILINGS = [(t, c) for t in (256, 512) for c in (512, 1024, 2048, 4096)]
 
 @pytest.mark.parametrize("threads,chunk", TILINGS)
 def test_every_tiling_builds_the_same_tables(batch, threads, chunk):
-    """The tiling only changes the time: rows and summaries are bit-identical
-    to the default tiling's."""
+    """The tiling only changes the time: rows and summaries of the chunked
+    kernel are bit-identical to the default (segmented) build's."""
     w, off, rows, summ, off_t = batch
     wt = torch.from_numpy(np.ascontiguousarray(w, np.float32)).cuda()
     rows2 = torch.zeros_like(rows)
@@ -136,7 +136,7 @@ def test_invalid_tiling_rejected(batch):
     w, off, rows, summ, off_t = batch
     wt = torch.from_numpy(np.ascontiguousarray(w, np.float32)).cuda()
     bb = wrs.BatchBuilder(int(off[-1]), off.size - 1)
-    for bad in ((128, 1024), (256, 8192), (300, 1024)):
+    for bad in ((128, 1024), (256, 8192), (300, 1024), (0, 1024)):
         bb.tuning = wrs.BatchTuning(bad[0], bad[1], 0, 0.0)
         with pytest.raises(wrs.WrsError):
             bb.build(wt, off_t, torch.zeros_like(rows), None)
@@ -148,8 +148,9 @@ def test_autotune_picks_a_candidate_and_caches_it(batch):
     rows2 = torch.zeros_like(rows)
     bb = wrs.BatchBuilder(int(off[-1]), off.size - 1)
     best, cand = bb.autotune(wt, off_t, rows2, None, force=True)
-    assert len(cand) == len(TILINGS)
-    assert {(c["threads"], c["chunk"]) for c in cand} == set(TILINGS)
+    # the segmented build (threads 0) and every tiling of the chunked kernel
+    assert len(cand) == len(TILINGS) + 1
+    assert {(c["threads"], c["chunk"]) for c in cand} == set(TILINGS) | {(0, 0)}
     assert all(c["ms"] > 0 for c in cand)
     assert best["ms"] == min(c["ms"] for c in cand)
     assert torch.equal(rows, rows2)            # the buffers hold a valid build
@@ -234,3 +235,45 @@ def test_batched_window_edges_equal_single_builds(threads, chunk):
         prob, alias = table_rows(rows, off, t)
         assert np.array_equal(prob.view(np.uint32), b.prob.view(np.uint32)), t
         assert np.array_equal(alias, b.alias), t
+
+
+@pytest.mark.parametrize("sizes", [[1 << 20 | 7, 1024, 1025, 2048, 3, 300001, 65536],
+                                   [5000] * 40 + [1 << 18]])
+def test_segmented_build_equals_single_builds(sizes):
+    """The segmented build (each table's lists and checkpoints by one CTA,
+    then the single-table split and pack over every table's sections of 1024
+    buckets): every table bit-identical to the single-table build of its
+    weights, with tables of one and of many sections, ragged and exact."""
+    sizes = np.asarray(sizes, np.int64)
+    w, off = inputs.batched(sizes, 23, "exponential")
+    rows, summ, _ = build_batch(w, off)
+    for t in range(sizes.size):
+        wt = w[off[t]: off[t + 1]]
+        b = Built(wt)
+        assert summ[t]["status"] == wrs.OK
+        assert (summ[t]["W"], summ[t]["nl"], summ[t]["nh"]) == \
+            (b.info["W"], b.info["nl"], b.info["nh"])
+        prob, alias = table_rows(rows, off, t)
+        assert np.array_equal(prob.view(np.uint32), b.prob.view(np.uint32)), t
+        assert np.array_equal(alias, b.alias), t
+
+
+def test_segmented_build_workspace_too_small():
+    """A workspace laid out for fewer items than the batch holds: the tables
+    that do not fit report WRS_EINVAL, the others are built."""
+    sizes = np.asarray([40000, 30000, 20000, 10000], np.int64)
+    w, off = inputs.batched(sizes, 29, "uniform")
+    wt = torch.from_numpy(w).cuda()
+    off_t = torch.from_numpy(off.astype(np.int64)).cuda()
+    rows = torch.zeros(int(off[-1]), dtype=torch.int64, device="cuda")
+    bb = wrs.BatchBuilder(70000, sizes.size)   # room for the first two tables
+    bb.build(wt, off_t, rows, None)
+    torch.cuda.synchronize()
+    summ = bb.summaries()
+    assert summ["status"].tolist()[:2] == [wrs.OK, wrs.OK]
+    assert summ["status"].tolist()[2:] == [wrs.EINVAL, wrs.EINVAL]
+    for t in range(2):
+        b = Built(w[off[t]: off[t + 1]])
+        prob, alias = table_rows(rows, off, t)
+        assert np.array_equal(prob.view(np.uint32), b.prob.view(np.uint32))
+        assert np.array_equal(alias, b.alias)
