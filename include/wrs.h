@@ -341,10 +341,11 @@ int wrs_batch_order(const uint64_t *h_off, uint32_t ntab, uint32_t *h_order);
 /* a8: build ntab tables with one launch sequence.  Table t has the weights
  * d_w[d_off[t] .. d_off[t+1]) and gets the rows d_rows[d_off[t] ..
  * d_off[t+1]) with table-local alias indices (PSA per table, Sec. 2.2 and
- * Sec. 4).  The default (segmented) build: one persistent CTA per table
- * computes its exact total, Q and stable partition with the prefix-sum
- * checkpoints; then the single-table split and pack run over the sections
- * (1024 buckets) of every table at once.  d_off: ntab+1 device uint64
+ * Sec. 4).  The default (segmented) build: a warp per table (a whole CTA
+ * for a table of more than half a warp's share of the batch's items and
+ * more than 8192 items) computes its exact total, Q and stable partition
+ * with the prefix-sum checkpoints; then the single-table split and pack
+ * run over the sections (1024 buckets) of every table at once.  d_off: ntab+1 device uint64
  * offsets, non-decreasing, d_off[0] = 0; d_order: ntab device table ids (a
  * permutation, e.g. from wrs_batch_order) or NULL for 0..ntab-1; d_info:
  * ntab device summaries.  A table with an error gets a status in its

@@ -18,6 +18,7 @@
 // a9, batched sampling: one CTA per table draws that table's samples with
 // Walker's rule, counters keyed by the table id.
 #include "wrs_device.cuh"
+#include "wrs_scatter.cuh"
 
 namespace wrs {
 
@@ -624,9 +625,10 @@ static cudaError_t launch_bb(const float *d_w, const uint64_t *d_off, uint32_t n
 
 
 // ---------------------------------------------------------------------------
-// Segmented batched build, first kernel.  A CTA takes the next table (work
-// counter, largest first) and runs the exact total, Q, and the stable
-// partition into the table's lh region as the chunked kernel does, and in
+// Segmented batched build, partition of the large tables (k_bseg_lists).  A
+// CTA takes the next one (work counter, in list order) and runs the exact
+// total, Q, and the stable partition into the table's lh region as the
+// chunked kernel does, and in
 // the same pass the clamped q prefix sums of both lists at every 32nd entry
 // (the checkpoints of the single-table build, table-local).  It then leaves
 // the table's BuildParams (W, the scale, Q, nl, nh, D'(nl), E'(nh)), takes
@@ -673,8 +675,9 @@ k_bseg_part(const float *__restrict__ w, const uint64_t *__restrict__ off,
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (;;) {
         if (tid == 0) {
-            uint32_t k = atomicAdd(ctr, 1u);
-            sm.table = k < ntab ? (order ? order[k] : k) : 0xffffffffu;
+            // the large tables, in the order of the list (k_bseg_lists)
+            const uint32_t k = atomicAdd(ctr, 1u);
+            sm.table = k < ctr[4] ? order[k] : 0xffffffffu;
         }
         __syncthreads();
         const uint32_t t = sm.table;
@@ -953,11 +956,260 @@ k_bseg_part(const float *__restrict__ w, const uint64_t *__restrict__ off,
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Which tables of a segmented batch a whole CTA partitions and which a single
+// warp does.  A warp takes a table when it holds at most T items, T the
+// larger of kWarpTableMin and half of a warp's share of all the items (so
+// that no warp gets much more than its share), capped at kWarpTableMax (a
+// lane's exact-sum bins hold at most 2^17 values below 2^47); the rest, and
+// the empty or invalid tables, go to the CTA kernel.  One CTA splits the
+// table order (d_order or 0..ntab-1) into the two lists, each in that order.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kWarpTableMax = 1ull << 22;
+constexpr uint64_t kWarpTableMin = 8192;
+constexpr int kBsegWarpCtas = 3;   // CTAs of 8 warps per SM of the warp kernel
+
+__device__ __forceinline__ bool bseg_small(uint64_t n, uint64_t T) { return n >= 1 && n <= T; }
+
+__device__ __forceinline__ uint64_t bseg_warp_limit(const uint64_t *off, uint32_t ntab,
+                                                    uint32_t nwarps) {
+    const uint64_t share = off[ntab] / (2ull * nwarps);
+    return min(kWarpTableMax, max(kWarpTableMin, share));
+}
+
+__global__ void __launch_bounds__(1024)
+k_bseg_lists(const uint64_t *__restrict__ off, const uint32_t *__restrict__ order, uint32_t ntab,
+             uint32_t nwarps, uint32_t *__restrict__ lists, uint32_t *__restrict__ ctr) {
+    __shared__ uint32_t wsum[32];
+    const uint64_t T = bseg_warp_limit(off, ntab, nwarps);
+    const uint32_t per = (ntab + 1023) / 1024;
+    const uint32_t k0 = min(threadIdx.x * per, ntab), k1 = min(k0 + per, ntab);
+    auto tab = [&](uint32_t k) { return order ? order[k] : k; };
+    uint32_t small = 0;
+    for (uint32_t k = k0; k < k1; ++k) {
+        const uint32_t t = tab(k);
+        small += bseg_small(off[t + 1] - off[t], T);
+    }
+    // exclusive scan of the small counts (the large ones follow: k - small)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = small;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += o;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t pre = inc - small, all = 0;
+    for (int k = 0; k < 32; ++k) {
+        pre += k < warp ? wsum[k] : 0u;
+        all += wsum[k];
+    }
+    uint32_t ps = pre, pl = k0 - pre;   // next slots in the small and large lists
+    uint32_t *big = lists, *sml = lists + ntab;
+    for (uint32_t k = k0; k < k1; ++k) {
+        const uint32_t t = tab(k);
+        if (bseg_small(off[t + 1] - off[t], T)) sml[ps++] = t;
+        else big[pl++] = t;
+    }
+    if (threadIdx.x == 0) {
+        ctr[4] = ntab - all;
+        ctr[5] = all;
+    }
+}
+
+// The small tables: each warp takes the next one (ctr[3]) and runs its whole
+// partition alone -- exact total, Q and the light count, and the placement
+// with checkpoints (scatter_range over the table) -- then leaves the same
+// per-table records as the CTA kernel.  No CTA barrier.
+__global__ void __launch_bounds__(256, kBsegWarpCtas)
+k_bseg_warp(const float *__restrict__ w, const uint64_t *__restrict__ off,
+            const uint32_t *__restrict__ lists, uint32_t ntab, uint32_t *__restrict__ ctr,
+            uint64_t cap, Entry *__restrict__ lh, BuildParams *__restrict__ tp,
+            BatchTab *__restrict__ tabs, uint32_t *__restrict__ sec_tab, CkRec *__restrict__ ckl,
+            CkRec *__restrict__ ckh, SplitRec *__restrict__ recs,
+            wrs_table_summary *__restrict__ info) {
+    __shared__ WarpStage stage[8];
+    __shared__ u128 sband[8][kBands];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpStage &sm = stage[warp];
+    // a lane's exact-sum bins (band b at bins[32 b + lane]) share the
+    // staging memory, which the placement uses only after the total
+    uint64_t *bins = reinterpret_cast<uint64_t *>(&sm);
+    static_assert(sizeof(WarpStage) >= kBands * 32 * sizeof(uint64_t), "bins fit the stage");
+    const uint32_t nsmall = ctr[5];
+    const uint32_t *sml = lists + ntab;
+    for (;;) {
+        uint32_t k = 0;
+        if (lane == 0) k = atomicAdd(ctr + 3, 1u);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= nsmall) return;
+        const uint32_t t = sml[k];
+        const uint64_t base = off[t], n = off[t + 1] - base;
+        const float *wt = w + base;
+        auto fail = [&](uint32_t st, int status) {
+            if (lane == 0) {
+                BuildParams z;
+                memset(&z, 0, sizeof z);
+                z.status = st;
+                z.n = n;
+                tp[t] = z;
+                tabs[t] = BatchTab{base, 0u, 0u};
+                wrs_table_summary r;
+                r.status = status; r.n = (uint32_t)n; r.W = 0.0; r.nl = r.nh = 0;
+                info[t] = r;
+            }
+        };
+        if (base + n > cap) {
+            fail(ERR_INTERNAL, WRS_EINVAL);
+            continue;
+        }
+        // ---- exact total
+#pragma unroll
+        for (int b = 0; b < kBands; ++b) bins[32 * b + lane] = 0;
+        uint32_t bad = 0;
+        auto add_bin = [&](float x) {
+            uint32_t band;
+            uint64_t val;
+            band_of(x, band, val, bad);
+            bins[32 * band + lane] += val;
+        };
+        {
+            // eight loads in flight per lane: one warp alone streams the table
+            uint64_t a = lane;
+            for (; a + 7 * 32 < n; a += 8 * 32) {
+                float x[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) x[r] = __ldg(wt + a + 32 * r);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) add_bin(x[r]);
+            }
+            for (; a < n; a += 32) add_bin(__ldg(wt + a));
+        }
+        bad = __reduce_or_sync(0xffffffffu, bad);
+        __syncwarp();
+        if (lane < kBands) {
+            u128 s = 0;
+            for (int k2 = 0; k2 < 32; ++k2) s += bins[32 * lane + k2];
+            sband[warp][lane] = s;
+        }
+        __syncwarp();
+        double W = 0.0;
+        int top = -1;
+        uint32_t st = bad;
+        if (lane == 0 && !st && !exact_total(sband[warp], W, top)) st |= ERR_ZEROSUM;
+        st = __shfl_sync(0xffffffffu, st, 0);
+        if (st) {
+            fail(st, (st & ERR_NONFINITE) ? WRS_ENONFINITE
+                     : (st & ERR_NEGATIVE) ? WRS_EINVAL : WRS_EZEROSUM);
+            __syncwarp();
+            continue;
+        }
+        W = __shfl_sync(0xffffffffu, W, 0);
+        top = __shfl_sync(0xffffffffu, top, 0);
+        const double avg = W / (double)n;
+        const int qshift = 61 - top;
+        const QScale qsc = qscale(qshift);
+        const float lmax = __double2float_rd(avg);
+        // ---- Q = sum of q over the table, and the light count
+        uint64_t Q = 0;
+        uint32_t c = 0;
+        {
+            uint64_t a = lane;
+            for (; a + 7 * 32 < n; a += 8 * 32) {
+                float x[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) x[r] = __ldg(wt + a + 32 * r);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    Q += fixed_q(x[r], qsc);
+                    c += x[r] <= lmax;
+                }
+            }
+            for (; a < n; a += 32) {
+                const float x = __ldg(wt + a);
+                Q += fixed_q(x, qsc);
+                c += x <= lmax;
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            Q += __shfl_xor_sync(0xffffffffu, Q, d);
+            c += __shfl_xor_sync(0xffffffffu, c, d);
+        }
+        const uint64_t nl = c, nh = n - nl, Qn = Q / n;
+        const uint64_t ckb = bseg_ck(base, t, 0);
+        // ---- stable partition with the prefix checkpoints
+        ScatterCtx X;
+        X.w = wt;
+        X.n = n;
+        X.lh = lh + base;
+        X.ckl = ckl + ckb;
+        X.ckh = ckh + ckb;
+        X.qsc = qsc;
+        X.Qn = Qn;
+        X.lmax = lmax;
+        threshold_interval(ldexp((double)Qn + 0.5, -(211 - top)), (double)lmax, X.tmid, X.thalf);
+        __syncwarp();   // the bins are done with; the stage is reused
+        uint64_t SL, SH;
+        scatter_range<false>(X, sm, 0u, 0, n, 0, SL, SH);
+        // ---- the table's parameters, sections and end splits
+        const uint32_t ns = (uint32_t)((n + kBSeg - 1) / kBSeg);
+        const u128 Dtot = (u128)nl * Q - (u128)SL * n;
+        const u128 Etot = (u128)SH * n - (u128)nh * Q;
+        uint32_t sec0 = 0, rec0 = 0;
+        if (lane == 0) {
+            sec0 = atomicAdd(ctr + 1, ns);
+            rec0 = atomicAdd(ctr + 2, ns + 1);
+            BuildParams p;
+            memset(&p, 0, sizeof p);
+            p.Dtot = Dtot;
+            p.Etot = Etot;
+            p.W = W;
+            p.avg = avg;
+            p.Q = Q;
+            p.Qn = Qn;
+            p.n = n;
+            p.nl = nl;
+            p.nh = nh;
+            p.scale = 211 - top;
+            p.qshift = qshift;
+            p.light_max = lmax;
+            p.inv_avg = __double2float_rn(1.0 / avg);
+            p.Qf = __ull2float_rn(Q);
+            p.invQ = __frcp_rn(p.Qf);
+            p.sections = ns;
+            tp[t] = p;
+            if ((nl & 31u) == 0) put_ck(ckl, ckb + (nl >> 5), 0u, SL);
+            if ((nh & 31u) == 0) put_ck(ckh, ckb + (nh >> 5), 0u, SH);
+            wrs_table_summary r;
+            r.status = WRS_OK;
+            r.n = (uint32_t)n;
+            r.W = W;
+            r.nl = nl;
+            r.nh = nh;
+            info[t] = r;
+            tabs[t] = BatchTab{base, sec0, rec0};
+            SplitRec r0, rs;
+            r0.i = r0.j = 0; r0.pad[0] = r0.pad[1] = 0; r0.D = 0; r0.E = 0;
+            rs.i = (uint32_t)nl; rs.j = (uint32_t)nh; rs.pad[0] = rs.pad[1] = 0;
+            rs.D = Dtot; rs.E = Etot;
+            recs[rec0] = r0;
+            recs[rec0 + ns] = rs;
+        }
+        sec0 = __shfl_sync(0xffffffffu, sec0, 0);
+        for (uint32_t j = lane; j < ns; j += 32) sec_tab[sec0 + j] = t;
+        __syncwarp();
+    }
+}
+
 cudaError_t launch_bseg_split_pack(unsigned char *ws, const BatchSegLayout &L, uint32_t ntab,
                                    wrs_row *d_rows, wrs_row *const *d_row_ptrs,
                                    wrs_table_summary *d_info, cudaStream_t st);
 
-// The segmented batched build: partition (one persistent CTA per table),
+// The segmented batched build: the tables split into large and small ones,
+// the partition (a persistent CTA per large table, a warp per small one),
 // then the single-table split and pack over every table's sections.
 cudaError_t launch_build_batched_seg(const float *d_w, const uint64_t *d_off, uint32_t ntab,
                                      const uint32_t *d_order, unsigned char *ws,
@@ -981,16 +1233,26 @@ cudaError_t launch_build_batched_seg(const float *d_w, const uint64_t *d_off, ui
         resident[slot].store(per_sm, std::memory_order_relaxed);
     }
     auto *ctr = reinterpret_cast<uint32_t *>(ws + L.counters);
-    e = cudaMemsetAsync(ctr, 0, 3 * sizeof(uint32_t), st);
+    auto *lists = reinterpret_cast<uint32_t *>(ws + L.lists);
+    e = cudaMemsetAsync(ctr, 0, 6 * sizeof(uint32_t), st);
     if (!e) e = cudaMemsetAsync(ws + L.zero, 0, sizeof(SegVal), st);
     if (e) return e;
+    const unsigned wblocks = (unsigned)num_sms() * kBsegWarpCtas;
+    k_bseg_lists<<<1, 1024, 0, st>>>(d_off, d_order, ntab, wblocks * 8, lists, ctr);
     unsigned blocks = (unsigned)num_sms() * (unsigned)per_sm;
     if (blocks > ntab) blocks = ntab ? ntab : 1;
-    k_bseg_part<BT><<<blocks, BT, smem, st>>>(
-        d_w, d_off, d_order, ntab, ctr, L.cap, reinterpret_cast<Entry *>(ws + L.lh),
-        reinterpret_cast<BuildParams *>(ws + L.tp), reinterpret_cast<BatchTab *>(ws + L.tabs),
-        reinterpret_cast<uint32_t *>(ws + L.sec_tab), reinterpret_cast<CkRec *>(ws + L.ckl),
-        reinterpret_cast<CkRec *>(ws + L.ckh), reinterpret_cast<SplitRec *>(ws + L.recs), d_info);
+    auto *lh = reinterpret_cast<Entry *>(ws + L.lh);
+    auto *tp = reinterpret_cast<BuildParams *>(ws + L.tp);
+    auto *tabs = reinterpret_cast<BatchTab *>(ws + L.tabs);
+    auto *sec_tab = reinterpret_cast<uint32_t *>(ws + L.sec_tab);
+    auto *ckl = reinterpret_cast<CkRec *>(ws + L.ckl);
+    auto *ckh = reinterpret_cast<CkRec *>(ws + L.ckh);
+    auto *recs = reinterpret_cast<SplitRec *>(ws + L.recs);
+    // the large tables (a CTA each), then the small ones (a warp each)
+    k_bseg_part<BT><<<blocks, BT, smem, st>>>(d_w, d_off, lists, ntab, ctr, L.cap, lh, tp, tabs,
+                                              sec_tab, ckl, ckh, recs, d_info);
+    k_bseg_warp<<<wblocks, 256, 0, st>>>(d_w, d_off, lists, ntab, ctr, L.cap, lh, tp, tabs, sec_tab,
+                                         ckl, ckh, recs, d_info);
     e = cudaGetLastError();
     if (e) return e;
     return launch_bseg_split_pack(ws, L, ntab, d_rows, d_row_ptrs, d_info, st);

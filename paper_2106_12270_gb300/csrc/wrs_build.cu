@@ -45,6 +45,7 @@
 #include <type_traits>
 
 #include "wrs_device.cuh"
+#include "wrs_scatter.cuh"
 
 
 namespace wrs {
@@ -304,47 +305,18 @@ k_qsum(BuildParams *__restrict__ P, const uint32_t *__restrict__ seg_cnt,
         // Clamps: a light (w <= lmax) changes only if q > Qn, i.e. w >= wq
         // with wq the least weight of q >= Qn + 1, about (Qn + 1/2) 2^-S;
         // a heavy only if w < wq.  Both lie between lmax and wq; the
-        // interval below covers that range with a relative margin of 2^-16
-        // (far above the FP64 and FP32 rounding of its ends).
-        const double wq = ldexp((double)Qn + 0.5, -P->scale);
-        const double lm = (double)P->light_max;
-        const double lo = fmin(wq, lm) * (1.0 - 0x1p-16);
-        const double hi = fmax(wq, lm) * (1.0 + 0x1p-16);
-        float mid = (float)(0.5 * (lo + hi)), half = (float)(0.5 * (hi - lo) * (1.0 + 0x1p-10));
-        if (!(lm > 0.0) || !(half > 0.0f) || !(half < INFINITY)) {
-            mid = 0.0f;
-            half = INFINITY;   // no usable interval: every chunk takes the exact clamps
-        }
+        // interval covers that range (threshold_interval).
+        float mid, half;
+        threshold_interval(ldexp((double)Qn + 0.5, -P->scale), (double)P->light_max, mid, half);
         P->tmid = mid;
         P->thalf = half;
     }
     (void)qe;
 }
 
-__device__ __forceinline__ void put_ck(CkRec *ck, uint64_t idx, uint32_t seg, uint64_t v) {
-    uint4 r = make_uint4(seg, 0u, (uint32_t)v, (uint32_t)(v >> 32));
-    *reinterpret_cast<uint4 *>(ck + idx) = r;
-}
-
-struct WarpStage {
-    float wv[kChunk + kChunk / 32];     // staged weights (padded, conflict-free)
-    Entry e[kChunk + kChunk / 16];      // staged entries in list order (padded)
-};
-
-// Place every item: lights at l[rank] (entry rank), heavies at h[rank]
-// (entry n-1-rank); both stay in index order.  Every 32nd list entry gets a
-// checkpoint of the q sum before it, relative to its sub-segment.
-//
-// Each warp works alone on its sub-segment, chunk by chunk (no CTA barrier):
-// classify in input order (lane = 16 consecutive items), rank with a warp
-// count scan, stage the chunk's entries in list order in the warp's shared
-// memory, then compute q once per entry in list order (lane = 16
-// consecutive slots) with one warp scan; checkpoint sums are snapshots of
-// the running sum at the one slot per lane where a checkpoint can fall.  The
-// next chunk's weights are loaded while the current one is processed.  Full
-// chunks (every chunk but a sub-segment's last) skip the per-item bounds
-// tests, and those without a weight near the light threshold skip the
-// clamps of q.
+// Place every item (scatter_range, wrs_scatter.cuh): each warp works alone
+// on its sub-segment, whose light offset the count pass found; checkpoints
+// are relative to the sub-segment (its prefix comes from the segment scan).
 template <bool kAligned>
 __global__ void __launch_bounds__(kPartThreads, 3)
 k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__ P,
@@ -355,174 +327,25 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
     const int lane = threadIdx.x & 31;
     const uint32_t s = blockIdx.x * (kPartThreads / 32) + (threadIdx.x >> 5);
     if (s >= NS) return;
-    WarpStage &sm = stage[threadIdx.x >> 5];
-    const QScale qsc = qscale(P->qshift);
-    const uint64_t Qn = P->Qn;
-    const float lmax = P->light_max;
-    const float tmid = P->tmid, thalf = P->thalf;
+    ScatterCtx X;
+    X.w = w;
+    X.n = n;
+    X.lh = lh;
+    X.ckl = ckl;
+    X.ckh = ckh;
+    X.qsc = qscale(P->qshift);
+    X.Qn = P->Qn;
+    X.lmax = P->light_max;
+    X.tmid = P->tmid;
+    X.thalf = P->thalf;
     uint64_t a, b;
     sub_range(s, NS, C, n, a, b);
-    uint64_t run_l = seg_loff[s];       // global rank of the next light
-    uint64_t run_h = a - run_l;         // global rank of the next heavy
-    uint64_t run_sl = 0, run_sh = 0;    // sub-segment-local q sums so far
-    const int e0 = lane * kPartItems;   // this lane's first item of the chunk
-    const int s0 = lane * kPartItems;   // this lane's first list slot
-    float4 pv[4];
-    auto load_chunk = [&](uint64_t base) {
-        const uint64_t lim = n - base;
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            int e = r * 128 + lane * 4;
-            if (kAligned && (uint64_t)e + 3 < lim) {
-                pv[r] = __ldcs(reinterpret_cast<const float4 *>(w + base + e));
-            } else {
-                pv[r].x = (uint64_t)e + 0 < lim ? w[base + e + 0] : 0.f;
-                pv[r].y = (uint64_t)e + 1 < lim ? w[base + e + 1] : 0.f;
-                pv[r].z = (uint64_t)e + 2 < lim ? w[base + e + 2] : 0.f;
-                pv[r].w = (uint64_t)e + 3 < lim ? w[base + e + 3] : 0.f;
-            }
-        }
-    };
-    if (a < b) load_chunk(a);
-    for (uint64_t base = a; base < b; base += kChunk) {
-        const uint64_t lim = b - base;   // items e of the chunk are valid for e < lim
-        __syncwarp();                    // previous chunk fully consumed
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            int e = r * 128 + lane * 4;
-            sm.wv[pad32(e + 0)] = pv[r].x;
-            sm.wv[pad32(e + 1)] = pv[r].y;
-            sm.wv[pad32(e + 2)] = pv[r].z;
-            sm.wv[pad32(e + 3)] = pv[r].w;
-        }
-        if (base + kChunk < b) load_chunk(base + kChunk);
-        __syncwarp();
-        // ---- classify (input order) and count
-        const bool full = lim >= (uint64_t)kChunk;   // every chunk but a sub-segment's last
-        uint32_t lmask = 0, vmask = 0;
-        if (full) {
-            vmask = (1u << kPartItems) - 1u;
-#pragma unroll
-            for (int k = 0; k < kPartItems; ++k)
-                lmask |= (uint32_t)(sm.wv[pad32(e0 + k)] <= lmax) << k;
-        } else {
-#pragma unroll
-            for (int k = 0; k < kPartItems; ++k) {
-                float x = sm.wv[pad32(e0 + k)];
-                bool valid = (uint64_t)(e0 + k) < lim;
-                vmask |= (uint32_t)valid << k;
-                lmask |= (uint32_t)(valid && x <= lmax) << k;
-            }
-        }
-        const uint32_t cnt = __popc(lmask);
-        uint32_t icnt = cnt;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            uint32_t c2 = __shfl_up_sync(0xffffffffu, icnt, d);
-            if (lane >= d) icnt += c2;
-        }
-        const uint32_t tl = __shfl_sync(0xffffffffu, icnt, 31);       // lights of the chunk
-        const uint32_t tv = lim < (uint64_t)kChunk ? (uint32_t)lim : (uint32_t)kChunk;
-        const uint32_t tnh = tv - tl;
-        // ---- stage entries in list order: lights at slot rank, heavies at
-        // slot kChunk-1-rank
-        {
-            uint32_t lrank = icnt - cnt;
-            uint32_t hslot = kChunk - 1 - ((uint32_t)e0 - lrank);
-#pragma unroll
-            for (int k = 0; k < kPartItems; ++k) {
-                const bool lt = (lmask >> k) & 1u;
-                const uint32_t slot = lt ? lrank : hslot;
-                if (full || ((vmask >> k) & 1u))
-                    sm.e[pad16(slot)] = Entry{(uint32_t)(base + e0 + k), sm.wv[pad32(e0 + k)]};
-                lrank += lt;
-                hslot -= !lt;
-            }
-        }
-        __syncwarp();
-        // ---- list-order q pass: slots [s0, s0+16) of this lane
-        const uint32_t hstart = kChunk - tnh;   // first heavy slot
-        const int cl = (int)((32u - (uint32_t)(run_l & 31u)) & 31u);   // light ckpt slots = cl mod 32
-        const int ch = (int)((uint32_t)(run_h + kChunk - 1) & 31u);  // heavy ckpt slots = ch mod 32
-        const int kl = (cl - s0) & 31;
-        const int kh = (ch - s0) & 31;
-        const int kb = (int)tl - s0;
-        const uint64_t Qn1 = Qn + 1;
-        uint64_t acc = 0, snap_l = 0, snap_h = 0, snap_b = 0;
-        // A full chunk with no weight near the light threshold needs no
-        // clamp (its lights have q <= Qn, its heavies q > Qn): sum q as is.
-        // Otherwise (a partial chunk, or a weight in the threshold
-        // interval) the pass applies the clamps.
-        bool exact = tv < (uint32_t)kChunk;
-        if (!exact) {
-            float dmin = INFINITY;
-#pragma unroll
-            for (int k = 0; k < kPartItems; ++k) {
-                if (k == kl) snap_l = acc;
-                if (k == kb) snap_b = acc;
-                const float x = sm.e[pad16(s0 + k)].w;
-                dmin = fminf(dmin, fabsf(x - tmid));
-                acc += fixed_q(x, qsc);
-                if (k == kh) snap_h = acc;    // inclusive of the heavy ckpt slot
-            }
-            exact = __any_sync(0xffffffffu, dmin <= thalf);
-        }
-        if (exact) {
-            acc = snap_l = snap_h = snap_b = 0;
-#pragma unroll
-            for (int k = 0; k < kPartItems; ++k) {
-                const uint32_t slot = (uint32_t)(s0 + k);
-                if (k == kl) snap_l = acc;
-                if (k == kb) snap_b = acc;
-                const uint64_t q = fixed_q(sm.e[pad16(slot)].w, qsc);
-                const uint64_t v = slot < tl ? min(q, Qn) : (slot >= hstart ? max(q, Qn1) : 0ull);
-                acc += v;
-                if (k == kh) snap_h = acc;    // inclusive of the heavy ckpt slot
-            }
-        }
-        uint64_t inc = acc;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            uint64_t o = __shfl_up_sync(0xffffffffu, inc, d);
-            if (lane >= d) inc += o;
-        }
-        const uint64_t X = inc - acc;
-        const uint64_t Tall = __shfl_sync(0xffffffffu, inc, 31);
-        // q sum of the chunk's lights: from the lane that holds slot tl
-        const int owner = tl >= (uint32_t)kChunk ? 31 : (int)(tl / kPartItems);
-        uint64_t TLcand = (kb >= 0 && kb < kPartItems) ? X + snap_b : Tall;
-        const uint64_t TL = tl >= (uint32_t)kChunk ? Tall : __shfl_sync(0xffffffffu, TLcand, owner);
-        if (kl < kPartItems && (uint32_t)(s0 + kl) < tl)
-            put_ck(ckl, (run_l + s0 + kl) >> 5, s, run_sl + X + snap_l);
-        if (kh < kPartItems && (uint32_t)(s0 + kh) >= hstart)
-            put_ck(ckh, (run_h + kChunk - 1 - (s0 + kh)) >> 5, s, run_sh + (Tall - X - snap_h));
-        // ---- coalesced copy-out
-        uint2 *lh2 = reinterpret_cast<uint2 *>(lh);
-        const uint2 *e2 = reinterpret_cast<const uint2 *>(sm.e);
-        // two entries in flight per lane
-        for (uint32_t q = lane; q < tl; q += 64) {
-            const uint2 v0 = e2[pad16(q)];
-            const bool two = q + 32 < tl;
-            const uint2 v1 = two ? e2[pad16(q + 32)] : v0;
-            lh2[run_l + q] = v0;
-            if (two) lh2[run_l + q + 32] = v1;
-        }
-        for (uint32_t q = lane; q < tnh; q += 64) {
-            const uint2 v0 = e2[pad16(kChunk - 1 - q)];
-            const bool two = q + 32 < tnh;
-            const uint2 v1 = two ? e2[pad16(kChunk - 1 - (q + 32))] : v0;
-            lh2[n - 1 - (run_h + q)] = v0;
-            if (two) lh2[n - 1 - (run_h + q + 32)] = v1;
-        }
-        run_l += tl;
-        run_h += tnh;
-        run_sl += TL;
-        run_sh += Tall - TL;
-    }
+    uint64_t sl, sh;
+    scatter_range<kAligned>(X, stage[threadIdx.x >> 5], s, a, b, seg_loff[s], sl, sh);
     if (lane == 0) {
         SegVal v;
-        v.sl = run_sl;
-        v.sh = run_sh;
+        v.sl = sl;
+        v.sh = sh;
         v.nl = 0;
         v.pad = 0;
         seg_sum[s] = v;
@@ -1041,6 +864,7 @@ BatchSegLayout batch_seg_layout(uint64_t cap, uint32_t ntab) {
     L.ckh = take(((cap >> 5) + 2ull * ntab + 2) * sizeof(CkRec));
     L.recs = take((cap / kBSeg + 2ull * ntab + 1) * sizeof(SplitRec));
     L.zero = take(sizeof(SegVal));
+    L.lists = take(2ull * ntab * 4);
     L.total = off;
     return L;
 }

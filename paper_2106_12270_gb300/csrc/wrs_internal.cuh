@@ -115,7 +115,8 @@ struct __align__(16) BatchTab {
 // tables (all offsets 256-byte aligned); the counters and lh sit where the
 // chunked kernel expects its counter and lh.
 struct BatchSegLayout {
-    uint64_t counters;   // [0] tables taken, [1] sections, [2] split records
+    uint64_t counters;   // [0] large tables taken, [1] sections, [2] split records,
+                         // [3] small tables taken, [4] large tables, [5] small tables
     uint64_t lh;         // cap Entry
     uint64_t tp;         // ntab BuildParams
     uint64_t tabs;       // ntab BatchTab
@@ -123,6 +124,7 @@ struct BatchSegLayout {
     uint64_t ckl, ckh;   // (cap >> 5) + 2 ntab + 2 CkRec each
     uint64_t recs;       // cap / kBSeg + 2 ntab + 1 SplitRec
     uint64_t zero;       // one zero SegVal (the checkpoints' segment prefix)
+    uint64_t lists;      // 2 ntab uint32: the large tables, then the small ones
     uint64_t total;
     uint64_t cap;
 };
