@@ -200,7 +200,7 @@ k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__
     const uint32_t s = blockIdx.x * (kPartThreads / 32) + (threadIdx.x >> 5);
     if (s >= NS) return;
     const float lmax = P->light_max;
-    const int qshift = P->qshift;
+    const QScale qsc = qscale(P->qshift);
     uint64_t a, b;
     sub_range(s, NS, C, n, a, b);
     uint32_t cnt = 0;
@@ -218,22 +218,21 @@ k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
                 cnt += (v[r].x <= lmax) + (v[r].y <= lmax) + (v[r].z <= lmax) + (v[r].w <= lmax);
-                qs += fixed_q_bits(v[r].x, qshift) + fixed_q_bits(v[r].y, qshift) +
-                      fixed_q_bits(v[r].z, qshift) + fixed_q_bits(v[r].w, qshift);
+                qs += fixed_q(v[r].x, qsc) + fixed_q(v[r].y, qsc) + fixed_q(v[r].z, qsc) +
+                      fixed_q(v[r].w, qsc);
             }
         }
         for (; i < b4; i += 32) {
             float4 v = __ldg(w4 + i);
             cnt += (v.x <= lmax) + (v.y <= lmax) + (v.z <= lmax) + (v.w <= lmax);
-            qs += fixed_q_bits(v.x, qshift) + fixed_q_bits(v.y, qshift) +
-                  fixed_q_bits(v.z, qshift) + fixed_q_bits(v.w, qshift);
+            qs += fixed_q(v.x, qsc) + fixed_q(v.y, qsc) + fixed_q(v.z, qsc) + fixed_q(v.w, qsc);
         }
         tail = b4 * 4 > a ? b4 * 4 : a;
     }
     for (uint64_t i = tail + lane; i < b; i += 32) {
         float x = __ldg(w + i);
         cnt += (x <= lmax);
-        qs += fixed_q_bits(x, qshift);
+        qs += fixed_q(x, qsc);
     }
     cnt = __reduce_add_sync(0xffffffffu, cnt);
 #pragma unroll

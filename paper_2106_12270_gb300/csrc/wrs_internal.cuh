@@ -214,17 +214,26 @@ __device__ __forceinline__ u128 shfl_u128(u128 v, int src) {
     return ((u128)hi << 64) | lo;
 }
 
-// Fixed point of an FP32 weight: q = round(w * 2^S) < 2^63, halves rounded
+// Fixed point of an FP32 weight: q = round(w * 2^S) < 2^62, halves rounded
 // up.  S = qshift + 150 lies in [-97, 210] (the total W is in [2^-149,
 // 2^159)); 2^S is applied as two exact power-of-two factors, so x = w * 2^S
 // is exact unless it falls below the FP32 normal range, where it is far
-// below 1/2 and q = 0 however it rounds (x < 2^62: no overflow).  Then
-// q = floor(x + 1/2) with the addition rounded down: from 2^23 on x is a
-// multiple of 1/2 and the sum is exact or rounds back to the integer x;
-// below, floor(x + 1/2) is itself a float <= x + 1/2, so rounding down never
-// crosses it.  Needs IEEE subnormals (no flush to zero).  The weight must be
-// finite and not negative (checked by the total-weight step before any caller
-// runs; -0 gives 0).
+// below 1/2 and q = 0 however it rounds (x <= W 2^S < 2^62: no overflow).
+// q is assembled from 32-bit conversions, which issue about eight times as
+// fast as a float to 64-bit integer conversion on sm_103 (that one runs on
+// the FP64 unit):
+//   hi = floor(x / 2^32) < 2^30 (the scaling is exact; below the normal
+//        range hi is 0 either way), a float of at most 24 significant bits;
+//   lo = x - hi 2^32 in [0, 2^32), one fused multiply-add, exact: lo is x
+//        itself below 2^32, 0 from 2^56 on (x is then a multiple of 2^33),
+//        and between, a multiple of ulp(x) below 2^32, at most 24 bits;
+//   q  = hi 2^32 + floor(lo + 1/2), the addition rounded down: from 2^23 on
+//        lo is an integer and the sum is exact or rounds back to lo; below,
+//        floor(lo + 1/2) is itself a float <= lo + 1/2, so rounding down
+//        never crosses it.
+// Needs IEEE subnormals (no flush to zero).  The weight must be finite and
+// not negative (checked by the total-weight step before any caller runs; -0
+// gives 0).
 struct QScale {
     float c1, c2;   // 2^min(S, 127), 2^(S - min(S, 127))
 };
@@ -238,22 +247,9 @@ __device__ __forceinline__ QScale qscale(int qshift) {
 }
 __device__ __forceinline__ uint64_t fixed_q(float w, QScale qs) {
     const float x = __fmul_rn(__fmul_rn(w, qs.c1), qs.c2);
-    return __float2ull_rd(__fadd_rd(x, 0.5f));
-}
-
-// The same q from the weight's bits, in integer operations only: with w =
-// m 2^(e'-150) (e' = max(biased exponent, 1)), q = m 2^(e' + qshift), a
-// negative exponent rounding half up (qshift = S - 150).  Equal to fixed_q
-// for every finite non-negative weight; the kernels use whichever form keeps
-// their busiest pipe free.
-__device__ __forceinline__ uint64_t fixed_q_bits(float w, int qshift) {
-    const uint32_t u = __float_as_uint(w) & 0x7fffffffu;
-    const uint32_t e = u >> 23;
-    const uint32_t m = (u & 0x7fffffu) | (e ? 0x800000u : 0u);
-    const int sh = (int)(e ? e : 1u) + qshift;
-    if (sh >= 0) return (uint64_t)m << sh;   // sh <= 39 for every weight <= W
-    const int r = -sh;
-    return r > 24 ? 0ull : (uint64_t)((m + (1u << (r - 1))) >> r);
+    const uint32_t hi = __float2uint_rz(__fmul_rn(x, 0x1p-32f));
+    const float lo = __fmaf_rn(__uint2float_rz(hi), -0x1p32f, x);
+    return ((uint64_t)hi << 32) | __float2uint_rd(__fadd_rd(lo, 0.5f));
 }
 
 // q of a light item clamped to at most Qn = floor(Q/N), so that its scaled
