@@ -331,10 +331,12 @@ k_greedy_tile(const float *__restrict__ w, uint64_t n, const BuildParams *__rest
             }
         }
         // ---- the items left over, in index order, to this sub-segment's region
+        // (both loops stay rolled: the kernel is large enough that its warps
+        // stall on instruction fetch, and these loops index no registers)
         uint32_t left = 0;
         {
             uint32_t lr = lrank0, hr = hrank0;
-#pragma unroll
+#pragma unroll 1
             for (int k = 0; k < kTilePer; ++k) {
                 const bool valid = (uint32_t)k < vt, lt = (lmask >> k) & 1u;
                 const bool keep = valid && (!elig || (lt ? lr >= xk : hr >= yk));
@@ -348,7 +350,7 @@ k_greedy_tile(const float *__restrict__ w, uint64_t n, const BuildParams *__rest
         {
             uint64_t pos = out + lpre;
             uint32_t lr = lrank0, hr = hrank0;
-#pragma unroll
+#pragma unroll 1
             for (int k = 0; k < kTilePer; ++k) {
                 const bool lt = (lmask >> k) & 1u, valid = (uint32_t)k < vt;
                 if ((left >> k) & 1u) {
