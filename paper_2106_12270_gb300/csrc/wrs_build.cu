@@ -243,28 +243,48 @@ k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__
     }
 }
 
-// Block-wide exclusive scan of up to kScanPer values per thread (1024
-// threads); returns this thread's exclusive prefix and the total.
+// The single-CTA scans over the sub-segments (1024 threads, kMaxSegs =
+// 8 * 1024 values at most): warp w holds values 256 w + 32 k + lane, k =
+// 0..7, so every load and store of a warp is contiguous; each warp scans its
+// 256 values in order (eight warp scans), then one step over the 32 warp
+// totals.  warp_excl_scan8 returns, for each k, the exclusive prefix of value
+// (k, lane) within the warp's run, and the run's total.
 template <typename T>
-__device__ __forceinline__ void block_scan_1024(T v, T &excl, T &total, T *wtot) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T inc = v;
+__device__ __forceinline__ T warp_excl_scan8(T (&v)[kMaxSegs / 1024]) {
+    const int lane = threadIdx.x & 31;
+    T run = 0;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        T o = __shfl_up_sync(0xffffffffu, inc, d);
-        if (lane >= d) inc += o;
+    for (int k = 0; k < kMaxSegs / 1024; ++k) {
+        T inc = v[k];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const T o = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += o;
+        }
+        const T x = v[k];
+        v[k] = run + inc - x;
+        run += __shfl_sync(0xffffffffu, inc, 31);
     }
-    if (lane == 31) wtot[warp] = inc;
+    return run;
+}
+
+// Exclusive prefix of this warp's run among the 32 runs, and the sum of all
+// runs (two barriers; wtot holds 32 values).
+template <typename T>
+__device__ __forceinline__ T block_runs_prefix(T run, T *wtot, T &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) wtot[warp] = run;
     __syncthreads();
     T pre = 0, tot = 0;
+#pragma unroll 8
     for (int k = 0; k < 32; ++k) {
-        T c = wtot[k];
+        const T c = wtot[k];
         pre += (k < warp) ? c : (T)0;
         tot += c;
     }
     __syncthreads();
-    excl = pre + inc - v;
     total = tot;
+    return pre;
 }
 
 // One CTA (1024 threads): Q = sum of all q, its derived constants, and the
@@ -276,23 +296,23 @@ k_qsum(BuildParams *__restrict__ P, const uint32_t *__restrict__ seg_cnt,
     __shared__ uint64_t wtot[32];
     if (P->status) return;
     constexpr int kPer = kMaxSegs / 1024;
-    const uint32_t s0 = threadIdx.x * kPer;
-    uint64_t c[kPer], qs = 0, cs = 0;
+    const uint32_t s0 = (threadIdx.x >> 5) * (32 * kPer) + (threadIdx.x & 31);
+    uint64_t c[kPer], qs = 0;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
-        uint32_t sidx = s0 + k;
+        const uint32_t sidx = s0 + 32 * k;
         c[k] = sidx < NS ? seg_cnt[sidx] : 0;
         qs += sidx < NS ? seg_q[sidx] : 0;
-        cs += c[k];
     }
-    uint64_t qe, Q, ce, ctot;
-    block_scan_1024(qs, qe, Q, wtot);
-    block_scan_1024(cs, ce, ctot, wtot);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, d);
+    uint64_t Q, ctot;
+    block_runs_prefix(qs, wtot, Q);
+    const uint64_t cpre = block_runs_prefix(warp_excl_scan8(c), wtot, ctot);
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
-        uint32_t sidx = s0 + k;
-        if (sidx <= NS) seg_loff[sidx] = ce;
-        ce += c[k];
+        const uint32_t sidx = s0 + 32 * k;
+        if (sidx <= NS) seg_loff[sidx] = cpre + c[k];
     }
     if (threadIdx.x == 0) {
         const uint64_t Qn = Q / n;
@@ -310,7 +330,6 @@ k_qsum(BuildParams *__restrict__ P, const uint32_t *__restrict__ seg_cnt,
         P->tmid = mid;
         P->thalf = half;
     }
-    (void)qe;
 }
 
 // Place every item (scatter_range, wrs_scatter.cuh): each warp works alone
@@ -361,32 +380,34 @@ k_segscan(BuildParams *__restrict__ P, const uint64_t *__restrict__ seg_loff,
     __shared__ uint64_t wtot[32];
     if (P->status) return;
     constexpr int kPer = kMaxSegs / 1024;
-    const uint32_t s0 = threadIdx.x * kPer;
-    uint64_t sl[kPer], sh[kPer], tsl = 0, tsh = 0;
+    const uint32_t s0 = (threadIdx.x >> 5) * (32 * kPer) + (threadIdx.x & 31);
+    // the light sums, then the heavy sums (one array of values live at a time)
+    uint64_t v[kPer], Ltot, Htot;
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
-        uint32_t sidx = s0 + k;
-        sl[k] = sidx < NS ? (uint64_t)seg_sum[sidx].sl : 0;
-        sh[k] = sidx < NS ? (uint64_t)seg_sum[sidx].sh : 0;
-        tsl += sl[k];
-        tsh += sh[k];
+        const uint32_t sidx = s0 + 32 * k;
+        v[k] = sidx < NS ? (uint64_t)seg_sum[sidx].sl : 0;
     }
-    uint64_t el, Ltot, eh, Htot;
-    block_scan_1024(tsl, el, Ltot, wtot);
-    block_scan_1024(tsh, eh, Htot, wtot);
+    const uint64_t lpre = block_runs_prefix(warp_excl_scan8(v), wtot, Ltot);
 #pragma unroll
     for (int k = 0; k < kPer; ++k) {
-        uint32_t sidx = s0 + k;
+        const uint32_t sidx = s0 + 32 * k;
+        if (sidx <= NS) seg_pre[sidx].sl = lpre + v[k];
+    }
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const uint32_t sidx = s0 + 32 * k;
+        v[k] = sidx < NS ? (uint64_t)seg_sum[sidx].sh : 0;
+    }
+    const uint64_t hpre = block_runs_prefix(warp_excl_scan8(v), wtot, Htot);
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const uint32_t sidx = s0 + 32 * k;
         if (sidx <= NS) {
-            SegVal v;
-            v.sl = el;
-            v.sh = eh;
-            v.nl = seg_loff[sidx];
-            v.pad = 0;
-            seg_pre[sidx] = v;
+            seg_pre[sidx].sh = hpre + v[k];
+            seg_pre[sidx].nl = seg_loff[sidx];
+            seg_pre[sidx].pad = 0;
         }
-        el += sl[k];
-        eh += sh[k];
     }
     if (threadIdx.x == 0) {
         const uint64_t Q = P->Q;
