@@ -673,6 +673,10 @@ k_bseg_part(const float *__restrict__ w, const uint64_t *__restrict__ off,
     extern __shared__ __align__(16) unsigned char bsm_raw[];
     BsegShared<BT> &sm = *reinterpret_cast<BsegShared<BT> *>(bsm_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // The warp kernel that follows works on other tables: it may start as
+    // soon as this grid's CTAs leave room (it waits for this grid to finish
+    // before it ends).
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     for (;;) {
         if (tid == 0) {
             // the large tables, in the order of the list (k_bseg_lists)
@@ -1044,7 +1048,13 @@ k_bseg_warp(const float *__restrict__ w, const uint64_t *__restrict__ off,
         uint32_t k = 0;
         if (lane == 0) k = atomicAdd(ctr + 3, 1u);
         k = __shfl_sync(0xffffffffu, k, 0);
-        if (k >= nsmall) return;
+        if (k >= nsmall) {
+            // launched as a dependent of the CTA kernel (the large tables):
+            // end only after that grid has finished and its writes are
+            // visible, so that the next kernel in the stream sees both
+            asm volatile("griddepcontrol.wait;\n" ::: "memory");
+            return;
+        }
         const uint32_t t = sml[k];
         const uint64_t base = off[t], n = off[t + 1] - base;
         const float *wt = w + base;
@@ -1248,13 +1258,37 @@ cudaError_t launch_build_batched_seg(const float *d_w, const uint64_t *d_off, ui
     auto *ckl = reinterpret_cast<CkRec *>(ws + L.ckl);
     auto *ckh = reinterpret_cast<CkRec *>(ws + L.ckh);
     auto *recs = reinterpret_cast<SplitRec *>(ws + L.recs);
-    // the large tables (a CTA each), then the small ones (a warp each)
+    // the large tables (a CTA each), then the small ones (a warp each).  The
+    // warp kernel is a programmatic dependent of the CTA kernel: its CTAs
+    // start in the CTA kernel's tail, where that kernel's last tables leave
+    // SMs idle.
     k_bseg_part<BT><<<blocks, BT, smem, st>>>(d_w, d_off, lists, ntab, ctr, L.cap, lh, tp, tabs,
                                               sec_tab, ckl, ckh, recs, d_info);
-    k_bseg_warp<<<wblocks, 256, 0, st>>>(d_w, d_off, lists, ntab, ctr, L.cap, lh, tp, tabs, sec_tab,
-                                         ckl, ckh, recs, d_info);
     e = cudaGetLastError();
     if (e) return e;
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(wblocks);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, k_bseg_warp, d_w, d_off, (const uint32_t *)lists, ntab, ctr,
+                               (uint64_t)L.cap, lh, tp, tabs, sec_tab, ckl, ckh, recs, d_info);
+        if (e == cudaErrorNotSupported || e == cudaErrorInvalidValue) {
+            // no programmatic launches here: an ordinary launch after the
+            // CTA kernel (griddepcontrol.wait then returns at once)
+            (void)cudaGetLastError();
+            k_bseg_warp<<<wblocks, 256, 0, st>>>(d_w, d_off, lists, ntab, ctr, L.cap, lh, tp, tabs,
+                                                 sec_tab, ckl, ckh, recs, d_info);
+            e = cudaGetLastError();
+        }
+        if (e) return e;
+    }
     return launch_bseg_split_pack(ws, L, ntab, d_rows, d_row_ptrs, d_info, st);
 }
 
