@@ -92,6 +92,7 @@ k_sum(const float *__restrict__ w, uint64_t n, u128 *__restrict__ bins_out,
     __shared__ uint64_t bins[kSumBands][kSumThreads];
     __shared__ u128 band[kSumBands];
     __shared__ uint32_t s_last;
+    pdl_trigger();
     const int tid = threadIdx.x;
 #pragma unroll
     for (int b = 0; b < kSumBands; ++b) bins[b][tid] = 0;
@@ -195,6 +196,8 @@ __global__ void __launch_bounds__(kPartThreads)
 k_count(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict__ P,
         uint32_t *__restrict__ seg_cnt, uint64_t *__restrict__ seg_q, uint64_t C, uint32_t NS,
         int aligned) {
+    pdl_trigger();
+    pdl_wait();
     if (P->status) return;
     const int lane = threadIdx.x & 31;
     const uint32_t s = blockIdx.x * (kPartThreads / 32) + (threadIdx.x >> 5);
@@ -294,6 +297,8 @@ k_qsum(BuildParams *__restrict__ P, const uint32_t *__restrict__ seg_cnt,
        const uint64_t *__restrict__ seg_q, uint64_t *__restrict__ seg_loff, uint32_t NS,
        uint64_t n) {
     __shared__ uint64_t wtot[32];
+    pdl_trigger();
+    pdl_wait();
     if (P->status) return;
     constexpr int kPer = kMaxSegs / 1024;
     const uint32_t s0 = (threadIdx.x >> 5) * (32 * kPer) + (threadIdx.x & 31);
@@ -341,6 +346,8 @@ k_scatter(const float *__restrict__ w, uint64_t n, const BuildParams *__restrict
           const uint64_t *__restrict__ seg_loff, Entry *__restrict__ lh, CkRec *__restrict__ ckl,
           CkRec *__restrict__ ckh, SegVal *__restrict__ seg_sum, uint64_t C, uint32_t NS) {
     __shared__ WarpStage stage[kPartThreads / 32];
+    pdl_trigger();
+    pdl_wait();
     if (P->status) return;
     const int lane = threadIdx.x & 31;
     const uint32_t s = blockIdx.x * (kPartThreads / 32) + (threadIdx.x >> 5);
@@ -378,6 +385,8 @@ k_segscan(BuildParams *__restrict__ P, const uint64_t *__restrict__ seg_loff,
           const SegVal *__restrict__ seg_sum, SegVal *__restrict__ seg_pre,
           CkRec *__restrict__ ckl, CkRec *__restrict__ ckh, uint64_t n, uint32_t NS) {
     __shared__ uint64_t wtot[32];
+    pdl_trigger();
+    pdl_wait();
     if (P->status) return;
     constexpr int kPer = kMaxSegs / 1024;
     const uint32_t s0 = (threadIdx.x >> 5) * (32 * kPer) + (threadIdx.x & 31);
@@ -534,6 +543,8 @@ k_split(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
         const SegVal *__restrict__ seg_pre, SplitRec *__restrict__ splits, uint64_t n,
         uint64_t S, uint32_t sections) {
     __shared__ unsigned long long s_a, s_b;
+    pdl_trigger();
+    pdl_wait();
     if (P->status) return;
     const BuildParams Pm = *P;
     SplitCtx C;
@@ -604,6 +615,8 @@ k_split_fine(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
              const CkRec *__restrict__ ckl, const CkRec *__restrict__ ckh,
              const SegVal *__restrict__ seg_pre, SplitRec *__restrict__ splits, uint64_t n,
              uint64_t S, uint32_t sections) {
+    pdl_trigger();
+    pdl_wait();
     if (P->status) return;
     const uint64_t t = 1 + (uint64_t)blockIdx.x * (kSplitThreads / 32) + (threadIdx.x >> 5);
     if (t >= sections) return;
@@ -620,6 +633,8 @@ k_split_fine(const BuildParams *__restrict__ P, const Entry *__restrict__ lh,
 // Splits 0 and s (the whole table's ends).
 __global__ void k_split_ends(const BuildParams *__restrict__ P, SplitRec *__restrict__ splits,
                              uint32_t sections) {
+    pdl_trigger();
+    pdl_wait();
     if (P->status) return;
     SplitRec r0, rs;
     r0.i = r0.j = 0; r0.pad[0] = r0.pad[1] = 0; r0.D = 0; r0.E = 0;
@@ -668,6 +683,8 @@ __device__ __forceinline__ void pack_section(const BuildParams *__restrict__ P,
                                              uint32_t t) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ u128 s_w[16];
+    pdl_trigger();
+    pdl_wait();
     if (P->status) return;
     int64_t *sK = reinterpret_cast<int64_t *>(smem);
     uint2 *sE = reinterpret_cast<uint2 *>(smem + 8 * pack_slots(S));
@@ -1006,6 +1023,7 @@ cudaError_t launch_bseg_split_pack(unsigned char *ws, const BatchSegLayout &L, u
 // build summary
 // ===========================================================================
 __global__ void k_info(const BuildParams *__restrict__ P, wrs_build_info *__restrict__ out) {
+    pdl_wait();
     uint32_t st = P->status;
     wrs_build_info r;
     r.status = (st & ERR_NONFINITE) ? WRS_ENONFINITE
@@ -1084,9 +1102,10 @@ cudaError_t launch_count(const float *d_w, uint64_t n, unsigned char *ws, const 
     const uint32_t NS = num_segments(n);
     const unsigned blocks = (NS + kPartThreads / 32 - 1) / (kPartThreads / 32);
     const int aligned = ((uintptr_t)d_w % 16) == 0;
-    k_count<<<blocks, kPartThreads, 0, st>>>(d_w, n, P, cnt, segq, C, NS, aligned);
-    k_qsum<<<1, 1024, 0, st>>>(P, cnt, segq, loff, NS, n);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(k_count, dim3(blocks), dim3(kPartThreads), 0, st, d_w, n, P, cnt,
+                               segq, C, NS, aligned);
+    if (!e) e = launch_pdl(k_qsum, dim3(1), dim3(1024), 0, st, P, cnt, segq, loff, NS, n);
+    return e;
 }
 
 cudaError_t launch_partition(const float *d_w, uint64_t n, unsigned char *ws, const Layout &L,
@@ -1104,15 +1123,14 @@ cudaError_t launch_partition(const float *d_w, uint64_t n, unsigned char *ws, co
     const uint32_t NS = num_segments(n);
     const unsigned blocks = (NS + kPartThreads / 32 - 1) / (kPartThreads / 32);
     const int aligned = ((uintptr_t)d_w % 16) == 0;
-    k_count<<<blocks, kPartThreads, 0, st>>>(d_w, n, P, cnt, segq, C, NS, aligned);
-    k_qsum<<<1, 1024, 0, st>>>(P, cnt, segq, loff, NS, n);
-    if (aligned)
-        k_scatter<true><<<blocks, kPartThreads, 0, st>>>(d_w, n, P, loff, lh, ckl, ckh, sum, C, NS);
-    else
-        k_scatter<false><<<blocks, kPartThreads, 0, st>>>(d_w, n, P, loff, lh, ckl, ckh, sum, C,
-                                                          NS);
-    k_segscan<<<1, 1024, 0, st>>>(P, loff, sum, pre, ckl, ckh, n, NS);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(k_count, dim3(blocks), dim3(kPartThreads), 0, st, d_w, n, P, cnt,
+                               segq, C, NS, aligned);
+    if (!e) e = launch_pdl(k_qsum, dim3(1), dim3(1024), 0, st, P, cnt, segq, loff, NS, n);
+    if (!e)
+        e = launch_pdl(aligned ? k_scatter<true> : k_scatter<false>, dim3(blocks),
+                       dim3(kPartThreads), 0, st, d_w, n, P, loff, lh, ckl, ckh, sum, C, NS);
+    if (!e) e = launch_pdl(k_segscan, dim3(1), dim3(1024), 0, st, P, loff, sum, pre, ckl, ckh, n, NS);
+    return e;
 }
 
 cudaError_t launch_split(uint64_t n, unsigned char *ws, const Layout &L, uint32_t S,
@@ -1124,17 +1142,17 @@ cudaError_t launch_split(uint64_t n, unsigned char *ws, const Layout &L, uint32_
     auto *pre = reinterpret_cast<const SegVal *>(ws + L.seg_pre);
     auto *sp = reinterpret_cast<SplitRec *>(ws + L.splits);
     uint32_t s = (uint32_t)L.sections;
-    k_split_ends<<<1, 1, 0, st>>>(P, sp, s);
-    if (s > 1) {
+    cudaError_t e = launch_pdl(k_split_ends, dim3(1), dim3(1), 0, st, P, sp, s);
+    if (!e && s > 1) {
         unsigned blocks = (unsigned)((s - 1 + kSplitThreads - 1) / kSplitThreads);
-        if (method == WRS_SPLIT_BINARY)
-            k_split<false><<<blocks, kSplitThreads, 0, st>>>(P, lh, ckl, ckh, pre, sp, n, S, s);
-        else
-            k_split<true><<<blocks, kSplitThreads, 0, st>>>(P, lh, ckl, ckh, pre, sp, n, S, s);
+        e = launch_pdl(method == WRS_SPLIT_BINARY ? k_split<false> : k_split<true>, dim3(blocks),
+                       dim3(kSplitThreads), 0, st, P, lh, ckl, ckh, pre, sp, n, (uint64_t)S, s);
         const unsigned fblocks = (unsigned)((s - 1 + kSplitThreads / 32 - 1) / (kSplitThreads / 32));
-        k_split_fine<<<fblocks, kSplitThreads, 0, st>>>(P, lh, ckl, ckh, pre, sp, n, S, s);
+        if (!e)
+            e = launch_pdl(k_split_fine, dim3(fblocks), dim3(kSplitThreads), 0, st, P, lh, ckl, ckh,
+                           pre, sp, n, (uint64_t)S, s);
     }
-    return cudaGetLastError();
+    return e;
 }
 
 template <int kPer>
@@ -1147,11 +1165,10 @@ static cudaError_t launch_pack_t(void (*kern)(const BuildParams *, const Entry *
     cudaError_t e = kPer == 8 ? ensure_dynamic_smem<k_pack8>(smem) : ensure_dynamic_smem<k_pack16>(smem);
     if (e) return e;
     const uint32_t threads = (S + kPer - 1) / kPer;   // S is a multiple of 256: whole warps
-    kern<<<(unsigned)L.sections, threads, smem, st>>>(
-        P, reinterpret_cast<const Entry *>(ws + L.lh),
-        reinterpret_cast<const SplitRec *>(ws + L.splits), reinterpret_cast<uint2 *>(d_rows), n,
-        S);
-    return cudaGetLastError();
+    return launch_pdl(kern, dim3((unsigned)L.sections), dim3(threads), smem, st, P,
+                      reinterpret_cast<const Entry *>(ws + L.lh),
+                      reinterpret_cast<const SplitRec *>(ws + L.splits),
+                      reinterpret_cast<uint2 *>(d_rows), n, S);
 }
 
 cudaError_t launch_pack(uint64_t n, wrs_row *d_rows, unsigned char *ws, const Layout &L,
@@ -1162,8 +1179,8 @@ cudaError_t launch_pack(uint64_t n, wrs_row *d_rows, unsigned char *ws, const La
 
 cudaError_t launch_info(unsigned char *ws, const Layout &L, wrs_build_info *d_info,
                         cudaStream_t st) {
-    k_info<<<1, 1, 0, st>>>(reinterpret_cast<const BuildParams *>(ws + L.params), d_info);
-    return cudaGetLastError();
+    return launch_pdl(k_info, dim3(1), dim3(1), 0, st,
+                      reinterpret_cast<const BuildParams *>(ws + L.params), d_info);
 }
 
 }  // namespace wrs

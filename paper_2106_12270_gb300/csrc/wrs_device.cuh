@@ -164,4 +164,39 @@ __device__ __forceinline__ int64_t key15_capped(const Limbs4 &a) {
     return big ? ((int64_t)1 << kKeyCap62) : key15(a);
 }
 
+
+// Programmatic dependent launch: a kernel launched with launch_pdl may start
+// while the previous kernel of the stream is still running; it calls
+// pdl_wait() before it reads anything that kernel (or an earlier one) wrote,
+// which returns once the previous grid has finished and its writes are
+// visible.  pdl_trigger() lets the next kernel start; it is issued at entry,
+// so that kernel's blocks only fill the room this grid's last blocks leave.
+// Neither waits on a flag: the wait ends when the previous grid ends, whose
+// blocks are all resident by the time a dependent starts.  Without a
+// programmatic launch both return at once.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+    if (e == cudaErrorNotSupported || e == cudaErrorInvalidValue) {
+        (void)cudaGetLastError();   // no programmatic launches: an ordinary one
+        cfg.numAttrs = 0;
+        e = cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+    }
+    return e;
+}
+
 }  // namespace wrs
