@@ -1042,6 +1042,7 @@ k_bseg_warp(const float *__restrict__ w, const uint64_t *__restrict__ off,
     // staging memory, which the placement uses only after the total
     uint64_t *bins = reinterpret_cast<uint64_t *>(&sm);
     static_assert(sizeof(WarpStage) >= kBands * 32 * sizeof(uint64_t), "bins fit the stage");
+    pdl_trigger();   // the split kernel may fill this grid's tail
     const uint32_t nsmall = ctr[5];
     const uint32_t *sml = lists + ntab;
     for (;;) {

@@ -933,6 +933,8 @@ k_bseg_split(const uint32_t *__restrict__ ctr, const uint32_t *__restrict__ sec_
              const Entry *__restrict__ lh, const CkRec *__restrict__ ckl,
              const CkRec *__restrict__ ckh, const SegVal *__restrict__ zero,
              SplitRec *__restrict__ recs) {
+    pdl_trigger();
+    pdl_wait();
     const uint32_t sec = blockIdx.x * 8 + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (sec >= ctr[1]) return;
@@ -978,6 +980,8 @@ k_bseg_pack(const uint32_t *__restrict__ ctr, const uint32_t *__restrict__ sec_t
             const BatchTab *__restrict__ tabs, BuildParams *__restrict__ tp,
             const Entry *__restrict__ lh, const SplitRec *__restrict__ recs,
             uint2 *__restrict__ rows, uint2 *const *__restrict__ row_ptrs) {
+    pdl_trigger();
+    pdl_wait();
     const uint32_t sec = blockIdx.x;
     if (sec >= ctr[1]) return;
     const uint32_t t = sec_tab[sec];
@@ -989,6 +993,7 @@ k_bseg_pack(const uint32_t *__restrict__ ctr, const uint32_t *__restrict__ sec_t
 // A table whose split or pack found an inconsistency reports it.
 __global__ void k_bseg_info(const BuildParams *__restrict__ tp, uint32_t ntab,
                             wrs_table_summary *__restrict__ info) {
+    pdl_wait();
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < ntab && (tp[t].status & ERR_INTERNAL)) info[t].status = WRS_EINVAL;
 }
@@ -1010,13 +1015,16 @@ cudaError_t launch_bseg_split_pack(unsigned char *ws, const BatchSegLayout &L, u
     auto *recs = reinterpret_cast<SplitRec *>(ws + L.recs);
     const uint64_t maxsec = L.cap / kBSeg + ntab;   // an upper bound of the sections
     if (maxsec >= (1ull << 31)) return cudaErrorInvalidValue;
-    k_bseg_split<<<(unsigned)((maxsec + 7) / 8), 256, 0, st>>>(ctr, sec_tab, tabs, tp, lh, ckl, ckh,
-                                                              zero, recs);
-    k_bseg_pack<<<(unsigned)maxsec, kBSeg / 8, smem, st>>>(
-        ctr, sec_tab, tabs, tp, lh, recs, reinterpret_cast<uint2 *>(d_rows),
-        reinterpret_cast<uint2 *const *>(d_row_ptrs));
-    k_bseg_info<<<(ntab + 255) / 256, 256, 0, st>>>(tp, ntab, d_info);
-    return cudaGetLastError();
+    e = launch_pdl(k_bseg_split, dim3((unsigned)((maxsec + 7) / 8)), dim3(256), 0, st, ctr, sec_tab,
+                   tabs, (const BuildParams *)tp, lh, ckl, ckh, zero, recs);
+    if (!e)
+        e = launch_pdl(k_bseg_pack, dim3((unsigned)maxsec), dim3(kBSeg / 8), smem, st, ctr, sec_tab,
+                       tabs, tp, lh, (const SplitRec *)recs,
+                       reinterpret_cast<uint2 *>(d_rows), reinterpret_cast<uint2 *const *>(d_row_ptrs));
+    if (!e)
+        e = launch_pdl(k_bseg_info, dim3((ntab + 255) / 256), dim3(256), 0, st,
+                       (const BuildParams *)tp, ntab, d_info);
+    return e;
 }
 
 // ===========================================================================

@@ -116,6 +116,8 @@ k_greedy_tile(const float *__restrict__ w, uint64_t n, const BuildParams *__rest
     __shared__ uint64_t s_q[2 * kTileWarps];
     __shared__ uint32_t s_c[kTileWarps];
     __shared__ __int128 s_rex;   // the remaining scaled excess of the carried heavy
+    pdl_trigger();
+    pdl_wait();
     if (P->status) return;
     const uint32_t tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -382,6 +384,8 @@ __global__ void __launch_bounds__(256)
 k_rest_sum(const BuildParams *__restrict__ P, const uint32_t *__restrict__ tile_rest,
            uint32_t *__restrict__ tile_off, uint32_t *__restrict__ seg_rest, uint64_t NT,
            uint32_t NS) {
+    pdl_trigger();
+    pdl_wait();
     if (P->status) return;
     const uint32_t s = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (s >= NS) return;
@@ -414,6 +418,8 @@ __global__ void __launch_bounds__(1024)
 k_rest_scan(const BuildParams *__restrict__ P, const uint32_t *__restrict__ seg_rest,
             uint64_t *__restrict__ rest_off, uint64_t *__restrict__ n_rest, uint32_t NS) {
     __shared__ uint64_t wtot[32];
+    pdl_trigger();
+    pdl_wait();
     if (P->status) {
         if (threadIdx.x == 0) *n_rest = ~0ull;   // marks the failed build
         return;
@@ -458,6 +464,8 @@ k_rest_copy(const BuildParams *__restrict__ P, const uint32_t *__restrict__ rest
             const uint32_t *__restrict__ tile_off, const uint64_t *__restrict__ rest_off,
             uint32_t *__restrict__ dense_idx, float *__restrict__ dense_w, uint64_t NT,
             uint32_t NS) {
+    pdl_trigger();
+    pdl_wait();
     if (P->status) return;   // the greedy pass wrote no counts
     const uint64_t t = (uint64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (t >= NT) return;
@@ -479,6 +487,8 @@ k_rest_copy(const BuildParams *__restrict__ P, const uint32_t *__restrict__ rest
 __global__ void __launch_bounds__(256)
 k_rest_remap(const BuildParams *__restrict__ PR, const uint2 *__restrict__ rest_rows,
              const uint32_t *__restrict__ dense_idx, uint2 *__restrict__ rows, uint64_t n_rest) {
+    pdl_trigger();
+    pdl_wait();
     if (PR->status) return;
     const uint64_t T = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_rest; k += T) {
@@ -492,6 +502,7 @@ k_rest_remap(const BuildParams *__restrict__ PR, const uint2 *__restrict__ rest_
 __global__ void k_plus_info(const BuildParams *__restrict__ P, const uint64_t *__restrict__ loff,
                             uint32_t NS, const wrs_build_info *__restrict__ rest_info,
                             int rest_built, wrs_build_info *__restrict__ out) {
+    pdl_wait();
     const uint32_t st = P->status;
     wrs_build_info r;
     r.status = (st & ERR_NONFINITE) ? WRS_ENONFINITE
@@ -574,15 +585,20 @@ cudaError_t launch_build_plus(const float *d_w, uint64_t n, wrs_row *d_rows, uns
     auto *rest_rows = reinterpret_cast<wrs_row *>(ws + pl.rest_rows);
     auto *rest_info = reinterpret_cast<wrs_build_info *>(ws + pl.rest_info);
     const int aligned = ((uintptr_t)d_w % 16) == 0;
-    k_greedy_tile<<<(unsigned)NT, kTileThreads, 0, st>>>(d_w, n, P,
-                                                           reinterpret_cast<uint2 *>(d_rows),
-                                                           rest_idx, rest_w, tile_rest, min_items,
-                                                           aligned);
-    k_rest_sum<<<(NS + 7) / 8, 256, 0, st>>>(P, tile_rest, tile_off, seg_rest, NT, NS);
-    k_rest_scan<<<1, 1024, 0, st>>>(P, seg_rest, rest_off, n_rest, NS);
-    k_rest_copy<<<(unsigned)((NT + 7) / 8), 256, 0, st>>>(P, rest_idx, rest_w, tile_rest, tile_off,
-                                                          rest_off, dense_idx, dense_w, NT, NS);
-    e = cudaGetLastError();
+    e = launch_pdl(k_greedy_tile, dim3((unsigned)NT), dim3(kTileThreads), 0, st, d_w, n,
+                   (const BuildParams *)P, reinterpret_cast<uint2 *>(d_rows), rest_idx, rest_w,
+                   tile_rest, min_items, aligned);
+    if (!e)
+        e = launch_pdl(k_rest_sum, dim3((NS + 7) / 8), dim3(256), 0, st, (const BuildParams *)P,
+                       (const uint32_t *)tile_rest, tile_off, seg_rest, NT, NS);
+    if (!e)
+        e = launch_pdl(k_rest_scan, dim3(1), dim3(1024), 0, st, (const BuildParams *)P,
+                       (const uint32_t *)seg_rest, rest_off, n_rest, NS);
+    if (!e)
+        e = launch_pdl(k_rest_copy, dim3((unsigned)((NT + 7) / 8)), dim3(256), 0, st,
+                       (const BuildParams *)P, (const uint32_t *)rest_idx, (const float *)rest_w,
+                       (const uint32_t *)tile_rest, (const uint32_t *)tile_off,
+                       (const uint64_t *)rest_off, dense_idx, dense_w, NT, NS);
     if (e) return e;
     // the rest's size decides its launches: one read back
     uint64_t nr = 0;
@@ -603,13 +619,15 @@ cudaError_t launch_build_plus(const float *d_w, uint64_t n, wrs_row *d_rows, uns
         if (!e) e = launch_info(rws, LR, rest_info, st);
         if (e) return e;
         const unsigned rb = (unsigned)std::min<uint64_t>((nr + 255) / 256, 4096);
-        k_rest_remap<<<rb, 256, 0, st>>>(reinterpret_cast<const BuildParams *>(rws + LR.params),
-                                         reinterpret_cast<const uint2 *>(rest_rows), dense_idx,
-                                         reinterpret_cast<uint2 *>(d_rows), nr);
+        e = launch_pdl(k_rest_remap, dim3(rb), dim3(256), 0, st,
+                       reinterpret_cast<const BuildParams *>(rws + LR.params),
+                       reinterpret_cast<const uint2 *>(rest_rows), (const uint32_t *)dense_idx,
+                       reinterpret_cast<uint2 *>(d_rows), nr);
+        if (e) return e;
     }
-    k_plus_info<<<1, 1, 0, st>>>(P, reinterpret_cast<const uint64_t *>(ws + L.seg_loff), NSc,
-                                 rest_info, rest_built, d_info);
-    return cudaGetLastError();
+    return launch_pdl(k_plus_info, dim3(1), dim3(1), 0, st, (const BuildParams *)P,
+                      reinterpret_cast<const uint64_t *>(ws + L.seg_loff), NSc,
+                      (const wrs_build_info *)rest_info, rest_built, d_info);
 }
 
 uint64_t plus_workspace_bytes(uint64_t n, uint32_t S) { return make_plus_layout(n, S).total; }
