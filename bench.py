@@ -45,13 +45,13 @@ SAMPLE_BYTES_PER_DRAW = 36     # one 32-byte row sector + a 4-byte output
 SECTOR_BYTES = 32
 KERNELS_PER_BUILD = 10         # sum, count, qsum, scatter, segscan, split ends, split, split fine, pack, info
 # DRAM bytes the hardware moved per unit (dram__bytes_read.sum +
-# dram__bytes_write.sum) in ncu captures of these kernels: the build at
-# N = 2^25 Exp(1) items (sum 4.09, count 4.01, scatter 10.64, split 1.04, pack 14.37) and
+# dram__bytes_write.sum) in ncu captures of these kernels, one kernel per capture: the build at
+# N = 2^25 Exp(1) items (sum 4.09, count 4.08, scatter 10.72, split 1.04, pack 14.45) and
 # the naive sampler drawing 2^25 samples from a 2^25-row table (87.6 B of row
 # sectors read + 4 B written per draw); both workloads exceed L2 and the
 # traffic grows with the units, so a launch's traffic is these times its
 # units.  To be re-measured whenever one of these kernels changes.
-BUILD_TRAFFIC_PER_ITEM = 34.16
+BUILD_TRAFFIC_PER_ITEM = 34.39
 SAMPLE_TRAFFIC_PER_DRAW = 91.5
 SEEDS = {"zipf": 3, "zipf0.5": 5, "uniform": 1, "exponential": 4, "gamma": 7}
 
