@@ -673,9 +673,9 @@ k_bseg_part(const float *__restrict__ w, const uint64_t *__restrict__ off,
     extern __shared__ __align__(16) unsigned char bsm_raw[];
     BsegShared<BT> &sm = *reinterpret_cast<BsegShared<BT> *>(bsm_raw);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // The warp kernel that follows works on other tables: it may start as
-    // soon as this grid's CTAs leave room (it waits for this grid to finish
-    // before it ends).
+    // The small tables' statistics kernel that follows works on other
+    // tables: it may start as soon as this grid's CTAs leave room (it waits
+    // for this grid to finish before it ends).
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     for (;;) {
         if (tid == 0) {
@@ -972,7 +972,7 @@ k_bseg_part(const float *__restrict__ w, const uint64_t *__restrict__ off,
 // ---------------------------------------------------------------------------
 constexpr uint64_t kWarpTableMax = 1ull << 22;
 constexpr uint64_t kWarpTableMin = 8192;
-constexpr int kBsegWarpCtas = 3;   // CTAs of 8 warps per SM of the warp kernel
+constexpr int kBsegWarpCtas = 3;   // CTAs of 8 warps per SM of the placement kernel
 
 __device__ __forceinline__ bool bseg_small(uint64_t n, uint64_t T) { return n >= 1 && n <= T; }
 
@@ -1023,37 +1023,38 @@ k_bseg_lists(const uint64_t *__restrict__ off, const uint32_t *__restrict__ orde
     }
 }
 
-// The small tables: each warp takes the next one (ctr[3]) and runs its whole
-// partition alone -- exact total, Q and the light count, and the placement
-// with checkpoints (scatter_range over the table) -- then leaves the same
-// per-table records as the CTA kernel.  No CTA barrier.
-__global__ void __launch_bounds__(256, kBsegWarpCtas)
-k_bseg_warp(const float *__restrict__ w, const uint64_t *__restrict__ off,
-            const uint32_t *__restrict__ lists, uint32_t ntab, uint32_t *__restrict__ ctr,
-            uint64_t cap, Entry *__restrict__ lh, BuildParams *__restrict__ tp,
-            BatchTab *__restrict__ tabs, uint32_t *__restrict__ sec_tab, CkRec *__restrict__ ckl,
-            CkRec *__restrict__ ckh, SplitRec *__restrict__ recs,
-            wrs_table_summary *__restrict__ info) {
-    __shared__ WarpStage stage[8];
+// The small tables, in two kernels of a warp per table (each table taken
+// from a counter, in list order):
+//   k_bseg_wstat  exact total, Q and the light count (two passes over the
+//                 table), the fixed-point constants and the threshold
+//                 interval, left in the table's BuildParams; small, so that
+//                 many warps stream at once;
+//   k_bseg_wplace the placement with checkpoints (scatter_range over the
+//                 table), then the per-table records.
+// No CTA barrier in either.
+constexpr int kWStatCtas = 6;   // CTAs of 8 warps per SM of k_bseg_wstat
+
+__global__ void __launch_bounds__(256, kWStatCtas)
+k_bseg_wstat(const float *__restrict__ w, const uint64_t *__restrict__ off,
+             const uint32_t *__restrict__ lists, uint32_t ntab, uint32_t *__restrict__ ctr,
+             uint64_t cap, BuildParams *__restrict__ tp, BatchTab *__restrict__ tabs,
+             wrs_table_summary *__restrict__ info) {
+    __shared__ uint64_t sbins[8][kBands * 32];
     __shared__ u128 sband[8][kBands];
+    pdl_trigger();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    WarpStage &sm = stage[warp];
-    // a lane's exact-sum bins (band b at bins[32 b + lane]) share the
-    // staging memory, which the placement uses only after the total
-    uint64_t *bins = reinterpret_cast<uint64_t *>(&sm);
-    static_assert(sizeof(WarpStage) >= kBands * 32 * sizeof(uint64_t), "bins fit the stage");
-    pdl_trigger();   // the split kernel may fill this grid's tail
+    uint64_t *bins = sbins[warp];   // band b of this lane at bins[32 b + lane]
     const uint32_t nsmall = ctr[5];
     const uint32_t *sml = lists + ntab;
     for (;;) {
         uint32_t k = 0;
-        if (lane == 0) k = atomicAdd(ctr + 3, 1u);
+        if (lane == 0) k = atomicAdd(ctr + 6, 1u);
         k = __shfl_sync(0xffffffffu, k, 0);
         if (k >= nsmall) {
-            // launched as a dependent of the CTA kernel (the large tables):
-            // end only after that grid has finished and its writes are
-            // visible, so that the next kernel in the stream sees both
-            asm volatile("griddepcontrol.wait;\n" ::: "memory");
+            // a programmatic dependent of the CTA kernel (the large tables):
+            // end only after that grid has finished, so that what follows
+            // this kernel sees both
+            pdl_wait();
             return;
         }
         const uint32_t t = sml[k];
@@ -1149,23 +1150,73 @@ k_bseg_warp(const float *__restrict__ w, const uint64_t *__restrict__ off,
             Q += __shfl_xor_sync(0xffffffffu, Q, d);
             c += __shfl_xor_sync(0xffffffffu, c, d);
         }
-        const uint64_t nl = c, nh = n - nl, Qn = Q / n;
+        if (lane == 0) {
+            const uint64_t Qn = Q / n;
+            BuildParams p;
+            memset(&p, 0, sizeof p);
+            p.W = W;
+            p.avg = avg;
+            p.Q = Q;
+            p.Qn = Qn;
+            p.n = n;
+            p.nl = c;
+            p.nh = n - c;
+            p.scale = 211 - top;
+            p.qshift = qshift;
+            p.light_max = lmax;
+            p.inv_avg = __double2float_rn(1.0 / avg);
+            p.Qf = __ull2float_rn(Q);
+            p.invQ = __frcp_rn(p.Qf);
+            float mid, half;
+            threshold_interval(ldexp((double)Qn + 0.5, -(211 - top)), (double)lmax, mid, half);
+            p.tmid = mid;
+            p.thalf = half;
+            tp[t] = p;   // Dtot, Etot and the sections follow the placement
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(256, kBsegWarpCtas)
+k_bseg_wplace(const float *__restrict__ w, const uint64_t *__restrict__ off,
+              const uint32_t *__restrict__ lists, uint32_t ntab, uint32_t *__restrict__ ctr,
+              Entry *__restrict__ lh, BuildParams *__restrict__ tp, BatchTab *__restrict__ tabs,
+              uint32_t *__restrict__ sec_tab, CkRec *__restrict__ ckl, CkRec *__restrict__ ckh,
+              SplitRec *__restrict__ recs, wrs_table_summary *__restrict__ info) {
+    __shared__ WarpStage stage[8];
+    pdl_trigger();
+    pdl_wait();   // the statistics of every small table (and the large tables) are done
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    WarpStage &sm = stage[warp];
+    const uint32_t nsmall = ctr[5];
+    const uint32_t *sml = lists + ntab;
+    for (;;) {
+        uint32_t k = 0;
+        if (lane == 0) k = atomicAdd(ctr + 3, 1u);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= nsmall) return;
+        const uint32_t t = sml[k];
+        const BuildParams &pr = tp[t];
+        if (pr.status) continue;   // the statistics kernel recorded the failure
+        const uint64_t base = off[t], n = pr.n;
+        const uint64_t Q = pr.Q, nl = pr.nl, nh = pr.nh;
         const uint64_t ckb = bseg_ck(base, t, 0);
         // ---- stable partition with the prefix checkpoints
         ScatterCtx X;
-        X.w = wt;
+        X.w = w + base;
         X.n = n;
         X.lh = lh + base;
         X.ckl = ckl + ckb;
         X.ckh = ckh + ckb;
-        X.qsc = qsc;
-        X.Qn = Qn;
-        X.lmax = lmax;
-        threshold_interval(ldexp((double)Qn + 0.5, -(211 - top)), (double)lmax, X.tmid, X.thalf);
-        __syncwarp();   // the bins are done with; the stage is reused
+        X.qsc = qscale(pr.qshift);
+        X.Qn = pr.Qn;
+        X.lmax = pr.light_max;
+        X.tmid = pr.tmid;
+        X.thalf = pr.thalf;
+        const double W = pr.W;
         uint64_t SL, SH;
         scatter_range<false>(X, sm, 0u, 0, n, 0, SL, SH);
-        // ---- the table's parameters, sections and end splits
+        // ---- the table's prefix totals, sections and end splits
         const uint32_t ns = (uint32_t)((n + kBSeg - 1) / kBSeg);
         const u128 Dtot = (u128)nl * Q - (u128)SL * n;
         const u128 Etot = (u128)SH * n - (u128)nh * Q;
@@ -1173,25 +1224,9 @@ k_bseg_warp(const float *__restrict__ w, const uint64_t *__restrict__ off,
         if (lane == 0) {
             sec0 = atomicAdd(ctr + 1, ns);
             rec0 = atomicAdd(ctr + 2, ns + 1);
-            BuildParams p;
-            memset(&p, 0, sizeof p);
-            p.Dtot = Dtot;
-            p.Etot = Etot;
-            p.W = W;
-            p.avg = avg;
-            p.Q = Q;
-            p.Qn = Qn;
-            p.n = n;
-            p.nl = nl;
-            p.nh = nh;
-            p.scale = 211 - top;
-            p.qshift = qshift;
-            p.light_max = lmax;
-            p.inv_avg = __double2float_rn(1.0 / avg);
-            p.Qf = __ull2float_rn(Q);
-            p.invQ = __frcp_rn(p.Qf);
-            p.sections = ns;
-            tp[t] = p;
+            tp[t].Dtot = Dtot;
+            tp[t].Etot = Etot;
+            tp[t].sections = ns;
             if ((nl & 31u) == 0) put_ck(ckl, ckb + (nl >> 5), 0u, SL);
             if ((nh & 31u) == 0) put_ck(ckh, ckb + (nh >> 5), 0u, SH);
             wrs_table_summary r;
@@ -1245,7 +1280,7 @@ cudaError_t launch_build_batched_seg(const float *d_w, const uint64_t *d_off, ui
     }
     auto *ctr = reinterpret_cast<uint32_t *>(ws + L.counters);
     auto *lists = reinterpret_cast<uint32_t *>(ws + L.lists);
-    e = cudaMemsetAsync(ctr, 0, 6 * sizeof(uint32_t), st);
+    e = cudaMemsetAsync(ctr, 0, 7 * sizeof(uint32_t), st);
     if (!e) e = cudaMemsetAsync(ws + L.zero, 0, sizeof(SegVal), st);
     if (e) return e;
     const unsigned wblocks = (unsigned)num_sms() * kBsegWarpCtas;
@@ -1259,35 +1294,22 @@ cudaError_t launch_build_batched_seg(const float *d_w, const uint64_t *d_off, ui
     auto *ckl = reinterpret_cast<CkRec *>(ws + L.ckl);
     auto *ckh = reinterpret_cast<CkRec *>(ws + L.ckh);
     auto *recs = reinterpret_cast<SplitRec *>(ws + L.recs);
-    // the large tables (a CTA each), then the small ones (a warp each).  The
-    // warp kernel is a programmatic dependent of the CTA kernel: its CTAs
-    // start in the CTA kernel's tail, where that kernel's last tables leave
-    // SMs idle.
+    // the large tables (a CTA each), then the small ones (a warp each, in two
+    // kernels).  The small tables' statistics kernel is a programmatic
+    // dependent of the CTA kernel: its CTAs start in the CTA kernel's tail,
+    // where that kernel's last tables leave SMs idle.
     k_bseg_part<BT><<<blocks, BT, smem, st>>>(d_w, d_off, lists, ntab, ctr, L.cap, lh, tp, tabs,
                                               sec_tab, ckl, ckh, recs, d_info);
     e = cudaGetLastError();
     if (e) return e;
     {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(wblocks);
-        cfg.blockDim = dim3(256);
-        cfg.dynamicSmemBytes = 0;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, k_bseg_warp, d_w, d_off, (const uint32_t *)lists, ntab, ctr,
-                               (uint64_t)L.cap, lh, tp, tabs, sec_tab, ckl, ckh, recs, d_info);
-        if (e == cudaErrorNotSupported || e == cudaErrorInvalidValue) {
-            // no programmatic launches here: an ordinary launch after the
-            // CTA kernel (griddepcontrol.wait then returns at once)
-            (void)cudaGetLastError();
-            k_bseg_warp<<<wblocks, 256, 0, st>>>(d_w, d_off, lists, ntab, ctr, L.cap, lh, tp, tabs,
-                                                 sec_tab, ckl, ckh, recs, d_info);
-            e = cudaGetLastError();
-        }
+        const unsigned sblocks = (unsigned)num_sms() * kWStatCtas;
+        e = launch_pdl(k_bseg_wstat, dim3(sblocks), dim3(256), 0, st, d_w, d_off,
+                       (const uint32_t *)lists, ntab, ctr, (uint64_t)L.cap, tp, tabs, d_info);
+        if (!e)
+            e = launch_pdl(k_bseg_wplace, dim3(wblocks), dim3(256), 0, st, d_w, d_off,
+                           (const uint32_t *)lists, ntab, ctr, lh, tp, tabs, sec_tab, ckl, ckh, recs,
+                           d_info);
         if (e) return e;
     }
     return launch_bseg_split_pack(ws, L, ntab, d_rows, d_row_ptrs, d_info, st);
