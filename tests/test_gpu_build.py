@@ -194,8 +194,11 @@ def test_split_methods_bit_identical():
     assert torch.equal(a.rows_t, c.rows_t)
 
 
-def test_steps_equal_full_build():
-    w = inputs.exponential(77777, 2)
+@pytest.mark.parametrize("kind,n", [("exponential", 77777), ("gamma", 3_000_001)])
+def test_steps_equal_full_build(kind, n):
+    # the one-call build chains its later kernels as programmatic dependents;
+    # the step calls run every kernel after its predecessor has finished
+    w = inputs.by_name(kind, n, 2)
     a = Built(w)
     s = Built(w, steps=True)
     assert torch.equal(a.rows_t, s.rows_t)
