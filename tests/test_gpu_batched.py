@@ -258,6 +258,31 @@ def test_segmented_build_equals_single_builds(sizes):
         assert np.array_equal(alias, b.alias), t
 
 
+def test_bad_tables_on_both_partition_paths():
+    """Bad tables among large ones (a CTA each, more than 8192 items) and
+    small ones (a warp each, statistics then placement): each reports its
+    status, and every good table is the single-table build bit for bit."""
+    sizes = np.array([20000, 100, 20011, 50, 30000, 7, 40000, 64], np.int64)
+    w, off = inputs.batched(sizes, 29, "gamma")
+    w[off[0] + 17] = np.nan          # large: non-finite
+    w[off[3] + 3] = -2.0             # small: negative
+    w[off[4]: off[5]] = 0.0          # large: zero total
+    w[off[5] + 2] = np.inf           # small: non-finite
+    w[off[6] + 39999] = -0.5         # large: negative, its last item
+    rows, summ, _ = build_batch(w, off)
+    want = [wrs.ENONFINITE, wrs.OK, wrs.OK, wrs.EINVAL, wrs.EZEROSUM, wrs.ENONFINITE,
+            wrs.EINVAL, wrs.OK]
+    assert summ["status"].tolist() == want
+    for t in np.flatnonzero(np.array(want) == wrs.OK):
+        wt = w[off[t]: off[t + 1]]
+        b = Built(wt)
+        assert (summ[t]["W"], summ[t]["nl"], summ[t]["nh"]) == \
+            (b.info["W"], b.info["nl"], b.info["nh"])
+        prob, alias = table_rows(rows, off, t)
+        assert np.array_equal(prob.view(np.uint32), b.prob.view(np.uint32)), t
+        assert np.array_equal(alias, b.alias), t
+
+
 def test_segmented_build_workspace_too_small():
     """A workspace laid out for fewer items than the batch holds: the tables
     that do not fit report WRS_EINVAL, the others are built."""
